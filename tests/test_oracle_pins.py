@@ -1,0 +1,399 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test reaches the expected value by a route that does not go through the
+oracle's own arithmetic: printed constants of the paper, textbook quadrature
+weights, a symbolic derivation from the continuous stage equation
+(eq. MB4_1), brute-force quadrature and root finding, a library ODE solver,
+and invariants (energy, translation, time reversal, plane waves).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.interpolate
+import scipy.optimize
+
+from oracle import mb4_oracle as orc
+from paper_2003_04345_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            out[parts[0]] = parts[1:]
+    return out
+
+
+PAPER = _golden("paper_constants.txt")
+TEXTBOOK = _golden("textbook_values.txt")
+ALPHA_PAPER = Fraction(int(PAPER["alpha1_paper_num"][0]), int(PAPER["alpha1_paper_den"][0]))
+C_PAPER = tuple(Fraction(PAPER[k][0]) for k in ("c1", "c2", "c3"))
+
+
+# ---------------------------------------------------------------------------
+# Independent brute-force stage residual: numerical quadrature of eq. (MB4_3)
+# with a 20-point Gauss-Legendre rule (exact to degree 39), the stage
+# polynomial from scipy's Lagrange interpolation, A from eq. (Adefinition) in
+# floats, and f from np.roll stencils.  No E matrix, no cubic tensor.
+# ---------------------------------------------------------------------------
+def _A_float(alpha, tau, zeta):
+    a = float(alpha)
+    M = np.array([[a + 4, -6 * a - 6, 6 * a],
+                  [-6 * a - 6, 36 * a + 12, -36 * a],
+                  [6 * a, -36 * a, 36 * a]])
+    return np.array([tau, tau ** 2 / 2, tau ** 3 / 3]) @ M @ np.array([1.0, zeta, zeta ** 2])
+
+
+def _f_roll(u, nx, ny, V, chi, tx, ty, eps0):
+    g = u.reshape(ny, nx)
+    Ku = (eps0 * g - tx * (np.roll(g, 1, axis=1) + np.roll(g, -1, axis=1))
+          - ty * (np.roll(g, 1, axis=0) + np.roll(g, -1, axis=0)))
+    Ku = Ku.reshape(nx * ny)
+    return -1j * (Ku + V * u + chi * np.abs(u) ** 2 * u)
+
+
+def brute_phi(nx, ny, V, chi, tx, ty, eps0, u0, U, h, alpha=ALPHA_PAPER, c=C_PAPER, nq=20):
+    nodes = np.array([0.0] + [float(x) for x in c])
+    zq, wq = np.polynomial.legendre.leggauss(nq)
+    zq = 0.5 * (zq + 1.0)
+    wq = 0.5 * wq
+    lag = scipy.interpolate.BarycentricInterpolator(nodes, np.eye(4))
+    X = np.vstack([u0[None, :], U])
+    acc = np.zeros_like(U)
+    for z, w in zip(zq, wq):
+        lz = lag(z)
+        Uz = sum(lz[j] * X[j] for j in range(4))
+        fz = _f_roll(Uz, nx, ny, V, chi, tx, ty, eps0)
+        for i in range(3):
+            acc[i] += w * _A_float(alpha, float(c[i]), z) * fz
+    return U - u0[None, :] - h * acc
+
+
+def _rand_state(rng, S, scale=1.0):
+    return scale * (rng.normal(size=S) + 1j * rng.normal(size=S))
+
+
+# ---------------------------------------------------------------------------
+# Constants.
+# ---------------------------------------------------------------------------
+def test_last_row_of_E_is_simpson_three_eighths():
+    """B_zeta = A_{1,zeta}, and with c3 = 1 the row E_3j = int B l_j is the
+    4-node Newton-Cotes (Simpson 3/8) weight set."""
+    k = orc.mb4_constants(ALPHA_PAPER, C_PAPER)
+    want = [Fraction(x) for x in TEXTBOOK["simpson38"]]
+    assert k["E"][2] == want
+
+
+def test_E_row_sums_are_the_nodes():
+    """Runge-Kutta row-sum condition: sum_{j=0..3} E_ij = c_i."""
+    for c in (C_PAPER, (Fraction(1, 4), Fraction(1, 2), Fraction(1)), (Fraction(3, 10), Fraction(7, 10), Fraction(1))):
+        k = orc.mb4_constants(ALPHA_PAPER, c)
+        for i in range(3):
+            assert sum(k["E"][i]) == c[i]
+
+
+def test_E_eigenvalues_real_and_independent_of_nodes():
+    """Sec. 2.2 (citing Miyatake-Butcher Thm 5.1): E is diagonalisable with real
+    eigenvalues that do not depend on c1, c2, c3."""
+    ev = []
+    for c in (C_PAPER, (Fraction(1, 4), Fraction(1, 2), Fraction(1)), (Fraction(1, 5), Fraction(3, 5), Fraction(1))):
+        E, _ = orc.constants_f64(ALPHA_PAPER, c)
+        lam = np.linalg.eigvals(E[:, 1:])
+        assert np.max(np.abs(lam.imag)) < 1e-12
+        ev.append(np.sort(lam.real))
+    for e in ev[1:]:
+        assert np.allclose(e, ev[0], rtol=0, atol=1e-12)
+    # The trace of E(1:3,1:3) equals the sum of the eigenvalues: a consistency check on the
+    # numerical eigen-solve only.
+    assert abs(sum(ev[0]) - np.trace(orc.constants_f64(ALPHA_PAPER, C_PAPER)[0][:, 1:])) < 1e-12
+
+
+def _charpoly_disc(alpha):
+    """Discriminant of det(x I - E(alpha)), exact (E from the oracle, Fractions)."""
+    E = [row[1:] for row in orc.mb4_constants(Fraction(alpha), C_PAPER)["E"]]
+    tr = E[0][0] + E[1][1] + E[2][2]
+    m2 = (E[0][0] * E[1][1] - E[0][1] * E[1][0] + E[0][0] * E[2][2] - E[0][2] * E[2][0]
+          + E[1][1] * E[2][2] - E[1][2] * E[2][1])
+    det = (E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1])
+           - E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0])
+           + E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]))
+    a, b, cc = -tr, m2, -det      # x^3 + a x^2 + b x + cc
+    return 18 * a * b * cc - 4 * a ** 3 * cc + a * a * b * b - 4 * b ** 3 - 27 * cc * cc
+
+
+def test_alpha1_bound_printed_in_paper():
+    """The paper requires alpha1 < -300 * 0.7770503941 (Sec. 2.2).  The oracle's
+    E(alpha) must switch from three real eigenvalues to a complex pair exactly
+    there (to the 10 printed digits)."""
+    factor = Fraction(PAPER["alpha1_bound_factor"][0])
+    ab = -300 * factor
+    eps = Fraction(300 * 6, 10 ** 11)          # half a unit in the last printed digit, x300, with margin
+    assert _charpoly_disc(ab - eps) > 0        # three distinct real eigenvalues below the bound
+    assert _charpoly_disc(ab + eps) < 0        # a complex pair above it
+    assert _charpoly_disc(ALPHA_PAPER) > 0
+
+
+# ---------------------------------------------------------------------------
+# Residual: exact-coefficient route vs brute-force quadrature.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,chi,eps0", [(4, 3, 1.3, 0.0), (5, 6, -0.7, 0.45)])
+def test_residual_matches_brute_force_quadrature(nx, ny, chi, eps0):
+    rng = np.random.default_rng(7)
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    tx, ty = 1.1, 0.8
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    u0 = _rand_state(rng, S)
+    U = u0[None, :] + 0.1 * np.vstack([_rand_state(rng, S) for _ in range(3)])
+    h = 0.03
+    got = orc.residual(prob, u0, U, h)
+    want = brute_phi(nx, ny, V, chi, tx, ty, eps0, u0, U, h)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(U))
+
+
+def test_residual_at_sites_matches_full_residual():
+    rng = np.random.default_rng(3)
+    nx, ny = 7, 5
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    prob = orc.Problem(nx, ny, V, 0.9, tx=1.2, ty=0.6, eps0=0.3)
+    u0 = _rand_state(rng, S)
+    U = u0[None, :] + 0.1 * np.vstack([_rand_state(rng, S) for _ in range(3)])
+    full = orc.residual(prob, u0, U, 0.02)
+    sites = np.array([0, 6, 7, 17, 34, 28])
+    part = orc.residual_at_sites(nx, ny, V, 0.9, 1.2, 0.6, 0.3, u0, U, 0.02, sites)
+    assert np.max(np.abs(full[:, sites] - part)) <= 1e-15 * np.max(np.abs(U)) * 10
+
+
+# ---------------------------------------------------------------------------
+# Whole step.
+# ---------------------------------------------------------------------------
+def test_step_matches_brute_force_root():
+    """3x3 grid: the root of the brute-force Phi found by MINPACK (finite-difference
+    Jacobian, no decoupling, no E) equals the oracle's Newton result."""
+    rng = np.random.default_rng(11)
+    nx, ny = 3, 3
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    V[4] += 5.0
+    chi, tx, ty, eps0, h = 1.7, 1.0, 0.9, 0.2, 0.05
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    u0 = _rand_state(rng, S, 0.5)
+    u1_orc, U_orc, _ = orc.step(prob, u0, h, return_stages=True)
+
+    def F(x):
+        U = x[:3 * S] + 1j * x[3 * S:]
+        Phi = brute_phi(nx, ny, V, chi, tx, ty, eps0, u0, U.reshape(3, S), h)
+        return np.concatenate([Phi.real.ravel(), Phi.imag.ravel()])
+
+    U0 = np.tile(u0, 3)
+    sol = scipy.optimize.root(F, np.concatenate([U0.real, U0.imag]), method="hybr", tol=1e-15)
+    Ub = (sol.x[:3 * S] + 1j * sol.x[3 * S:]).reshape(3, S)
+    assert np.max(np.abs(F(sol.x))) < 1e-13
+    assert np.max(np.abs(Ub - U_orc)) <= 1e-13 * np.max(np.abs(u0))
+
+
+def _stability_function():
+    """R(z) of MB4 from the continuous stage equation (eq. MB4_1) for u' = lambda u,
+    u0 = 1: U_tau is a cubic in tau; equating coefficients gives R(z) = U_1
+    (c3 = 1, B = A_1)."""
+    sympy = pytest.importorskip("sympy")
+    z, tau, zeta = sympy.symbols("z tau zeta")
+    al = sympy.Rational(ALPHA_PAPER.numerator, ALPHA_PAPER.denominator)
+    M = sympy.Matrix([[al + 4, -6 * al - 6, 6 * al],
+                      [-6 * al - 6, 36 * al + 12, -36 * al],
+                      [6 * al, -36 * al, 36 * al]])
+    A = (sympy.Matrix([[tau, tau ** 2 / 2, tau ** 3 / 3]]) * M * sympy.Matrix([1, zeta, zeta ** 2]))[0]
+    a = sympy.symbols("a1:4")
+    Ut = lambda s: 1 + a[0] * s + a[1] * s ** 2 + a[2] * s ** 3
+    rhs = 1 + z * sympy.integrate(A * Ut(zeta), (zeta, 0, 1))
+    diff = sympy.Poly(sympy.expand(Ut(tau) - rhs), tau)
+    sol = sympy.solve([diff.coeff_monomial(tau ** k) for k in (1, 2, 3)], a, dict=True)[0]
+    R = sympy.simplify(Ut(1).subs(sol))
+    return sympy, z, R
+
+
+def test_stability_function_is_order4_and_unimodular():
+    sympy, z, R = _stability_function()
+    ser = sympy.series(R - sympy.exp(z), z, 0, 6).removeO()
+    for k in range(5):
+        assert sympy.simplify(ser.coeff(z, k)) == 0
+    assert sympy.simplify(ser.coeff(z, 5)) != 0          # order exactly 4
+    assert sympy.simplify(R * R.subs(z, -z) - 1) == 0     # |R(iy)| = 1: the norm is kept for chi = 0
+
+
+def test_linear_step_equals_stability_function():
+    """chi = 0: n oracle steps equal Q R(-i h Lambda)^n Q^H u0 with K+V = Q Lambda Q^H
+    (dense eigendecomposition of a matrix built here by explicit loops)."""
+    sympy, z, R = _stability_function()
+    Rf = sympy.lambdify(z, R, "numpy")
+    rng = np.random.default_rng(5)
+    nx, ny, tx, ty, eps0 = 6, 5, 1.3, 0.7, 0.4
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    V[7] = 20.0
+    A = np.zeros((S, S))
+    for y in range(ny):
+        for x in range(nx):
+            k = y * nx + x
+            A[k, k] = eps0 + V[k]
+            A[k, y * nx + (x + 1) % nx] -= tx
+            A[k, y * nx + (x - 1) % nx] -= tx
+            A[k, ((y + 1) % ny) * nx + x] -= ty
+            A[k, ((y - 1) % ny) * nx + x] -= ty
+    lam, Q = np.linalg.eigh(A)
+    h, n = 0.01, 10
+    u0 = _rand_state(rng, S)
+    want = Q @ (Rf(-1j * h * lam) ** n * (Q.conj().T @ u0))
+    prob = orc.Problem(nx, ny, V, 0.0, tx=tx, ty=ty, eps0=eps0)
+    got, _ = orc.run(prob, u0, h, n)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(u0))
+    assert abs(orc.norm2(got) - orc.norm2(u0)) <= 1e-13 * orc.norm2(u0)
+
+
+def test_fourth_order_convergence_nonlinear():
+    """chi != 0: error against a tight DOP853 reference falls by ~2^4 per halving of h."""
+    rng = np.random.default_rng(9)
+    nx, ny = 4, 3
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    chi = 1.0
+    prob = orc.Problem(nx, ny, V, chi, tx=1.0, ty=1.0, eps0=0.0)
+    u0 = _rand_state(rng, S, 0.7)
+    T = 0.4
+
+    def rhs(t, y):
+        u = y[:S] + 1j * y[S:]
+        f = _f_roll(u, nx, ny, V, chi, 1.0, 1.0, 0.0)
+        return np.concatenate([f.real, f.imag])
+
+    ref = scipy.integrate.solve_ivp(rhs, (0, T), np.concatenate([u0.real, u0.imag]), method="DOP853",
+                                    rtol=1e-13, atol=1e-14).y[:, -1]
+    ref = ref[:S] + 1j * ref[S:]
+    errs = []
+    for n in (10, 20, 40):
+        u, _ = orc.run(prob, u0, T / n, n)
+        errs.append(np.max(np.abs(u - ref)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > 3.8, (errs, rates)
+    assert rates[0] > 3.5, (errs, rates)
+
+
+def test_energy_preserved_grid16():
+    """16x16 wavepacket workload, 100 steps: |dH/H| at the paper's 1e-14 level
+    (we allow 1e-13), the norm to the paper's 1e-8."""
+    w = inputs.grid16_fp64()
+    prob = orc.Problem(w.nx, w.ny, w.potential(), w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
+    u = w.psi0()
+    H0 = orc.energy(prob, u)[0]
+    n0 = orc.norm2(u)
+    drift = 0.0
+    for _ in range(w.steps):
+        u = orc.step(prob, u, w.h)
+        drift = max(drift, abs(orc.energy(prob, u)[0] - H0) / abs(H0))
+    assert drift <= 1e-13
+    assert abs(orc.norm2(u) - n0) <= float(PAPER["norm_rel_drift_bound"][0])
+
+
+def test_time_reversal():
+    """MB4 is symmetric: a step of -h undoes a step of h."""
+    rng = np.random.default_rng(1)
+    nx, ny = 6, 5
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    prob = orc.Problem(nx, ny, V, 1.0, tx=1.3, ty=0.7, eps0=0.4)
+    u0 = _rand_state(rng, S)
+    back = orc.step(prob, orc.step(prob, u0, 0.02), -0.02)
+    assert np.max(np.abs(back - u0)) <= 1e-14 * np.max(np.abs(u0))
+
+
+def test_translation_and_transpose_equivariance():
+    rng = np.random.default_rng(2)
+    nx = ny = 6
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    u0 = _rand_state(rng, S)
+    prob = orc.Problem(nx, ny, V, 1.1, tx=1.0, ty=1.0, eps0=0.2)
+    u1 = orc.step(prob, u0, 0.03).reshape(ny, nx)
+    roll = lambda a: np.roll(np.roll(a.reshape(ny, nx), 2, axis=1), -1, axis=0)
+    prob_r = orc.Problem(nx, ny, roll(V).ravel(), 1.1, tx=1.0, ty=1.0, eps0=0.2)
+    u1r = orc.step(prob_r, roll(u0).ravel(), 0.03)
+    assert np.max(np.abs(u1r - roll(u1).ravel())) <= 1e-14 * np.max(np.abs(u0))
+    tr = lambda a: a.reshape(ny, nx).T.copy()
+    prob_t = orc.Problem(nx, ny, tr(V).ravel(), 1.1, tx=1.0, ty=1.0, eps0=0.2)
+    u1t = orc.step(prob_t, tr(u0).ravel(), 0.03)
+    assert np.max(np.abs(u1t - u1.T.ravel())) <= 1e-14 * np.max(np.abs(u0))
+
+
+def test_plane_wave_keeps_modulus():
+    """psi = a exp(i k.x) with constant V stays a plane wave with |a| kept: the
+    flow is a' = -i(e_k + V + chi |a|^2) a and MB4 preserves the per-site
+    energy, which fixes |a|."""
+    nx, ny = 8, 6
+    S = nx * ny
+    kx, ky = 2 * math.pi * 3 / nx, 2 * math.pi * 1 / ny
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    a = 0.8 * np.exp(0.3j)
+    u0 = (a * np.exp(1j * (kx * x + ky * y))).ravel()
+    prob = orc.Problem(nx, ny, np.full(S, 0.7), 1.5, tx=1.0, ty=0.5, eps0=0.1)
+    u = u0
+    for _ in range(5):
+        u = orc.step(prob, u, 0.05)
+    ratio = u / u0
+    assert np.max(np.abs(ratio - ratio[0])) < 1e-14
+    assert abs(abs(ratio[0]) - 1.0) < 1e-14
+
+
+def test_splitmix64_reference_outputs():
+    want = [int(x, 16) for x in TEXTBOOK["splitmix64_seed0"]]
+    got = [int(v) for v in inputs.splitmix64(0, 3)]
+    assert got == want
+
+
+def test_inputs_shapes_and_normalisation():
+    w = inputs.grid16_fp64()
+    V = w.potential()
+    assert V.shape == (256,)
+    assert np.sum(V > 10) == 3
+    psi = w.psi0()
+    assert abs(orc.norm2(psi) - 1.0) < 1e-15
+    w2 = inputs.grid512_fp64()
+    assert w2.defects() == round(0.01 * 512 * 512)
+
+
+def test_jacobian_matches_finite_difference():
+    """J of eq. (JL) + eq. (JR) (real form, gamma = -chi) against central differences
+    of the brute-force f.  J only steers the simplified Newton iteration, so a
+    wrong J would not move the root; this pins it directly."""
+    rng = np.random.default_rng(4)
+    nx, ny = 4, 3
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    chi, tx, ty, eps0 = 1.4, 1.2, 0.7, 0.3
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    u0 = _rand_state(rng, S)
+    J = orc.jacobian_real(prob, u0).toarray()
+
+    def freal(x):
+        f = _f_roll(x[:S] + 1j * x[S:], nx, ny, V, chi, tx, ty, eps0)
+        return np.concatenate([f.real, f.imag])
+
+    x0 = np.concatenate([u0.real, u0.imag])
+    d = 1e-6
+    Jfd = np.zeros((2 * S, 2 * S))
+    for k in range(2 * S):
+        e = np.zeros(2 * S)
+        e[k] = d
+        Jfd[:, k] = (freal(x0 + e) - freal(x0 - e)) / (2 * d)
+    assert np.max(np.abs(J - Jfd)) < 1e-7 * max(1.0, np.max(np.abs(J)))
