@@ -1,0 +1,201 @@
+/*
+ * mb4.h -- C ABI of libmb4: one time step of the MB4 energy-preserving
+ * integrator (a fourth-order continuous-stage Runge-Kutta method) for the
+ * 2D-grid nonlinear Schroedinger-type system, on one NVIDIA GB300 (sm_103a).
+ *
+ * Source of the method: T. Sakai, S. Kudo, H. Imachi, Y. Miyatake, T. Hoshi,
+ * Y. Yamamoto, "A parallelizable energy-preserving integrator MB4 and its
+ * application to quantum-mechanical wavepacket dynamics", arXiv:2003.04345.
+ *
+ * The system (Sec. 2.1, eq. dNLS, with chi = -gamma):
+ *     i dpsi/dt = (K + V) psi + chi |psi|^2 psi
+ * on an nx x ny periodic grid, site k = y*nx + x (x fastest).  K is the
+ * 5-point operator of eq. (Kdefinition) generalised to hoppings tx, ty and an
+ * on-site shift:  (K psi)_k = onsite*psi_k - tx (psi_{x-1} + psi_{x+1})
+ *                                        - ty (psi_{y-1} + psi_{y+1}).
+ * The paper's Laplacian is tx = 1/hx^2, ty = 1/hy^2, onsite = 2tx + 2ty.
+ * The conserved energy is H = psi^H K psi + psi^H V psi + (chi/2) sum |psi|^4.
+ *
+ * One step (Algorithm 1, one pass of its time loop): the stage equations
+ * Phi(U) = 0 (eq. Phidefinition) are solved by the simplified Newton
+ * iteration (eq. Newton1) with the Jacobian frozen at u0 (eq. Jacobian2),
+ * decoupled through E = T Lambda T^-1 into three independent shifted systems
+ * (I - h lambda_i J) rbar_i = -Phibar_i (eq. Newton3, eq. MB4_4..MB4_6), each
+ * solved matrix-free by an s-step GMRES cycle; u1 = U_c3 (c3 = 1, Sec. 2.2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: MB4_OK (0) or a negative MB4_ERR_* code; mb4_status_string
+ *     gives a message.  Nothing aborts or prints.
+ *   - Pointers are borrowed: the library copies what it needs before the call
+ *     returns (device-to-device or host-to-device) and keeps no reference.
+ *     `on_device` = 1 means the pointer is CUDA device memory of the current
+ *     device, 0 means host memory.
+ *   - A context owns all of its device memory (allocated in mb4_create,
+ *     released in mb4_destroy) and its CUDA stream binding; it is not
+ *     thread-safe.  Calls are asynchronous with respect to the host only where
+ *     stated; every call that returns data synchronises the context's stream.
+ *   - Arrays of S = nx*ny doubles are row-major, k = y*nx + x.  Stage arrays
+ *     hold 3*S doubles, stage i (i = 1..3) at offset (i-1)*S.
+ */
+#ifndef MB4_H
+#define MB4_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MB4_OK                        0
+#define MB4_ERR_INVALID_ARG          -1  /* a size, pointer or option is out of range            */
+#define MB4_ERR_OUT_OF_MEMORY        -2  /* cudaMalloc failed                                     */
+#define MB4_ERR_CUDA                 -3  /* any other CUDA runtime error (no GPU, launch failure) */
+#define MB4_ERR_NEWTON_NOT_CONVERGED -4  /* ||r||_inf still above tolerance after newton_max
+                                            iterations (Sec. 2.2: decrease h and redo)          */
+#define MB4_ERR_KRYLOV_BREAKDOWN     -5  /* the inner least-squares problem was singular          */
+#define MB4_ERR_NONFINITE            -6  /* NaN or Inf met in a Newton update                     */
+#define MB4_ERR_TIMEOUT              -7  /* a bounded device-side wait ran out                    */
+#define MB4_ERR_ADMISSION_REJECTED   -8  /* a batch slot or memory budget is exhausted            */
+
+/* ---- precision modes --------------------------------------------------- */
+#define MB4_FP64   0   /* every step of the path in FP64                                        */
+#define MB4_MIXED  1   /* shifted-system Krylov solves in FP32; residual, state, update and the
+                          energy/norm reductions in FP64 (simplified Newton refines the result) */
+
+typedef struct mb4_ctx mb4_ctx;   /* opaque */
+
+/* Grid and kinetic operator (eq. Kdefinition, generalised; see above). nx, ny >= 3. */
+typedef struct {
+    int nx, ny;
+    double tx, ty;     /* hoppings along x and y                           */
+    double onsite;     /* diagonal of K                                    */
+} mb4_grid;
+
+/* External potential V: S doubles (diagonal of V, Sec. 2.1). Copied at create. */
+typedef struct {
+    const double* v;
+    int on_device;
+} mb4_potential;
+
+/* Nonlinearity: chi = -gamma of eq. (dNLS); Table 2 of the paper calls it eps. */
+typedef struct {
+    double chi;
+} mb4_nonlinearity;
+
+typedef struct {
+    double newton_rtol;  /* stop when ||r^l||_inf <= newton_rtol * ||u0||_inf (Algorithm 1's
+                            test on the Newton update, made relative); default 1e-13           */
+    int    newton_max;   /* Newton iteration cap per step, then MB4_ERR_NEWTON_NOT_CONVERGED;
+                            default 30                                                          */
+    int    krylov_s;     /* Krylov subspace dimension of the one s-step GMRES cycle per Newton
+                            iteration, 1..MB4_MAX_KRYLOV_S; 0 = default (8 FP64, 6 mixed)      */
+    int    precision;    /* MB4_FP64 or MB4_MIXED; default MB4_FP64                            */
+    double alpha1;       /* eq. (Adefinition); must be < -300*0.7770503941; default -712.5    */
+    double c1, c2;       /* interior Lagrange nodes, 0 < c1 < c2 < 1; c3 = 1; default 1/3, 2/3 */
+    void*  stream;       /* cudaStream_t to run on; NULL = the legacy default stream            */
+    int    use_graph;    /* 1 (default): each step is one CUDA-graph launch whose Newton loop is
+                            a device-side conditional WHILE node; 0: host-driven Newton loop    */
+} mb4_options;
+
+#define MB4_MAX_KRYLOV_S 10
+
+typedef struct {
+    long long steps_done;         /* steps accepted by this call                               */
+    long long newton_iters_total; /* Newton iterations over those steps                        */
+    int       newton_iters_last;  /* Newton iterations of the last step attempted              */
+    double    last_update_inf;    /* ||r^l||_inf of the last Newton iteration                  */
+    double    u0_inf;             /* ||u0||_inf of the last step attempted                     */
+} mb4_stats;
+
+/* Fill *opt with the defaults listed above.  Never fails for a non-NULL pointer. */
+int mb4_default_options(mb4_options* opt);
+
+/* Create a context on the current CUDA device: validates the arguments,
+ * computes the MB4 constants (E, E_i0, Lambda, T, T^-1 -- Algorithm 1 lines 1-3,
+ * Sec. 2.2 -- and a 6-node Gauss-Legendre rule that integrates the degree-11
+ * stage integrand of eq. (fIu2) exactly), allocates every device buffer and,
+ * with use_graph, builds the step graph.  h may be negative (MB4 is symmetric).
+ * The state starts at zero; set it with mb4_set_state.  opt may be NULL. */
+int mb4_create(const mb4_grid* grid, const mb4_potential* pot, const mb4_nonlinearity* nl,
+               double h, const mb4_options* opt, mb4_ctx** out);
+
+void mb4_destroy(mb4_ctx* ctx);
+
+/* Copy psi = re + i im (S doubles each) into the context's state. */
+int mb4_set_state(mb4_ctx* ctx, const double* re, const double* im, int on_device);
+
+/* Copy the state out (S doubles each).  Synchronises the context's stream. */
+int mb4_get_state(const mb4_ctx* ctx, double* re, double* im, int on_device);
+
+/* Copy out the converged stage values U_c1, U_c2, U_c3 (eq. Lagrange) of the last
+ * accepted step, 3*S doubles each (untransformed, i.e. T applied).  Synchronises. */
+int mb4_get_stages(const mb4_ctx* ctx, double* re3, double* im3, int on_device);
+
+/* Advance nsteps MB4 steps (Algorithm 1's time loop).  On success returns MB4_OK.
+ * On a Newton failure (Sec. 2.2, last paragraph) or a non-finite update the
+ * state stays at the last accepted step and the code is returned; stats
+ * (nullable) reports what was done.  Synchronises the context's stream. */
+int mb4_step(mb4_ctx* ctx, int nsteps, mb4_stats* stats);
+
+/* Kernel classes reported by mb4_step_profiled. */
+#define MB4_K_STEP_BEGIN   0
+#define MB4_K_SETUP        1   /* u0, (K+V)u0, J coefficients, first right-hand side          */
+#define MB4_K_RESIDUAL     2   /* stage residual Phi (FP64)                                    */
+#define MB4_K_MATVEC       3   /* Krylov basis v_{a+1} = (J/theta) v_a, three systems         */
+#define MB4_K_GRAM         4   /* Gram matrix partial sums                                     */
+#define MB4_K_LSQ          5   /* Gram reduction + least squares                               */
+#define MB4_K_UPDATE       6   /* Newton update Ubar += rbar, ||r||_inf                         */
+#define MB4_K_CHECK        7   /* Newton loop test                                             */
+#define MB4_K_ACCEPT       8   /* u1 = U_c3                                                    */
+#define MB4_K_COUNT        9
+
+/* mb4_step with a host-driven Newton loop and a CUDA event pair around every
+ * kernel launch, for profiling.  Same arithmetic and results as mb4_step (bit
+ * for bit).  Adds to ms[MB4_K_COUNT] the summed device time of each kernel
+ * class and to launches[MB4_K_COUNT] its launch count (both nullable). */
+int mb4_step_profiled(mb4_ctx* ctx, int nsteps, mb4_stats* stats, double* ms, long long* launches);
+
+/* Energy H = U_K + U_E + U_nl of the current state (Sec. 2.1: U_K = u^H K u,
+ * U_E = u^H V u, U_nl = -(gamma/2)||n||^2 = (chi/2) sum |u|^4), with compensated
+ * FP64 sums in a fixed order.  parts3 (nullable) receives U_K, U_E, U_nl. */
+int mb4_energy(const mb4_ctx* ctx, double* H, double* parts3);
+
+/* Norm sum |u|^2 (the total probability of Sec. 3.1), compensated FP64. */
+int mb4_norm(const mb4_ctx* ctx, double* norm2);
+
+/* All observables in one sweep: out[6] = {H, U_K, U_E, U_nl, sum|u|^2, sum|u|^4}
+ * (the last is the participation ratio of Sec. 3.2). */
+int mb4_observables(const mb4_ctx* ctx, double* out6);
+
+/* Stage residual Phi(U) of eq. (Phidefinition) evaluated by the step's FP64
+ * residual kernel for a given u0 (S complex) and stages U (3*S complex), all
+ * untransformed; writes Phi (3*S complex).  For testing the kernel on its own;
+ * it overwrites the context's state with u0 and its stage buffers.  Synchronises. */
+int mb4_residual(mb4_ctx* ctx, const double* u0_re, const double* u0_im,
+                 const double* U_re3, const double* U_im3,
+                 double* phi_re3, double* phi_im3, int on_device);
+
+/* One s-step GMRES cycle on each decoupled system (I - h lambda_i J) x_i = b_i
+ * (eq. MB4_5), J frozen at u0 (eq. JL, eq. JR), in the context's precision.
+ * b and x are in the eigenbasis of E (3*S complex each).  Overwrites the
+ * context's state with u0.  Synchronises. */
+int mb4_solve_shifted(mb4_ctx* ctx, const double* u0_re, const double* u0_im,
+                      const double* b_re3, const double* b_im3,
+                      double* x_re3, double* x_im3, int on_device);
+
+/* Host-only: the MB4 constants the library computes for (alpha1, c1, c2), c3 = 1.
+ * E34: 12 doubles, row-major E[i][j], i = 1..3, j = 0..3 (j = 0 is E_i0, eq. Ei0).
+ * lam3: eigenvalues of E(1:3,1:3), ascending.  T9, Tinv9: row-major 3x3.
+ * gauss_x6, gauss_w6: the 6-node Gauss-Legendre rule on [0, 1].
+ * Any output pointer may be NULL.  Needs no GPU. */
+int mb4_constants(double alpha1, double c1, double c2, double* E34, double* lam3,
+                  double* T9, double* Tinv9, double* gauss_x6, double* gauss_w6);
+
+const char* mb4_status_string(int status);
+
+/* Library version, for diagnostics. */
+const char* mb4_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB4_H */

@@ -32,7 +32,10 @@ quantum-mechanical wavepacket dynamics", arXiv:2003.04345):
   eigen-decoupling of eq. (Newton3) is deliberately not used, so that the GPU
   path's decoupled solves are checked against an independent route.  Each
   linear solve is a sparse direct LU (SuperLU via scipy), like the paper's use
-  of a sparse direct solver (Sec. 3.2).
+  of a sparse direct solver (Sec. 3.2), for grids of up to 1024 sites; above
+  that, where the LU fill-in makes it slow, scipy's restarted GMRES on the same
+  coupled matrix to a relative residual of 1e-13.  The solver changes only how
+  fast the Newton iteration reaches the root of Phi(U) = 0, not the root.
 * Energy H = u^H K u + u^H V u + (chi/2) sum |u|^4 (Sec. 2.1, U_K + U_E + U_I)
   and the norm sum |u|^2 are summed with math.fsum (correctly rounded).
 """
@@ -279,8 +282,29 @@ class NewtonNotConverged(RuntimeError):
     pass
 
 
+def _coupled_solver(M, method):
+    """x = M^-1 rhs for the coupled Newton matrix: SuperLU, or scipy GMRES."""
+    if method == "lu":
+        lu = spla.splu(sp.csc_matrix(M))
+        return lu.solve
+    Mc = sp.csr_matrix(M)
+
+    def solve(rhs):
+        nrm = np.linalg.norm(rhs)
+        if nrm == 0.0:
+            return np.zeros_like(rhs)
+        try:
+            x, info = spla.gmres(Mc, rhs, rtol=1e-13, atol=0.0, restart=60, maxiter=50)
+        except TypeError:   # older scipy spells the relative tolerance ``tol``
+            x, info = spla.gmres(Mc, rhs, tol=1e-13, atol=0.0, restart=60, maxiter=50)
+        if info != 0:
+            raise RuntimeError(f"oracle GMRES did not converge (info={info})")
+        return x
+    return solve
+
+
 def step(prob: Problem, u0, h, tol=1e-14, max_iter=50, alpha1=ALPHA1_PAPER, c=C_PAPER,
-         return_stages=False):
+         return_stages=False, solver=None):
     """One MB4 step (Algorithm 1, one pass of its time loop) by simplified Newton
     on the coupled system (eq. Newton1).  Requires c3 = 1 so that u1 = U_c3.
 
@@ -290,13 +314,15 @@ def step(prob: Problem, u0, h, tol=1e-14, max_iter=50, alpha1=ALPHA1_PAPER, c=C_
         raise ValueError("the u1 = U_c3 shortcut needs c3 = 1")
     S = prob.S
     u0 = np.asarray(u0, dtype=np.complex128).reshape(S)
-    lu = spla.splu(newton_matrix(prob, u0, h, alpha1, c))
+    if solver is None:
+        solver = "lu" if S <= 1024 else "gmres"
+    solve = _coupled_solver(newton_matrix(prob, u0, h, alpha1, c), solver)
     U = np.vstack([u0, u0, u0])                    # U^0 = e3 (x) u0
     scale = max(float(np.max(np.abs(np.concatenate([u0.real, u0.imag])))), 1e-300)
     for it in range(1, max_iter + 1):
         Phi = residual(prob, u0, U, h, alpha1, c)
         rhs = -np.concatenate([to_real(Phi[i]) for i in range(3)])
-        r = lu.solve(rhs)
+        r = solve(rhs)
         U = U + np.vstack([to_complex(r[i * 2 * S:(i + 1) * 2 * S], S) for i in range(3)])
         rho = float(np.max(np.abs(r)))
         if rho <= tol * scale:

@@ -1,0 +1,620 @@
+// libmb4 C ABI: contexts, device buffers, the step graph and the entry points
+// declared in include/mb4.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mb4_internal.h"
+
+using namespace mb4;
+
+struct mb4_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = MB4_FP64;
+  int use_graph = 1;
+  Constants k{};
+  StepParams p{};
+  DevBuffers b{};
+  size_t tk = 8;                  // sizeof(TK)
+  // step graph (one launch = one MB4 step)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle handle = 0;
+  // scratch for state I/O and the test entry points (allocated on first use)
+  double2* tmp3a = nullptr;
+  double2* tmp3b = nullptr;
+  double* io = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) {
+  if (e == cudaSuccess) return MB4_OK;
+  if (e == cudaErrorMemoryAllocation) return MB4_ERR_OUT_OF_MEMORY;
+  return MB4_ERR_CUDA;
+}
+
+#define MB4_TRY(call)                        \
+  do {                                       \
+    int _rc = cuda_rc(call);                 \
+    if (_rc != MB4_OK) return _rc;           \
+  } while (0)
+
+int dalloc(mb4_ctx* c, void** ptr, size_t bytes) {
+  // 256-byte aligned by cudaMalloc; bytes rounded up so every plane keeps that alignment.
+  bytes = (bytes + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_rc(e);
+  }
+  c->allocs.push_back(*ptr);
+  return MB4_OK;
+}
+
+template <typename TK>
+void enqueue_newton_body(mb4_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+  launch_residual<TK>(c->p, c->b, true, s);
+  launch_krylov<TK>(c->p, c->b, s);
+  launch_update<TK>(c->p, c->b, s);
+  launch_newton_check(c->p, c->b, handle, use_cond, s);
+}
+
+void enqueue_body(mb4_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+  if (c->precision == MB4_MIXED) enqueue_newton_body<float>(c, s, handle, use_cond);
+  else enqueue_newton_body<double>(c, s, handle, use_cond);
+}
+
+void enqueue_setup(mb4_ctx* c, cudaStream_t s) {
+  launch_step_begin(c->b, s);
+  if (c->precision == MB4_MIXED) launch_setup<float>(c->p, c->b, s);
+  else launch_setup<double>(c->p, c->b, s);
+}
+
+// One MB4 step as a graph: [begin, setup] -> WHILE(cont){residual, krylov, update, check} -> accept.
+int build_graph(mb4_ctx* c) {
+  cudaStream_t cap;
+  MB4_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  int rc = MB4_OK;
+  cudaGraph_t g = nullptr;
+  do {
+    if ((rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) != MB4_OK) break;
+    enqueue_setup(c, cap);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((rc = cuda_rc(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &capg, &deps, nullptr, &ndeps))) != MB4_OK) {
+      cudaStreamEndCapture(cap, &g);
+      break;
+    }
+    cudaGraphConditionalHandle h;
+    if ((rc = cuda_rc(cudaGraphConditionalHandleCreate(&h, capg, 1, cudaGraphCondAssignDefault))) != MB4_OK) {
+      cudaStreamEndCapture(cap, &g);
+      break;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if ((rc = cuda_rc(cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp))) != MB4_OK) {
+      cudaStreamEndCapture(cap, &g);
+      break;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((rc = cuda_rc(cudaStreamUpdateCaptureDependencies(cap, &cnode, nullptr, 1,
+                                                          cudaStreamSetCaptureDependencies))) != MB4_OK) {
+      cudaStreamEndCapture(cap, &g);
+      break;
+    }
+    launch_accept(c->p, c->b, cap);
+    if ((rc = cuda_rc(cudaStreamEndCapture(cap, &g))) != MB4_OK) break;
+    if ((rc = cuda_rc(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                                    cudaStreamCaptureModeThreadLocal))) != MB4_OK)
+      break;
+    enqueue_body(c, cap, (unsigned long long)h, 1);
+    cudaGraph_t body_out = nullptr;
+    if ((rc = cuda_rc(cudaStreamEndCapture(cap, &body_out))) != MB4_OK) break;
+    if ((rc = cuda_rc(cudaGraphInstantiate(&c->exec, g, 0))) != MB4_OK) break;
+    c->graph = g;
+    c->handle = h;
+    g = nullptr;
+  } while (0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  return rc;
+}
+
+int ensure_scratch(mb4_ctx* c) {
+  if (c->tmp3a) return MB4_OK;
+  const size_t S = (size_t)c->p.S;
+  int rc;
+  if ((rc = dalloc(c, (void**)&c->tmp3a, 3 * S * sizeof(double2))) != MB4_OK) return rc;
+  if ((rc = dalloc(c, (void**)&c->tmp3b, 3 * S * sizeof(double2))) != MB4_OK) return rc;
+  if ((rc = dalloc(c, (void**)&c->io, 6 * S * sizeof(double))) != MB4_OK) return rc;
+  return MB4_OK;
+}
+
+// Bring n doubles (re, im each) onto the device, planar, into c->io[0..2n).
+int stage_in(mb4_ctx* c, const double* re, const double* im, size_t n, int on_device, const double** dre,
+             const double** dim) {
+  if (on_device) {
+    *dre = re;
+    *dim = im;
+    return MB4_OK;
+  }
+  MB4_TRY(cudaMemcpyAsync(c->io, re, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  MB4_TRY(cudaMemcpyAsync(c->io + n, im, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  *dre = c->io;
+  *dim = c->io + n;
+  return MB4_OK;
+}
+
+int stage_out(mb4_ctx* c, const double2* z, double* re, double* im, size_t n, int on_device) {
+  if (on_device) {
+    launch_unpack(z, re, im, (int)n, c->stream);
+    MB4_TRY(cudaGetLastError());
+    MB4_TRY(cudaStreamSynchronize(c->stream));
+    return MB4_OK;
+  }
+  launch_unpack(z, c->io, c->io + n, (int)n, c->stream);
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaMemcpyAsync(re, c->io, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MB4_TRY(cudaMemcpyAsync(im, c->io + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int reset_status(mb4_ctx* c) {
+  MB4_TRY(cudaMemsetAsync(c->b.status, 0, sizeof(DevStatus), c->stream));
+  return MB4_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mb4_default_options(mb4_options* o) {
+  if (!o) return MB4_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->newton_rtol = 1e-13;
+  o->newton_max = 30;
+  o->krylov_s = 0;
+  o->precision = MB4_FP64;
+  o->alpha1 = -300.0 * 19.0 / 8.0;
+  o->c1 = 1.0 / 3.0;
+  o->c2 = 2.0 / 3.0;
+  o->stream = nullptr;
+  o->use_graph = 1;
+  return MB4_OK;
+}
+
+const char* mb4_version(void) { return "libmb4 0.1 (sm_103a)"; }
+
+const char* mb4_status_string(int s) {
+  switch (s) {
+    case MB4_OK: return "ok";
+    case MB4_ERR_INVALID_ARG: return "invalid argument";
+    case MB4_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case MB4_ERR_CUDA: return "CUDA runtime error";
+    case MB4_ERR_NEWTON_NOT_CONVERGED: return "simplified Newton iteration did not converge (reduce h)";
+    case MB4_ERR_KRYLOV_BREAKDOWN: return "Krylov least-squares breakdown";
+    case MB4_ERR_NONFINITE: return "non-finite value in a Newton update";
+    case MB4_ERR_TIMEOUT: return "bounded device wait timed out";
+    case MB4_ERR_ADMISSION_REJECTED: return "admission rejected: no slot or memory budget";
+    default: return "unknown status";
+  }
+}
+
+void mb4_destroy(mb4_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+int mb4_create(const mb4_grid* grid, const mb4_potential* pot, const mb4_nonlinearity* nl, double h,
+               const mb4_options* opt_in, mb4_ctx** out) {
+  if (!out) return MB4_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grid || !pot || !nl || !pot->v) return MB4_ERR_INVALID_ARG;
+  if (grid->nx < 3 || grid->ny < 3) return MB4_ERR_INVALID_ARG;
+  if ((long long)grid->nx * grid->ny > (1LL << 30)) return MB4_ERR_INVALID_ARG;
+  if (!std::isfinite(h) || h == 0.0) return MB4_ERR_INVALID_ARG;
+  if (!std::isfinite(grid->tx) || !std::isfinite(grid->ty) || !std::isfinite(grid->onsite) ||
+      !std::isfinite(nl->chi))
+    return MB4_ERR_INVALID_ARG;
+  mb4_options o;
+  if (opt_in) o = *opt_in;
+  else mb4_default_options(&o);
+  if (o.precision != MB4_FP64 && o.precision != MB4_MIXED) return MB4_ERR_INVALID_ARG;
+  if (o.krylov_s == 0) o.krylov_s = (o.precision == MB4_FP64) ? 8 : 6;
+  if (o.krylov_s < 1 || o.krylov_s > MB4_MAX_KRYLOV_S) return MB4_ERR_INVALID_ARG;
+  if (!(o.newton_rtol > 0.0) || o.newton_max < 1) return MB4_ERR_INVALID_ARG;
+
+  mb4_ctx* c = new (std::nothrow) mb4_ctx();
+  if (!c) return MB4_ERR_OUT_OF_MEMORY;
+  int rc = compute_constants(o.alpha1, o.c1, o.c2, &c->k);
+  if (rc != MB4_OK) {
+    delete c;
+    return rc;
+  }
+  c->precision = o.precision;
+  c->use_graph = o.use_graph ? 1 : 0;
+  c->stream = (cudaStream_t)o.stream;
+  c->tk = (o.precision == MB4_MIXED) ? sizeof(float) : sizeof(double);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return MB4_ERR_CUDA;
+  }
+  const int nx = grid->nx, ny = grid->ny;
+  const size_t S = (size_t)nx * ny;
+
+  // Potential on the host (to derive d = onsite + V and the Krylov scale).
+  std::vector<double> V(S);
+  if (pot->on_device) {
+    if (cudaMemcpy(V.data(), pot->v, S * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      delete c;
+      return MB4_ERR_CUDA;
+    }
+  } else {
+    std::memcpy(V.data(), pot->v, S * sizeof(double));
+  }
+  double vmax = 0.0;
+  for (size_t k = 0; k < S; ++k) {
+    if (!std::isfinite(V[k])) {
+      delete c;
+      return MB4_ERR_INVALID_ARG;
+    }
+    vmax = std::fmax(vmax, std::fabs(grid->onsite + V[k]));
+  }
+  std::vector<double> D(S);
+  for (size_t k = 0; k < S; ++k) D[k] = grid->onsite + V[k];
+
+  // Kernel constants.
+  StepParams& p = c->p;
+  const Constants& K = c->k;
+  p.nx = nx;
+  p.ny = ny;
+  p.S = (int)S;
+  p.s = o.krylov_s;
+  p.tx = grid->tx;
+  p.ty = grid->ty;
+  p.eps0 = grid->onsite;
+  p.chi = nl->chi;
+  p.h = h;
+  for (int i = 0; i < 3; ++i) {
+    p.hlam[i] = h * K.lam[i];
+    double e0 = 0, tau = 0, tc = 0;
+    for (int j = 0; j < 3; ++j) {
+      e0 += K.Tinv[i][j] * K.E[j][0];
+      tau += K.Tinv[i][j];
+      tc += K.Tinv[i][j] * K.c[j];
+    }
+    p.he0[i] = h * e0;
+    p.tau[i] = tau;
+    p.hTc[i] = h * tc;
+    for (int j = 0; j < 3; ++j) p.T[i][j] = K.T[i][j];
+  }
+  for (int q = 0; q < kGauss; ++q) {
+    const double z = K.gx[q];
+    double l[4];
+    for (int j = 0; j < 4; ++j) l[j] = ((K.lag[j][3] * z + K.lag[j][2]) * z + K.lag[j][1]) * z + K.lag[j][0];
+    p.L0[q] = l[0];
+    for (int n = 0; n < 3; ++n) {
+      double s = 0;
+      for (int m = 0; m < 3; ++m) s += l[m + 1] * K.T[m][n];
+      p.LT[q][n] = s;
+    }
+    double W[3];
+    for (int j = 0; j < 3; ++j) W[j] = K.gw[q] * ((K.Acoef[j][2] * z + K.Acoef[j][1]) * z + K.Acoef[j][0]);
+    for (int i = 0; i < 3; ++i) {
+      double s = 0;
+      for (int j = 0; j < 3; ++j) s += K.Tinv[i][j] * W[j];
+      p.hchiW[i][q] = h * nl->chi * s;
+    }
+  }
+  double theta = vmax + 2.0 * std::fabs(grid->tx) + 2.0 * std::fabs(grid->ty);
+  if (!(theta > 0.0)) theta = 1.0;
+  p.inv_theta = 1.0 / theta;
+  for (int i = 0; i < 3; ++i) p.sig[i] = h * K.lam[i] * theta;
+  p.newton_rtol = o.newton_rtol;
+  p.newton_max = o.newton_max;
+  p.trunc_rel = (o.precision == MB4_MIXED) ? 1e-12f : 1e-26f;
+
+  // Device buffers.
+  DevBuffers& b = c->b;
+  const size_t tk = c->tk;
+  const int nent = (p.s + 1) * (p.s + 2) / 2;
+  if ((rc = dalloc(c, (void**)&b.u, S * sizeof(double2))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.V, S * sizeof(double))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.d, S * sizeof(double))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.S0, S * sizeof(double2))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.Ubar, 3 * S * sizeof(double2))) != MB4_OK ||
+      (rc = dalloc(c, &b.jc, S * 4 * tk)) != MB4_OK ||
+      (rc = dalloc(c, &b.v, (size_t)(p.s + 1) * 3 * S * 2 * tk)) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.gram_part, (size_t)kGramBlocks * 3 * nent * sizeof(double))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.coef, 3 * kMaxS * sizeof(double))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.obs_part, 304 * 6 * 2 * sizeof(double))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.obs_out, 16 * sizeof(double))) != MB4_OK ||
+      (rc = dalloc(c, (void**)&b.status, sizeof(DevStatus))) != MB4_OK) {
+    mb4_destroy(c);
+    return rc;
+  }
+  if ((rc = cuda_rc(cudaMemcpyAsync(b.V, V.data(), S * sizeof(double), cudaMemcpyHostToDevice, c->stream))) ||
+      (rc = cuda_rc(cudaMemcpyAsync(b.d, D.data(), S * sizeof(double), cudaMemcpyHostToDevice, c->stream))) ||
+      (rc = cuda_rc(cudaMemsetAsync(b.u, 0, S * sizeof(double2), c->stream))) ||
+      (rc = cuda_rc(cudaMemsetAsync(b.Ubar, 0, 3 * S * sizeof(double2), c->stream))) ||
+      (rc = cuda_rc(cudaMemsetAsync(b.coef, 0, 3 * kMaxS * sizeof(double), c->stream))) ||
+      (rc = reset_status(c)) || (rc = cuda_rc(cudaStreamSynchronize(c->stream)))) {
+    mb4_destroy(c);
+    return rc;
+  }
+  if (c->use_graph) {
+    if ((rc = build_graph(c)) != MB4_OK) {
+      mb4_destroy(c);
+      return rc;
+    }
+  }
+  *out = c;
+  return MB4_OK;
+}
+
+int mb4_set_state(mb4_ctx* c, const double* re, const double* im, int on_device) {
+  if (!c || !re || !im) return MB4_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = ensure_scratch(c)) != MB4_OK) return rc;
+  const size_t S = (size_t)c->p.S;
+  const double *dre, *dim;
+  if ((rc = stage_in(c, re, im, S, on_device, &dre, &dim)) != MB4_OK) return rc;
+  launch_pack(dre, dim, c->b.u, (int)S, c->stream);
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int mb4_get_state(const mb4_ctx* cc, double* re, double* im, int on_device) {
+  mb4_ctx* c = const_cast<mb4_ctx*>(cc);
+  if (!c || !re || !im) return MB4_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = ensure_scratch(c)) != MB4_OK) return rc;
+  return stage_out(c, c->b.u, re, im, (size_t)c->p.S, on_device);
+}
+
+int mb4_get_stages(const mb4_ctx* cc, double* re3, double* im3, int on_device) {
+  mb4_ctx* c = const_cast<mb4_ctx*>(cc);
+  if (!c || !re3 || !im3) return MB4_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = ensure_scratch(c)) != MB4_OK) return rc;
+  launch_mix3(c->p.S, c->b.Ubar, c->tmp3a, c->p.T, c->stream);
+  MB4_TRY(cudaGetLastError());
+  // the io buffer holds 6*S doubles: enough for 3*S re + 3*S im
+  return stage_out(c, c->tmp3a, re3, im3, 3 * (size_t)c->p.S, on_device);
+}
+
+int mb4_step(mb4_ctx* c, int nsteps, mb4_stats* stats) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  int rc0 = reset_status(c);
+  if (rc0 != MB4_OK) return rc0;
+  if (c->use_graph) {
+    for (int n = 0; n < nsteps; ++n) MB4_TRY(cudaGraphLaunch(c->exec, c->stream));
+  } else {
+    for (int n = 0; n < nsteps; ++n) {
+      enqueue_setup(c, c->stream);
+      DevStatus hs;
+      for (;;) {
+        enqueue_body(c, c->stream, 0ull, 0);
+        MB4_TRY(cudaGetLastError());
+        MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+        MB4_TRY(cudaStreamSynchronize(c->stream));
+        if (hs.error || !hs.cont) break;
+      }
+      launch_accept(c->p, c->b, c->stream);
+      if (hs.error) break;
+    }
+  }
+  MB4_TRY(cudaGetLastError());
+  DevStatus hs;
+  MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  if (stats) {
+    stats->steps_done = hs.steps_done;
+    stats->newton_iters_total = hs.newton_total;
+    stats->newton_iters_last = hs.last_newton_iters;
+    stats->last_update_inf = hs.last_rmax;
+    stats->u0_inf = hs.last_u0max;
+  }
+  return hs.error;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct Prof {
+  cudaStream_t s;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> open;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  double ms[MB4_K_COUNT] = {0};
+  long long n[MB4_K_COUNT] = {0};
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  template <typename F> void run(int cls, int count, F f) {
+    cudaEvent_t a = ev(), b = ev();
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(b, s);
+    open.push_back({cls, {a, b}});
+    n[cls] += count;
+  }
+  void harvest() {  // stream must be synchronised
+    for (auto& o : open) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, o.second.first, o.second.second);
+      ms[o.first] += t;
+    }
+    open.clear();
+    used = 0;
+  }
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+template <typename TK>
+int profiled_steps(mb4_ctx* c, int nsteps, Prof& P) {
+  cudaStream_t s = c->stream;
+  for (int n = 0; n < nsteps; ++n) {
+    P.run(MB4_K_STEP_BEGIN, 1, [&] { launch_step_begin(c->b, s); });
+    P.run(MB4_K_SETUP, 1, [&] { launch_setup<TK>(c->p, c->b, s); });
+    DevStatus hs;
+    for (;;) {
+      P.run(MB4_K_RESIDUAL, 1, [&] { launch_residual<TK>(c->p, c->b, true, s); });
+      P.run(MB4_K_MATVEC, c->p.s, [&] { launch_matvecs<TK>(c->p, c->b, s); });
+      P.run(MB4_K_GRAM, 1, [&] { launch_gram<TK>(c->p, c->b, s); });
+      P.run(MB4_K_LSQ, 1, [&] { launch_lsq(c->p, c->b, s); });
+      P.run(MB4_K_UPDATE, 1, [&] { launch_update<TK>(c->p, c->b, s); });
+      P.run(MB4_K_CHECK, 1, [&] { launch_newton_check(c->p, c->b, 0ull, 0, s); });
+      MB4_TRY(cudaGetLastError());
+      MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      MB4_TRY(cudaStreamSynchronize(s));
+      P.harvest();
+      if (hs.error || !hs.cont) break;
+    }
+    P.run(MB4_K_ACCEPT, 1, [&] { launch_accept(c->p, c->b, s); });
+    if (hs.error) break;
+  }
+  MB4_TRY(cudaStreamSynchronize(s));
+  P.harvest();
+  return MB4_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  int rc = reset_status(c);
+  if (rc != MB4_OK) return rc;
+  Prof P;
+  P.s = c->stream;
+  rc = (c->precision == MB4_MIXED) ? profiled_steps<float>(c, nsteps, P) : profiled_steps<double>(c, nsteps, P);
+  if (rc != MB4_OK) return rc;
+  for (int k = 0; k < MB4_K_COUNT; ++k) {
+    if (ms) ms[k] += P.ms[k];
+    if (launches) launches[k] += P.n[k];
+  }
+  DevStatus hs;
+  MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  if (stats) {
+    stats->steps_done = hs.steps_done;
+    stats->newton_iters_total = hs.newton_total;
+    stats->newton_iters_last = hs.last_newton_iters;
+    stats->last_update_inf = hs.last_rmax;
+    stats->u0_inf = hs.last_u0max;
+  }
+  return hs.error;
+}
+
+int mb4_observables(const mb4_ctx* cc, double* out6) {
+  mb4_ctx* c = const_cast<mb4_ctx*>(cc);
+  if (!c || !out6) return MB4_ERR_INVALID_ARG;
+  launch_observables(c->p, c->b, c->stream);
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaMemcpyAsync(out6, c->b.obs_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int mb4_energy(const mb4_ctx* c, double* H, double* parts3) {
+  if (!c || !H) return MB4_ERR_INVALID_ARG;
+  double o[6];
+  int rc = mb4_observables(c, o);
+  if (rc != MB4_OK) return rc;
+  *H = o[0];
+  if (parts3) {
+    parts3[0] = o[1];
+    parts3[1] = o[2];
+    parts3[2] = o[3];
+  }
+  return MB4_OK;
+}
+
+int mb4_norm(const mb4_ctx* c, double* norm2) {
+  if (!c || !norm2) return MB4_ERR_INVALID_ARG;
+  double o[6];
+  int rc = mb4_observables(c, o);
+  if (rc != MB4_OK) return rc;
+  *norm2 = o[4];
+  return MB4_OK;
+}
+
+int mb4_residual(mb4_ctx* c, const double* u0_re, const double* u0_im, const double* U_re3, const double* U_im3,
+                 double* phi_re3, double* phi_im3, int on_device) {
+  if (!c || !u0_re || !u0_im || !U_re3 || !U_im3 || !phi_re3 || !phi_im3) return MB4_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = mb4_set_state(c, u0_re, u0_im, on_device)) != MB4_OK) return rc;
+  const size_t S = (size_t)c->p.S;
+  if ((rc = reset_status(c)) != MB4_OK) return rc;
+  enqueue_setup(c, c->stream);
+  const double *dre, *dim;
+  if ((rc = stage_in(c, U_re3, U_im3, 3 * S, on_device, &dre, &dim)) != MB4_OK) return rc;
+  launch_pack(dre, dim, c->tmp3a, (int)(3 * S), c->stream);
+  launch_mix3((int)S, c->tmp3a, c->b.Ubar, c->k.Tinv, c->stream);
+  if (c->precision == MB4_MIXED) launch_residual_out<float>(c->p, c->b, c->tmp3b, c->stream);
+  else launch_residual_out<double>(c->p, c->b, c->tmp3b, c->stream);
+  // Phi = T Phibar = -T b
+  double mT[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) mT[i][j] = -c->k.T[i][j];
+  launch_mix3((int)S, c->tmp3b, c->tmp3a, mT, c->stream);
+  MB4_TRY(cudaGetLastError());
+  return stage_out(c, c->tmp3a, phi_re3, phi_im3, 3 * S, on_device);
+}
+
+int mb4_solve_shifted(mb4_ctx* c, const double* u0_re, const double* u0_im, const double* b_re3,
+                      const double* b_im3, double* x_re3, double* x_im3, int on_device) {
+  if (!c || !u0_re || !u0_im || !b_re3 || !b_im3 || !x_re3 || !x_im3) return MB4_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = mb4_set_state(c, u0_re, u0_im, on_device)) != MB4_OK) return rc;
+  const size_t S = (size_t)c->p.S;
+  if ((rc = reset_status(c)) != MB4_OK) return rc;
+  enqueue_setup(c, c->stream);
+  const double *dre, *dim;
+  if ((rc = stage_in(c, b_re3, b_im3, 3 * S, on_device, &dre, &dim)) != MB4_OK) return rc;
+  launch_pack(dre, dim, c->tmp3a, (int)(3 * S), c->stream);
+  if (c->precision == MB4_MIXED) {
+    launch_copy_rhs_in<float>(c->p, c->b, c->tmp3a, c->stream);
+    launch_krylov<float>(c->p, c->b, c->stream);
+    launch_copy_solution_out<float>(c->p, c->b, c->tmp3b, c->stream);
+  } else {
+    launch_copy_rhs_in<double>(c->p, c->b, c->tmp3a, c->stream);
+    launch_krylov<double>(c->p, c->b, c->stream);
+    launch_copy_solution_out<double>(c->p, c->b, c->tmp3b, c->stream);
+  }
+  MB4_TRY(cudaGetLastError());
+  return stage_out(c, c->tmp3b, x_re3, x_im3, 3 * S, on_device);
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Internal declarations shared by the libmb4 translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mb4.h"
+
+namespace mb4 {
+
+constexpr int kGauss = 6;          // Gauss-Legendre nodes: exact for the degree-11 integrand of eq. (fIu2)
+constexpr int kMaxS = MB4_MAX_KRYLOV_S;
+constexpr int kGramBlocks = 304;   // blocks of the Gram reduction (2 per SM on 152 SMs)
+
+// MB4 constants in FP64, computed on the host (mb4_consts.cpp).
+struct Constants {
+  double alpha1, c[3];
+  double E[3][4];        // E[i][j], i = 1..3 -> 0..2, j = 0..3 (j = 0: E_i0)
+  double lam[3];         // eigenvalues of E(1:3,1:3), ascending
+  double T[3][3];        // E3 = T diag(lam) Tinv, unit columns
+  double Tinv[3][3];
+  double gx[kGauss], gw[kGauss];   // Gauss-Legendre on [0, 1]
+  double lag[4][4];      // l_j(zeta) = sum_p lag[j][p] zeta^p on nodes (0, c1, c2, c3)
+  double Acoef[3][3];    // A_{c_i, zeta} = sum_b Acoef[i][b] zeta^b  (eq. Adefinition)
+};
+
+// Returns 0 or an MB4_ERR_* code (alpha1 out of range, bad nodes).
+int compute_constants(double alpha1, double c1, double c2, Constants* out);
+
+// Everything a kernel needs, passed by value (kernel parameter space), so that
+// several contexts with different h, grids or potentials can coexist.
+struct StepParams {
+  int nx, ny, S;
+  int s;                   // Krylov subspace dimension
+  double tx, ty, eps0, chi, h;
+  // residual in the eigenbasis of E: Ubar = Tinv U
+  double hlam[3];          // h * lambda_i
+  double he0[3];           // h * (Tinv E_{.0})_i
+  double tau[3];           // (Tinv 1)_i : Ubar^0 = tau (x) u0
+  double hTc[3];           // h * (Tinv c)_i : Phibar^0 = i hTc_i f-part at u0
+  double L0[kGauss];       // l_0(zeta_q)
+  double LT[kGauss][3];    // sum_m l_m(zeta_q) T[m][n]
+  double hchiW[3][kGauss]; // h chi (Tinv W)_iq, W_jq = w_q A_{c_j}(zeta_q)
+  double T[3][3];          // r = T rbar ;  u1 = sum_n T[2][n] Ubar_n
+  // Krylov (monomial basis of J/theta)
+  double inv_theta;        // 1 / theta
+  double sig[3];           // h lambda_i theta
+  double newton_rtol;
+  int newton_max;
+  float trunc_rel;         // relative pivot threshold of the Gram Cholesky
+};
+
+// Device-resident control block of one context.
+struct DevStatus {
+  int error;                         // MB4_OK or MB4_ERR_*
+  int newton_iter;                   // iterations of the current step
+  int nonfinite;                     // set by update kernels
+  int last_newton_iters;
+  long long steps_done;              // accepted steps since the last reset
+  long long newton_total;
+  unsigned long long rmax_bits;      // max |r| of the current iteration (double bits, >= 0)
+  unsigned long long u0max_bits;     // ||u0||_inf of the current step (double bits)
+  double last_rmax;
+  double last_u0max;
+  int cont;                          // 1 while the Newton loop of the current step goes on
+};
+
+// Device buffers of one context.
+struct DevBuffers {
+  double2* u;        // state, S
+  double* V;         // potential, S
+  double* d;         // onsite + V, S
+  double2* S0;       // (K+V) u0, S
+  double2* Ubar;     // transformed stages, 3*S
+  void* jc;          // J coefficients {e1, e2, a, 0} (TK4), S
+  void* v;           // Krylov basis, (s+1)*3*S of TK2; v[0] = right-hand side b
+  double* gram_part; // kGramBlocks * 3 * nent
+  double* coef;      // 3 * kMaxS LSQ coefficients
+  double* obs_part;  // observables partial sums
+  double* obs_out;   // 12 doubles (6 hi/lo pairs reduced)
+  DevStatus* status;
+};
+
+// Host launchers (mb4_kernels.cu).  TK = float (mixed) or double (fp64).
+void launch_step_begin(const DevBuffers& b, cudaStream_t st);
+template <typename TK> void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+template <typename TK> void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first,
+                                            cudaStream_t st);
+template <typename TK> void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// the three parts of launch_krylov, for profiling
+template <typename TK> void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+template <typename TK> void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+void launch_lsq(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+template <typename TK> void launch_update(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+void launch_newton_check(const StepParams& p, const DevBuffers& b, unsigned long long cond_handle,
+                         int use_cond, cudaStream_t st);
+void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// Y_j = sum_n M[j][n] X_n on three complex planes of S sites.
+void launch_mix3(int S, const double2* X, double2* Y, const double M[3][3], cudaStream_t st);
+template <typename TK> void launch_copy_rhs_in(const StepParams& p, const DevBuffers& b, const double2* b3,
+                                               cudaStream_t st);
+template <typename TK> void launch_copy_solution_out(const StepParams& p, const DevBuffers& b,
+                                                     double2* x3, cudaStream_t st);
+template <typename TK> void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3,
+                                                cudaStream_t st);
+void launch_pack(const double* re, const double* im, double2* z, int n, cudaStream_t st);
+void launch_unpack(const double2* z, double* re, double* im, int n, cudaStream_t st);
+
+}  // namespace mb4

@@ -1,0 +1,318 @@
+"""Thin ctypes binding of libmb4 (include/mb4.h).
+
+Argument marshalling only: every step of the MB4 path runs in the library's
+CUDA kernels.  There is no CPU fallback; if libmb4.so has not been built, or
+no GPU is present, calls raise.
+
+Arrays may be numpy (host memory) or torch CUDA tensors (device memory,
+passed by pointer with on_device = 1).  Complex states are split into their
+real and imaginary parts, S = nx*ny doubles each, row-major (k = y*nx + x).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmb4.so")
+
+MB4_OK = 0
+MB4_ERR_INVALID_ARG = -1
+MB4_ERR_OUT_OF_MEMORY = -2
+MB4_ERR_CUDA = -3
+MB4_ERR_NEWTON_NOT_CONVERGED = -4
+MB4_ERR_KRYLOV_BREAKDOWN = -5
+MB4_ERR_NONFINITE = -6
+MB4_ERR_TIMEOUT = -7
+MB4_ERR_ADMISSION_REJECTED = -8
+
+MB4_FP64 = 0
+MB4_MIXED = 1
+MAX_KRYLOV_S = 10
+KERNEL_CLASSES = ("step_begin", "setup", "residual", "matvec", "gram", "lsq", "update", "check", "accept")
+
+# Every entry point include/mb4.h declares.
+EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", "mb4_get_state",
+           "mb4_get_stages", "mb4_step", "mb4_step_profiled", "mb4_energy", "mb4_norm", "mb4_observables", "mb4_residual",
+           "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version")
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("tx", C.c_double), ("ty", C.c_double),
+                ("onsite", C.c_double)]
+
+
+class Potential(C.Structure):
+    _fields_ = [("v", C.c_void_p), ("on_device", C.c_int)]
+
+
+class Nonlinearity(C.Structure):
+    _fields_ = [("chi", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("krylov_s", C.c_int),
+                ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+                ("stream", C.c_void_p), ("use_graph", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps_done", C.c_longlong), ("newton_iters_total", C.c_longlong),
+                ("newton_iters_last", C.c_int), ("last_update_inf", C.c_double), ("u0_inf", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MB4Error(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libmb4.so (built in-tree by paper_2003_04345_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_2003_04345_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        L.mb4_default_options.argtypes = [C.POINTER(Options)]
+        L.mb4_create.argtypes = [C.POINTER(Grid), C.POINTER(Potential), C.POINTER(Nonlinearity), C.c_double,
+                                 C.POINTER(Options), C.POINTER(_P)]
+        L.mb4_destroy.argtypes = [_P]
+        L.mb4_destroy.restype = None
+        L.mb4_set_state.argtypes = [_P, _P, _P, C.c_int]
+        L.mb4_get_state.argtypes = [_P, _P, _P, C.c_int]
+        L.mb4_get_stages.argtypes = [_P, _P, _P, C.c_int]
+        L.mb4_step.argtypes = [_P, C.c_int, C.POINTER(Stats)]
+        L.mb4_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), _D, C.POINTER(C.c_longlong)]
+        L.mb4_energy.argtypes = [_P, _D, _D]
+        L.mb4_norm.argtypes = [_P, _D]
+        L.mb4_observables.argtypes = [_P, _D]
+        L.mb4_residual.argtypes = [_P, _P, _P, _P, _P, _P, _P, C.c_int]
+        L.mb4_solve_shifted.argtypes = [_P, _P, _P, _P, _P, _P, _P, C.c_int]
+        L.mb4_constants.argtypes = [C.c_double, C.c_double, C.c_double, _D, _D, _D, _D, _D, _D]
+        L.mb4_status_string.argtypes = [C.c_int]
+        L.mb4_status_string.restype = C.c_char_p
+        L.mb4_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(code):
+    try:
+        return lib().mb4_status_string(int(code)).decode()
+    except Exception:  # the library itself failed to load
+        return "unknown"
+
+
+def _check(rc, what):
+    if rc != MB4_OK:
+        raise MB4Error(rc, what)
+
+
+def constants(alpha1=-712.5, c1=1.0 / 3.0, c2=2.0 / 3.0):
+    """The MB4 constants computed by the library on the host (no GPU needed)."""
+    E = np.zeros(12)
+    lam = np.zeros(3)
+    T = np.zeros(9)
+    Ti = np.zeros(9)
+    gx = np.zeros(6)
+    gw = np.zeros(6)
+    ptr = lambda a: a.ctypes.data_as(_D)
+    _check(lib().mb4_constants(alpha1, c1, c2, ptr(E), ptr(lam), ptr(T), ptr(Ti), ptr(gx), ptr(gw)),
+           "mb4_constants")
+    return {"E": E.reshape(3, 4), "lam": lam, "T": T.reshape(3, 3), "Tinv": Ti.reshape(3, 3),
+            "gauss_x": gx, "gauss_w": gw}
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class _Planar:
+    """Real/imag planes of a complex array as two contiguous float64 buffers.
+
+    numpy input -> host buffers; torch CUDA input -> device buffers."""
+
+    def __init__(self, z, n):
+        if _is_torch(z):
+            import torch
+            z = z.reshape(-1)
+            if z.numel() != n:
+                raise ValueError(f"expected {n} complex values, got {z.numel()}")
+            if z.is_complex():
+                self.re = z.real.to(torch.float64).contiguous()
+                self.im = z.imag.to(torch.float64).contiguous()
+            else:
+                raise ValueError("expected a complex tensor")
+            if not self.re.is_cuda:
+                raise ValueError("torch tensors must be on the GPU; pass numpy arrays for host memory")
+            self.on_device = 1
+            self.pre, self.pim = self.re.data_ptr(), self.im.data_ptr()
+        else:
+            z = np.asarray(z).reshape(-1)
+            if z.size != n:
+                raise ValueError(f"expected {n} complex values, got {z.size}")
+            self.re = np.ascontiguousarray(z.real, dtype=np.float64)
+            self.im = np.ascontiguousarray(z.imag, dtype=np.float64)
+            self.on_device = 0
+            self.pre, self.pim = self.re.ctypes.data, self.im.ctypes.data
+
+
+class Integrator:
+    """One MB4 context (mb4_create ... mb4_destroy)."""
+
+    def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", krylov_s=0,
+                 newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0, c2=2.0 / 3.0,
+                 stream=None, use_graph=True):
+        L = lib()
+        self.nx, self.ny = int(nx), int(ny)
+        self.S = self.nx * self.ny
+        self.h = float(h)
+        self._ctx = _P()
+        grid = Grid(self.nx, self.ny, float(tx), float(tx if ty is None else ty), float(onsite))
+        if _is_torch(V):
+            Vd = V.reshape(-1).to(dtype=__import__("torch").float64).contiguous()
+            if Vd.numel() != self.S or not Vd.is_cuda:
+                raise ValueError("V must hold nx*ny values on the GPU (or be a numpy array)")
+            pot = Potential(Vd.data_ptr(), 1)
+            keep = Vd
+        else:
+            Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+            if Vh.size != self.S:
+                raise ValueError("V must hold nx*ny values")
+            pot = Potential(Vh.ctypes.data, 0)
+            keep = Vh
+        opt = Options()
+        L.mb4_default_options(C.byref(opt))
+        opt.newton_rtol = float(newton_rtol)
+        opt.newton_max = int(newton_max)
+        opt.krylov_s = int(krylov_s)
+        opt.precision = {"fp64": MB4_FP64, "mixed": MB4_MIXED}[precision] if isinstance(precision, str) \
+            else int(precision)
+        opt.alpha1 = float(alpha1)
+        opt.c1, opt.c2 = float(c1), float(c2)
+        opt.use_graph = 1 if use_graph else 0
+        if stream is not None:
+            opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.precision = precision
+        _check(L.mb4_create(C.byref(grid), C.byref(pot), C.byref(Nonlinearity(float(chi))), self.h,
+                            C.byref(opt), C.byref(self._ctx)), "mb4_create")
+        del keep
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().mb4_destroy(self._ctx)
+            self._ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- state -----------------------------------------------------------
+    def set_state(self, psi):
+        p = _Planar(psi, self.S)
+        _check(lib().mb4_set_state(self._ctx, p.pre, p.pim, p.on_device), "mb4_set_state")
+
+    def get_state(self):
+        re = np.empty(self.S)
+        im = np.empty(self.S)
+        _check(lib().mb4_get_state(self._ctx, re.ctypes.data, im.ctypes.data, 0), "mb4_get_state")
+        return re + 1j * im
+
+    def get_state_device(self, re, im):
+        """Copy the state into two caller-owned float64 CUDA tensors of S elements."""
+        _check(lib().mb4_get_state(self._ctx, re.data_ptr(), im.data_ptr(), 1), "mb4_get_state")
+
+    def stages(self):
+        re = np.empty(3 * self.S)
+        im = np.empty(3 * self.S)
+        _check(lib().mb4_get_stages(self._ctx, re.ctypes.data, im.ctypes.data, 0), "mb4_get_stages")
+        return (re + 1j * im).reshape(3, self.S)
+
+    # -- stepping --------------------------------------------------------
+    def step(self, nsteps=1, check=True):
+        st = Stats()
+        rc = lib().mb4_step(self._ctx, int(nsteps), C.byref(st))
+        if check:
+            _check(rc, "mb4_step")
+        return (st.as_dict(), rc) if not check else st.as_dict()
+
+    def step_profiled(self, nsteps=1):
+        """Host-driven steps with CUDA events around every kernel: returns
+        (stats, {kernel class: (total ms, launches)})."""
+        st = Stats()
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = (C.c_longlong * len(KERNEL_CLASSES))()
+        _check(lib().mb4_step_profiled(self._ctx, int(nsteps), C.byref(st), ms.ctypes.data_as(_D), n),
+               "mb4_step_profiled")
+        return st.as_dict(), {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def set_state_ptr(self, re_ptr, im_ptr, on_device):
+        """Set the state from raw pointers (host pinned or device), S doubles each."""
+        _check(lib().mb4_set_state(self._ctx, re_ptr, im_ptr, int(on_device)), "mb4_set_state")
+
+    def get_state_ptr(self, re_ptr, im_ptr, on_device):
+        _check(lib().mb4_get_state(self._ctx, re_ptr, im_ptr, int(on_device)), "mb4_get_state")
+
+    # -- observables -----------------------------------------------------
+    def observables(self):
+        out = np.zeros(6)
+        _check(lib().mb4_observables(self._ctx, out.ctypes.data_as(_D)), "mb4_observables")
+        return {"H": out[0], "U_K": out[1], "U_E": out[2], "U_nl": out[3], "norm2": out[4],
+                "participation": out[5]}
+
+    def energy(self):
+        H = C.c_double()
+        parts = np.zeros(3)
+        _check(lib().mb4_energy(self._ctx, C.byref(H), parts.ctypes.data_as(_D)), "mb4_energy")
+        return H.value, parts
+
+    def norm2(self):
+        n = C.c_double()
+        _check(lib().mb4_norm(self._ctx, C.byref(n)), "mb4_norm")
+        return n.value
+
+    # -- kernels on their own (testing) ------------------------------------
+    def residual(self, u0, U):
+        a = _Planar(u0, self.S)
+        b = _Planar(np.asarray(U), 3 * self.S)
+        re = np.empty(3 * self.S)
+        im = np.empty(3 * self.S)
+        _check(lib().mb4_residual(self._ctx, a.pre, a.pim, b.pre, b.pim, re.ctypes.data, im.ctypes.data, 0),
+               "mb4_residual")
+        return (re + 1j * im).reshape(3, self.S)
+
+    def solve_shifted(self, u0, rhs):
+        a = _Planar(u0, self.S)
+        b = _Planar(np.asarray(rhs), 3 * self.S)
+        re = np.empty(3 * self.S)
+        im = np.empty(3 * self.S)
+        _check(lib().mb4_solve_shifted(self._ctx, a.pre, a.pim, b.pre, b.pim, re.ctypes.data, im.ctypes.data,
+                                       0), "mb4_solve_shifted")
+        return (re + 1j * im).reshape(3, self.S)
+
+
+def from_workload(w, precision="fp64", **kw):
+    """An Integrator for an inputs.Workload, with its potential and wavepacket set."""
+    it = Integrator(w.nx, w.ny, w.potential(), w.chi, w.h, tx=w.tx, ty=w.ty, onsite=w.eps0,
+                    precision=precision, **kw)
+    it.set_state(w.psi0())
+    return it

@@ -1,0 +1,295 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: GPU vs oracle <= 1e-11 relative in u after the stated steps, and
+|dH/H| <= 1e-13 over a run, in both precision modes (FP32 inner solves do not
+move the root of the stage equations).  The residual kernel on its own is
+FP64 and must agree to rounding (1e-13 relative).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mb4_oracle as orc
+from paper_2003_04345_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module")
+def mb4():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2003_04345_gb300 import mb4 as m
+    m.lib()
+    return m
+
+
+def _rand_state(rng, S, scale=1.0):
+    return scale * (rng.normal(size=S) + 1j * rng.normal(size=S))
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def _rel2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------------------
+# Residual kernel alone.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(3, 3), (16, 16), (33, 17), (64, 40)])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_residual_kernel_matches_oracle(mb4, nx, ny, precision):
+    rng = np.random.default_rng(nx * 100 + ny)
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    V[rng.integers(0, S, 3)] += 20.0
+    chi, tx, ty, eps0, h = 1.3, 1.1, 0.8, 0.25, 0.01
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    u0 = _rand_state(rng, S, 0.3)
+    U = u0[None, :] + 0.05 * np.vstack([_rand_state(rng, S, 0.3) for _ in range(3)])
+    want = orc.residual(prob, u0, U, h)
+    with mb4.Integrator(nx, ny, V, chi, h, tx=tx, ty=ty, onsite=eps0, precision=precision) as it:
+        got = it.residual(u0, U)
+    scale = np.max(np.abs(U))
+    assert np.max(np.abs(got - want)) <= 1e-13 * scale
+
+
+# ---------------------------------------------------------------------------
+# Shifted solves alone: (I - h lam_i J) x_i = b_i to the accuracy of one cycle.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,eta", [("fp64", 1e-7), ("mixed", 3e-5)])
+def test_shifted_solves_reduce_residual(mb4, precision, eta):
+    w = inputs.grid16_fp64()
+    S = w.S
+    V = w.potential()
+    rng = np.random.default_rng(3)
+    u0 = w.psi0()
+    b = np.vstack([_rand_state(rng, S) for _ in range(3)])
+    prob = orc.Problem(w.nx, w.ny, V, w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
+    J = orc.jacobian_real(prob, u0)
+    lam = mb4.constants()["lam"]
+    with mb4.Integrator(w.nx, w.ny, V, w.chi, w.h, precision=precision) as it:
+        x = it.solve_shifted(u0, b)
+    for i in range(3):
+        xr = orc.to_real(x[i])
+        br = orc.to_real(b[i])
+        res = br - (xr - w.h * lam[i] * (J @ xr))
+        assert np.linalg.norm(res) <= eta * np.linalg.norm(br), (i, np.linalg.norm(res) / np.linalg.norm(br))
+
+
+# ---------------------------------------------------------------------------
+# Whole steps.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def grid16_oracle_run():
+    w = inputs.grid16_fp64()
+    prob = orc.Problem(w.nx, w.ny, w.potential(), w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
+    u = w.psi0()
+    H0 = orc.energy(prob, u)[0]
+    traj = [u]
+    for _ in range(w.steps):
+        u = orc.step(prob, u, w.h)
+        traj.append(u)
+    return w, prob, traj, H0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_grid16_trajectory_matches_oracle(mb4, grid16_oracle_run, precision):
+    """16x16 wavepacket workload, 100 steps: <= 1e-11 relative in u at every 10th step."""
+    w, prob, traj, H0 = grid16_oracle_run
+    with mb4.from_workload(w, precision=precision) as it:
+        drift = 0.0
+        for n in range(10, w.steps + 1, 10):
+            it.step(10)
+            u = it.get_state()
+            assert _rel(u, traj[n]) <= 1e-11, (n, _rel(u, traj[n]))
+            assert _rel2(u, traj[n]) <= 1e-11
+            H = it.energy()[0]
+            drift = max(drift, abs(H - H0) / abs(H0))
+        assert drift <= 1e-13, drift
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_stages_match_oracle(mb4, precision):
+    rng = np.random.default_rng(21)
+    nx, ny = 33, 17
+    S = nx * ny
+    V = rng.uniform(-0.5, 0.5, S)
+    V[[5, 100, 400]] = 20.0
+    prob = orc.Problem(nx, ny, V, 1.0)
+    u0 = inputs.wavepacket(nx, ny, 3.0, math.pi / 4, 0.3)
+    u1, U, _ = orc.step(prob, u0, 0.01, return_stages=True)
+    with mb4.Integrator(nx, ny, V, 1.0, 0.01, precision=precision) as it:
+        it.set_state(u0)
+        it.step(1)
+        Ug = it.stages()
+        ug = it.get_state()
+    assert _rel(Ug, U) <= 1e-12
+    assert _rel(ug, u1) <= 1e-12
+    assert np.array_equal(ug, Ug[2]) or _rel(ug, Ug[2]) <= 1e-15
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (5, 7), (40, 24)])
+def test_small_and_ragged_grids_match_oracle(mb4, nx, ny):
+    rng = np.random.default_rng(nx + 7 * ny)
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    chi, tx, ty, eps0, h = 0.8, 1.2, 0.7, 0.3, 0.02
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    u0 = _rand_state(rng, S, 0.5)
+    u = u0
+    for _ in range(5):
+        u = orc.step(prob, u, h)
+    for precision in PRECISIONS:
+        with mb4.Integrator(nx, ny, V, chi, h, tx=tx, ty=ty, onsite=eps0, precision=precision) as it:
+            it.set_state(u0)
+            it.step(5)
+            assert _rel(it.get_state(), u) <= 1e-11
+
+
+def test_observables_match_oracle(mb4):
+    rng = np.random.default_rng(8)
+    nx, ny = 48, 20
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    prob = orc.Problem(nx, ny, V, 1.7, tx=1.1, ty=0.9, eps0=0.2)
+    u = _rand_state(rng, S, 0.1)
+    with mb4.Integrator(nx, ny, V, 1.7, 0.01, tx=1.1, ty=0.9, onsite=0.2) as it:
+        it.set_state(u)
+        o = it.observables()
+    H, UK, UE, UI = orc.energy(prob, u)
+    for got, want in ((o["H"], H), (o["U_K"], UK), (o["U_E"], UE), (o["U_nl"], UI),
+                      (o["norm2"], orc.norm2(u)), (o["participation"], orc.participation(u))):
+        assert abs(got - want) <= 2e-15 * max(abs(want), 1e-300) + 1e-18, (got, want)
+
+
+# ---------------------------------------------------------------------------
+# Control flow, determinism, checkpoint/resume, failure detection.
+# ---------------------------------------------------------------------------
+def test_graph_and_host_loop_agree_bitwise(mb4):
+    w = inputs.grid16_fp64()
+    out = []
+    for g in (True, False):
+        with mb4.from_workload(w, use_graph=g) as it:
+            st = it.step(10)
+            out.append((it.get_state(), st["newton_iters_total"]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_deterministic_and_resumable(mb4, precision):
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w, precision=precision) as a:
+        a.step(20)
+        ua = a.get_state()
+    with mb4.from_workload(w, precision=precision) as b:
+        b.step(20)
+        ub = b.get_state()
+    assert np.array_equal(ua, ub)
+    with mb4.from_workload(w, precision=precision) as c:
+        c.step(10)
+        mid = c.get_state()
+    with mb4.Integrator(w.nx, w.ny, w.potential(), w.chi, w.h, precision=precision) as d:
+        d.set_state(mid)
+        d.step(10)
+        assert np.array_equal(d.get_state(), ua)
+
+
+def test_time_reversal_on_gpu(mb4):
+    w = inputs.grid16_fp64()
+    V = w.potential()
+    with mb4.from_workload(w) as f, mb4.Integrator(w.nx, w.ny, V, w.chi, -w.h) as b:
+        u0 = f.get_state()
+        f.step(5)
+        b.set_state(f.get_state())
+        b.step(5)
+        assert _rel(b.get_state(), u0) <= 1e-13
+
+
+def test_newton_failure_keeps_last_state(mb4):
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w, newton_max=1) as it:
+        u0 = it.get_state()
+        st, rc = it.step(3, check=False)
+        assert rc == mb4.MB4_ERR_NEWTON_NOT_CONVERGED
+        assert st["steps_done"] == 0
+        assert np.array_equal(it.get_state(), u0)
+
+
+def test_nonfinite_state_is_reported(mb4):
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w) as it:
+        psi = w.psi0()
+        psi[17] = np.nan
+        it.set_state(psi)
+        st, rc = it.step(2, check=False)
+        assert rc == mb4.MB4_ERR_NONFINITE
+        assert st["steps_done"] == 0
+        after = it.get_state()
+        assert np.isnan(after[17]) and np.array_equal(np.delete(after, 17), np.delete(psi, 17))
+
+
+def test_invalid_arguments_rejected(mb4):
+    for kw in ({"nx": 2, "ny": 8}, {"h": 0.0}, {"krylov_s": 11}, {"precision": 7}):
+        args = {"nx": 4, "ny": 4, "h": 0.01}
+        args.update(kw)
+        nx, ny = args.pop("nx"), args.pop("ny")
+        with pytest.raises((mb4.MB4Error, ValueError, KeyError)):
+            mb4.Integrator(nx, ny, np.zeros(nx * ny), 1.0, **args)
+
+
+# ---------------------------------------------------------------------------
+# Full size (the benchmark's configuration): checks the oracle can make one site
+# at a time, and properties that hold at any size.
+# ---------------------------------------------------------------------------
+def _sample_sites(w, n, seed):
+    rng = np.random.default_rng(seed)
+    edges = [0, w.nx - 1, w.S - w.nx, w.S - 1, w.nx * (w.ny // 2)]
+    V = w.potential()
+    defects = list(np.nonzero(V > 10)[0][:8])
+    return np.unique(np.concatenate([edges, defects, rng.integers(0, w.S, n)]))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_grid512_stages_solve_oracle_stage_equations(mb4, precision):
+    """512x512, bench configuration: after each of 3 steps the converged stages
+    satisfy the oracle's Phi(U) = 0 at sampled sites to the Newton tolerance."""
+    w = inputs.grid512_fp64()
+    V = w.potential()
+    with mb4.from_workload(w, precision=precision) as it:
+        u0 = it.get_state()
+        H0 = it.energy()[0]
+        for n in range(3):
+            st = it.step(1)
+            U = it.stages()
+            sites = _sample_sites(w, 300, n)
+            phi = orc.residual_at_sites(w.nx, w.ny, V, w.chi, w.tx, w.ty, w.eps0, u0, U, w.h, sites)
+            assert np.max(np.abs(phi)) <= 1e-13 * np.max(np.abs(u0)), np.max(np.abs(phi))
+            u0 = it.get_state()
+            assert np.array_equal(u0, U[2]) or _rel(u0, U[2]) < 1e-15
+        H = it.energy()[0]
+        assert abs(H - H0) <= 1e-13 * abs(H0)
+
+
+def test_grid512_translation_equivariance(mb4):
+    w = inputs.grid512_fp64()
+    V = w.potential().reshape(w.ny, w.nx)
+    psi = w.psi0().reshape(w.ny, w.nx)
+    roll = lambda a: np.roll(np.roll(a, 37, axis=1), -101, axis=0)
+    with mb4.Integrator(w.nx, w.ny, V.ravel(), w.chi, w.h) as a, \
+            mb4.Integrator(w.nx, w.ny, roll(V).ravel(), w.chi, w.h) as b:
+        a.set_state(psi.ravel())
+        b.set_state(roll(psi).ravel())
+        a.step(3)
+        b.step(3)
+        ua = a.get_state().reshape(w.ny, w.nx)
+        ub = b.get_state().reshape(w.ny, w.nx)
+    assert _rel(ub, roll(ua)) <= 1e-13

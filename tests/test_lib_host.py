@@ -1,0 +1,87 @@
+"""Host-side checks of libmb4 that need no GPU: the library loads, exports every
+entry point include/mb4.h declares, computes the MB4 constants correctly on the
+host, and fails loudly (no CPU fallback) when no GPU is present."""
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import mb4_oracle as orc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mb4():
+    from paper_2003_04345_gb300 import build, mb4 as m
+    if not os.path.exists(m.LIB_PATH):
+        build.build()
+    return m
+
+
+def _declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mb4_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(mb4):
+    L = mb4.lib()
+    declared = _declared_entry_points()
+    assert declared, "no entry points found in include/"
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(mb4.EXPORTS) <= declared
+
+
+def test_library_constants_match_exact_ones(mb4):
+    k = mb4.constants()
+    E_exact, _ = orc.constants_f64()
+    assert np.max(np.abs(k["E"] - E_exact)) < 4e-15 * np.max(np.abs(E_exact))
+    lam_oracle = np.sort(np.linalg.eigvals(E_exact[:, 1:]).real)
+    assert np.max(np.abs(k["lam"] - lam_oracle)) < 1e-14
+    assert np.all(np.diff(k["lam"]) > 0)
+    T, Ti = k["T"], k["Tinv"]
+    assert np.max(np.abs(T @ Ti - np.eye(3))) < 1e-14
+    assert np.max(np.abs(T @ np.diag(k["lam"]) @ Ti - E_exact[:, 1:])) < 1e-13
+    assert np.allclose(np.linalg.norm(T, axis=0), 1.0, atol=1e-15)
+
+
+def test_library_gauss_rule_is_exact_to_degree_11(mb4):
+    k = mb4.constants()
+    x, w = k["gauss_x"], k["gauss_w"]
+    for deg in range(12):
+        assert abs(np.sum(w * x ** deg) - 1.0 / (deg + 1)) < 2e-16 * 8
+    assert abs(np.sum(w * x ** 12) - 1.0 / 13) > 1e-8   # and not beyond (6 nodes)
+
+
+def test_library_constants_other_nodes(mb4):
+    k = mb4.constants(-712.5, 0.25, 0.5)
+    E_exact, _ = orc.constants_f64(Fraction(-5700, 8), (Fraction(1, 4), Fraction(1, 2), Fraction(1)))
+    assert np.max(np.abs(k["E"] - E_exact)) < 4e-15 * np.max(np.abs(E_exact))
+
+
+def test_library_rejects_alpha_above_bound(mb4):
+    with pytest.raises(mb4.MB4Error) as e:
+        mb4.constants(-200.0)
+    assert e.value.code == mb4.MB4_ERR_INVALID_ARG
+
+
+def test_create_fails_loudly_without_gpu(mb4):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(mb4.MB4Error) as e:
+        mb4.Integrator(4, 4, np.zeros(16), 1.0, 0.01)
+    assert e.value.code == mb4.MB4_ERR_CUDA
+
+
+def test_status_strings(mb4):
+    assert mb4.status_string(0) == "ok"
+    assert "Newton" in mb4.status_string(mb4.MB4_ERR_NEWTON_NOT_CONVERGED)

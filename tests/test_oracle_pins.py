@@ -397,3 +397,16 @@ def test_jacobian_matches_finite_difference():
         e[k] = d
         Jfd[:, k] = (freal(x0 + e) - freal(x0 - e)) / (2 * d)
     assert np.max(np.abs(J - Jfd)) < 1e-7 * max(1.0, np.max(np.abs(J)))
+
+
+def test_oracle_linear_solvers_agree():
+    """The oracle's two Newton linear solvers (sparse LU, GMRES on the coupled
+    matrix) reach the same root of Phi(U) = 0."""
+    w = inputs.grid512_fp64()
+    n = 24
+    V = inputs.potential(n, n, 1.0, 6, 20.0, 3)
+    prob = orc.Problem(n, n, V, 1.0)
+    u0 = inputs.wavepacket(n, n, 3.0, math.pi / 4, 0.0)
+    ul, _ = orc.run(prob, u0, w.h, 3, solver="lu")
+    ug, _ = orc.run(prob, u0, w.h, 3, solver="gmres")
+    assert np.max(np.abs(ul - ug)) <= 1e-15 * np.max(np.abs(ul))
