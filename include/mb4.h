@@ -87,13 +87,21 @@ typedef struct {
     int    newton_max;   /* Newton iteration cap per step, then MB4_ERR_NEWTON_NOT_CONVERGED;
                             default 30                                                          */
     int    krylov_s;     /* Krylov subspace dimension of the one s-step GMRES cycle per Newton
-                            iteration, 1..MB4_MAX_KRYLOV_S; 0 = default (8 FP64, 6 mixed)      */
+                            iteration, 1..MB4_MAX_KRYLOV_S; 0 = default: 4, or 5 when
+                            newton_predict > 0                                                  */
     int    precision;    /* MB4_FP64 or MB4_MIXED; default MB4_FP64                            */
     double alpha1;       /* eq. (Adefinition); must be < -300*0.7770503941; default -712.5    */
     double c1, c2;       /* interior Lagrange nodes, 0 < c1 < c2 < 1; c3 = 1; default 1/3, 2/3 */
     void*  stream;       /* cudaStream_t to run on; NULL = the legacy default stream            */
     int    use_graph;    /* 1 (default): each step is one CUDA-graph launch whose Newton loop is
                             a device-side conditional WHILE node; 0: host-driven Newton loop    */
+    double newton_predict; /* 0 (default): only the test above.  > 0: also stop after iteration
+                            l >= 1 when the predicted remaining error theta/(1-theta)*||r^l||_inf,
+                            theta = ||r^l||/||r^(l-1)|| < 1, is <= newton_predict*||u0||_inf
+                            (Hairer-Wanner's stopping test for simplified Newton, Solving ODEs II
+                            Sec. IV.8); the iterate is then accurate to that bound, so a value at
+                            the rounding level (1e-16) skips only an iteration that changes U by
+                            less than rounding                                                */
 } mb4_options;
 
 #define MB4_MAX_KRYLOV_S 10
@@ -104,6 +112,7 @@ typedef struct {
     int       newton_iters_last;  /* Newton iterations of the last step attempted              */
     double    last_update_inf;    /* ||r^l||_inf of the last Newton iteration                  */
     double    u0_inf;             /* ||u0||_inf of the last step attempted                     */
+    double    update_hist[8];     /* ||r^l||_inf, l = 0..7, of the last step attempted (0 if not run) */
 } mb4_stats;
 
 /* Fill *opt with the defaults listed above.  Never fails for a non-NULL pointer. */
@@ -137,16 +146,13 @@ int mb4_get_stages(const mb4_ctx* ctx, double* re3, double* im3, int on_device);
 int mb4_step(mb4_ctx* ctx, int nsteps, mb4_stats* stats);
 
 /* Kernel classes reported by mb4_step_profiled. */
-#define MB4_K_STEP_BEGIN   0
-#define MB4_K_SETUP        1   /* u0, (K+V)u0, J coefficients, first right-hand side          */
-#define MB4_K_RESIDUAL     2   /* stage residual Phi (FP64)                                    */
-#define MB4_K_MATVEC       3   /* Krylov basis v_{a+1} = (J/theta) v_a, three systems         */
-#define MB4_K_GRAM         4   /* Gram matrix partial sums                                     */
-#define MB4_K_LSQ          5   /* Gram reduction + least squares                               */
-#define MB4_K_UPDATE       6   /* Newton update Ubar += rbar, ||r||_inf                         */
-#define MB4_K_CHECK        7   /* Newton loop test                                             */
-#define MB4_K_ACCEPT       8   /* u1 = U_c3                                                    */
-#define MB4_K_COUNT        9
+#define MB4_K_SETUP        0   /* u0, (K+V)u0, J coefficients, first right-hand side          */
+#define MB4_K_RESIDUAL     1   /* stage residual Phi (FP64)                                    */
+#define MB4_K_MATVEC       2   /* Krylov basis v_{a+1} = (J/theta) v_a, three systems         */
+#define MB4_K_GRAM         3   /* Gram matrix, its fixed-order reduction and least squares     */
+#define MB4_K_UPDATE       4   /* Newton update Ubar += rbar, ||r||_inf, Newton loop test      */
+#define MB4_K_ACCEPT       5   /* u1 = U_c3                                                    */
+#define MB4_K_COUNT        6
 
 /* mb4_step with a host-driven Newton loop and a CUDA event pair around every
  * kernel launch, for profiling.  Same arithmetic and results as mb4_step (bit

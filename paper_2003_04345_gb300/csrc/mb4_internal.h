@@ -12,7 +12,8 @@ namespace mb4 {
 
 constexpr int kGauss = 6;          // Gauss-Legendre nodes: exact for the degree-11 integrand of eq. (fIu2)
 constexpr int kMaxS = MB4_MAX_KRYLOV_S;
-constexpr int kGramBlocks = 304;   // blocks of the Gram reduction (2 per SM on 152 SMs)
+constexpr int kGramBlocks = 304;   // upper bound on the Gram blocks per shifted system
+constexpr int kGramCap = 96;       // Gram blocks per system actually used (at most)
 
 // MB4 constants in FP64, computed on the host (mb4_consts.cpp).
 struct Constants {
@@ -34,6 +35,8 @@ int compute_constants(double alpha1, double c1, double c2, Constants* out);
 struct StepParams {
   int nx, ny, S;
   int s;                   // Krylov subspace dimension
+  int gram_blocks;         // Gram blocks per shifted system (one wave over all SMs)
+  int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   double tx, ty, eps0, chi, h;
   // residual in the eigenbasis of E: Ubar = Tinv U
   double hlam[3];          // h * lambda_i
@@ -48,8 +51,15 @@ struct StepParams {
   double inv_theta;        // 1 / theta
   double sig[3];           // h lambda_i theta
   double newton_rtol;
+  double newton_predict;   // 0: off; else Hairer-Wanner predicted-error stop
   int newton_max;
   float trunc_rel;         // relative pivot threshold of the Gram Cholesky
+  double chi_theta;        // chi / theta
+  // FP32 copies of uniform constants (no per-thread conversions on the FP64 pipe)
+  float fT[3][3];          // T
+  float f_inv_theta, f_chi_theta, f_chi;
+  float f_hTc[3];
+  float f_txt, f_tyt;      // tx / theta, ty / theta
 };
 
 // Device-resident control block of one context.
@@ -61,10 +71,14 @@ struct DevStatus {
   long long steps_done;              // accepted steps since the last reset
   long long newton_total;
   unsigned long long rmax_bits;      // max |r| of the current iteration (double bits, >= 0)
-  unsigned long long u0max_bits;     // ||u0||_inf of the current step (double bits)
+  unsigned int u0max_bits;           // ||u0||_inf of the current step (float bits, >= 0)
   double last_rmax;
   double last_u0max;
   int cont;                          // 1 while the Newton loop of the current step goes on
+  unsigned int ticket_gram;          // last-block tickets (reset by the last block)
+  unsigned int ticket_update;
+  double prev_rmax;                  // ||r^(l-1)||_inf
+  double hist[8];                    // ||r^l||_inf of the current step
 };
 
 // Device buffers of one context.
@@ -76,7 +90,7 @@ struct DevBuffers {
   double2* Ubar;     // transformed stages, 3*S
   void* jc;          // J coefficients {e1, e2, a, 0} (TK4), S
   void* v;           // Krylov basis, (s+1)*3*S of TK2; v[0] = right-hand side b
-  double* gram_part; // kGramBlocks * 3 * nent
+  double* gram_part; // 3 * kGramBlocks * nent
   double* coef;      // 3 * kMaxS LSQ coefficients
   double* obs_part;  // observables partial sums
   double* obs_out;   // 12 doubles (6 hi/lo pairs reduced)
@@ -84,18 +98,20 @@ struct DevBuffers {
 };
 
 // Host launchers (mb4_kernels.cu).  TK = float (mixed) or double (fp64).
-void launch_step_begin(const DevBuffers& b, cudaStream_t st);
 template <typename TK> void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 template <typename TK> void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first,
                                             cudaStream_t st);
 template <typename TK> void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t st);
-// the three parts of launch_krylov, for profiling
+// the two parts of launch_krylov, for profiling
 template <typename TK> void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 template <typename TK> void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t st);
-void launch_lsq(const StepParams& p, const DevBuffers& b, cudaStream_t st);
-template <typename TK> void launch_update(const StepParams& p, const DevBuffers& b, cudaStream_t st);
-void launch_newton_check(const StepParams& p, const DevBuffers& b, unsigned long long cond_handle,
-                         int use_cond, cudaStream_t st);
+// Raise the dynamic shared-memory limit of the matrix-powers kernels (once per process/device).
+int prepare_powers();
+// Blocks per system that make the Gram kernel a single wave on this device (0 on error).
+template <typename TK> int gram_blocks_per_system(int s_dim);
+// Newton update and loop test; cond_handle drives the graph's WHILE node when use_cond.
+template <typename TK> void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long cond_handle,
+                                          int use_cond, cudaStream_t st);
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 // Y_j = sum_n M[j][n] X_n on three complex planes of S sites.

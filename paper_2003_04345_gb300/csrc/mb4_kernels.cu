@@ -46,33 +46,77 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// ---------------------------------------------------------------------------
-// Step control.
-// ---------------------------------------------------------------------------
-__global__ void k_step_begin(DevStatus* st) {
-  if (st->error) return;
-  st->newton_iter = 0;
-  st->nonfinite = 0;
-  st->rmax_bits = 0ull;
-  st->u0max_bits = 0ull;
+// Float <-> double conversions on the integer pipe.  On this GPU the FP64 pipe
+// is the scarce unit (about 1/59 of the FP32 rate) and a hardware conversion
+// occupies it like several FP64 FMAs, so the kernels move values between the
+// FP64 state and the FP32 Krylov solve by rearranging IEEE-754 bit fields.
+//  - f2d_bits: exact for zero, normal floats, +-inf and NaN; FP32 subnormals
+//    (below 1.2e-38) become +-0.
+//  - d2f_trunc: rounds toward zero (relative error below 2^-23), which is
+//    harmless for values that only feed the FP32 solve; magnitudes below the
+//    FP32 normal range become +-0, above it +-inf; NaN stays NaN.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned int m = u & 0x7fffffu;
+  unsigned int hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned int lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 255u) { hi = sign | 0x7ff00000u | (m ? 0x80000u : 0u); lo = 0u; }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
-void launch_step_begin(const DevBuffers& b, cudaStream_t s) { k_step_begin<<<1, 1, 0, s>>>(b.status); }
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  unsigned int r = sign | ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e <= 0) r = sign;
+  if (e >= 255) r = sign | 0x7f800000u;
+  if ((hi & 0x7ff00000u) == 0x7ff00000u && ((hi & 0xfffffu) | lo)) r = 0x7fc00000u;
+  return __uint_as_float(r);
+}
 
-// Algorithm 1, lines 7-9 and the first residual: u0 = u(t); J at u0 (stored as
-// per-site coefficients); Ubar^0 = T^-1 (e3 (x) u0) = tau (x) u0.  At U^0 = e3 (x) u0
-// every stage polynomial value equals u0, so Phi_i(U^0) = -h c_i f(u0) and
-// b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].  Also (K+V) u0 and ||u0||_inf.
+// |x| of a double as a float (integer pipe, truncating): for max-norms.
+__device__ __forceinline__ float absf_of(double x) {
+  return d2f_trunc(__hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x)));
+}
+
+// A uniform constant in the Krylov precision: the host-made FP32 copy, or the FP64 value.
+template <typename T> __device__ __forceinline__ T kval(double d, float f);
+template <> __device__ __forceinline__ float kval<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double kval<double>(double d, float) { return d; }
+
+template <typename T> __device__ __forceinline__ T from_double(double x);
+template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_trunc(x); }
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <typename T> __device__ __forceinline__ double to_double(T x);
+template <> __device__ __forceinline__ double to_double<float>(float x) { return f2d_bits(x); }
+template <> __device__ __forceinline__ double to_double<double>(double x) { return x; }
+template <typename T> __device__ __forceinline__ float to_float(T x);
+template <> __device__ __forceinline__ float to_float<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_float<double>(double x) { return d2f_trunc(x); }
+
+// ---------------------------------------------------------------------------
+// Step set-up (Algorithm 1 lines 7-9 and the first residual): u0 = u(t); J at u0
+// as per-site coefficients; (K+V) u0; ||u0||_inf.  At U^0 = e3 (x) u0 every stage
+// polynomial value equals u0, so Phi_i(U^0) = -h c_i f(u0) and the first
+// right-hand side is b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].
+// J and b^0 only feed the Krylov solve, so they are formed in its precision TK;
+// (K+V) u0 is reused by every residual and stays FP64.  Ubar^0 = tau (x) u0 is
+// formed by the first update.
+// ---------------------------------------------------------------------------
 template <typename TK>
 __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
-                                               double2* __restrict__ Ubar, JCoef<TK>* __restrict__ jc,
+                                               JCoef<TK>* __restrict__ jc,
                                                typename Vec2<TK>::type* __restrict__ v0, DevStatus* st) {
   if (st->error) return;
   typedef typename Vec2<TK>::type TK2;
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  double m = 0.0;
+  float m = 0.f;
   if (k < S) {
     Nbr n = neighbours(k, p.nx, p.ny, S);
     double2 c = u[k];
@@ -82,34 +126,37 @@ __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __re
     s0.x = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
     s0.y = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
     S0[k] = s0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Ubar[(size_t)i * S + k] = make_double2(p.tau[i] * c.x, p.tau[i] * c.y);
-    double pp = c.x * c.x, qq = c.y * c.y, nn = pp + qq;
+    const TK pk = from_double<TK>(c.x), qk = from_double<TK>(c.y);
+    const TK pp = pk * pk, qq = qk * qk, nn = pp + qq;
+    const TK dt = from_double<TK>(d) * kval<TK>(p.inv_theta, p.f_inv_theta);
+    const TK ct = kval<TK>(p.chi_theta, p.f_chi_theta);
     JCoef<TK> j;
-    j.e1 = (TK)((d + p.chi * (pp + 3.0 * qq)) * p.inv_theta);
-    j.e2 = (TK)((d + p.chi * (3.0 * pp + qq)) * p.inv_theta);
-    j.a = (TK)(2.0 * p.chi * c.x * c.y * p.inv_theta);
+    j.e1 = dt + ct * (pp + (TK)3 * qq);
+    j.e2 = dt + ct * ((TK)3 * pp + qq);
+    j.a = (TK)2 * ct * pk * qk;
     j.pad = (TK)0;
     jc[k] = j;
-    double Fx = fma(p.chi * nn, c.x, s0.x), Fy = fma(p.chi * nn, c.y, s0.y);
+    const TK cn = kval<TK>(p.chi, p.f_chi) * nn;
+    const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       TK2 bi;
-      bi.x = (TK)(p.hTc[i] * Fy);
-      bi.y = (TK)(-p.hTc[i] * Fx);
+      const TK hc = kval<TK>(p.hTc[i], p.f_hTc[i]);
+      bi.x = hc * Fy;
+      bi.y = -hc * Fx;
       v0[(size_t)i * S + k] = bi;
     }
-    m = fmax(fabs(c.x), fabs(c.y));
+    m = fmaxf(absf_of(c.x), absf_of(c.y));
   }
   m = warp_max(m);
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&st->u0max_bits, dbits(m));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&st->u0max_bits, __float_as_uint(m));
 }
 
 template <typename TK>
 void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   int blocks = (p.S + 255) / 256;
-  k_setup<TK><<<blocks, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (JCoef<TK>*)b.jc,
-                                     (typename Vec2<TK>::type*)b.v, b.status);
+  k_setup<TK><<<blocks, 256, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
+                                     b.status);
 }
 
 // ---------------------------------------------------------------------------
@@ -136,12 +183,16 @@ __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* _
   const double2 u0 = u[k];
   const double2 s0 = S0[k];
   const double d = D[k];
-  double2 Ub[3], acc[3];
+  // dU_m = Ubar_m - tau_m u0: the departure of the stages from the trivial guess.
+  // The stage polynomial at node q is then X_q = u0 + sum_m (L T)_qm dU_m (since
+  // l_0(zeta) + sum_m (L T)_qm tau_m = 1), and b_i = -dU_i + i-rotated sums.
+  double2 dU[3], acc[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const double2* P = Ubar + (size_t)m * S;
     double2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-    Ub[m] = c;
+    dU[m].x = fma(-p.tau[m], u0.x, c.x);
+    dU[m].y = fma(-p.tau[m], u0.y, c.y);
     double sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
     double sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
     acc[m].x = fma(p.hlam[m], sx, p.he0[m] * s0.x);
@@ -149,14 +200,13 @@ __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* _
   }
 #pragma unroll
   for (int q = 0; q < kGauss; ++q) {
-    double Xx = p.L0[q] * u0.x, Xy = p.L0[q] * u0.y;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      Xx = fma(p.LT[q][m], Ub[m].x, Xx);
-      Xy = fma(p.LT[q][m], Ub[m].y, Xy);
-    }
-    double nn = fma(Xx, Xx, Xy * Xy);
-    double gx = nn * Xx, gy = nn * Xy;
+    double Xx = fma(p.LT[q][0], dU[0].x, u0.x), Xy = fma(p.LT[q][0], dU[0].y, u0.y);
+    Xx = fma(p.LT[q][1], dU[1].x, Xx);
+    Xy = fma(p.LT[q][1], dU[1].y, Xy);
+    Xx = fma(p.LT[q][2], dU[2].x, Xx);
+    Xy = fma(p.LT[q][2], dU[2].y, Xy);
+    const double nn = fma(Xx, Xx, Xy * Xy);
+    const double gx = nn * Xx, gy = nn * Xy;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       acc[i].x = fma(p.hchiW[i][q], gx, acc[i].x);
@@ -166,8 +216,8 @@ __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* _
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     TO2 o;
-    o.x = (TO)(fma(p.tau[i], u0.x, -Ub[i].x) + acc[i].y);
-    o.y = (TO)(fma(p.tau[i], u0.y, -Ub[i].y) - acc[i].x);
+    o.x = from_double<TO>(acc[i].y - dU[i].x);
+    o.y = from_double<TO>(-acc[i].x - dU[i].y);
     out[(size_t)i * S + k] = o;
   }
 }
@@ -203,7 +253,7 @@ __global__ void __launch_bounds__(256) k_matvec(StepParams p, const JCoef<TK>* _
   if (k >= S) return;
   Nbr n = neighbours(k, p.nx, p.ny, S);
   const JCoef<TK> j = jc[k];
-  const TK tx = (TK)(p.tx * p.inv_theta), ty = (TK)(p.ty * p.inv_theta);
+  const TK tx = kval<TK>(p.tx * p.inv_theta, p.f_txt), ty = kval<TK>(p.ty * p.inv_theta, p.f_tyt);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const TK2* P = vin + (size_t)i * S;
@@ -217,45 +267,102 @@ __global__ void __launch_bounds__(256) k_matvec(StepParams p, const JCoef<TK>* _
   }
 }
 
-// Exact-product double-float accumulation for the FP32 Gram matrix: the normal
-// equations square the condition number, so the Gram entries are summed to
-// about 2^-44 relative even though the basis vectors are FP32.
-struct DF { float hi, lo; };
+// Matrix powers on a tile (FP32 Krylov basis): one block builds v_1..v_SK on a
+// TX x TY tile from v_0 and the J coefficients loaded once, with an SK-wide
+// periodic halo in shared memory; level a is valid on the tile grown by SK - a,
+// so no block needs another block's result.  Replaces SK stencil launches by
+// one at the price of recomputing the shrinking halo (cheap in FP32).
+constexpr int kPowTX = 32, kPowTY = 16, kPowThreads = 256;
 
-__device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
-  float pr = __fmul_rn(a, b);
-  float pe = __fmaf_rn(a, b, -pr);
-  float t = __fadd_rn(s.hi, pr);
-  float bp = __fsub_rn(t, s.hi);
-  float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
-  s.hi = t;
-  s.lo = __fadd_rn(s.lo, __fadd_rn(err, pe));
+template <int SK>
+__host__ __device__ constexpr int pow_ext_x() { return kPowTX + 2 * SK; }
+template <int SK>
+__host__ __device__ constexpr int pow_ext_y() { return kPowTY + 2 * SK; }
+template <int SK>
+constexpr size_t pow_smem_bytes() {
+  return (size_t)pow_ext_x<SK>() * pow_ext_y<SK>() * (sizeof(float4) + 2 * 3 * sizeof(float2));
 }
 
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  float t = __fadd_rn(a.hi, b.hi);
-  float bp = __fsub_rn(t, a.hi);
-  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, bp)), __fsub_rn(b.hi, bp));
-  DF r;
-  r.hi = t;
-  r.lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
-  return r;
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
 }
 
+template <int SK>
+__global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const float4* __restrict__ jc,
+                                                        float2* __restrict__ v, const DevStatus* st) {
+  if (st->error) return;
+  constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* sj = reinterpret_cast<float4*>(smem_raw);
+  float2* buf0 = reinterpret_cast<float2*>(sj + EA);     // [3][EA]
+  float2* buf1 = buf0 + 3 * EA;                           // [3][EA]
+  const int S = p.S, nx = p.nx, ny = p.ny;
+  const int x0 = blockIdx.x * kPowTX - SK, y0 = blockIdx.y * kPowTY - SK;
+  const int tx0 = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // 32 x 8 thread layout
+  for (int ly = ty0; ly < EY; ly += kPowThreads / 32) {
+    const int grow = wrap(y0 + ly, ny) * nx;
+    for (int lx = tx0; lx < EX; lx += 32) {
+      const int t = ly * EX + lx;
+      const int g = grow + wrap(x0 + lx, nx);
+      sj[t] = jc[g];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) buf0[i * EA + t] = v[(size_t)i * S + g];
+    }
+  }
+  __syncthreads();
+  const float tx = p.f_txt, ty = p.f_tyt;
+  float2* src = buf0;
+  float2* dst = buf1;
+#pragma unroll 1
+  for (int a = 1; a <= SK; ++a) {
+    for (int ly = a + ty0; ly < EY - a; ly += kPowThreads / 32)
+    for (int lx = a + tx0; lx < EX - a; lx += 32) {
+      const int c = ly * EX + lx;
+      const float4 j = sj[c];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float2* P = src + i * EA;
+        const float2 cc = P[c], xa = P[c - 1], xb = P[c + 1], ya = P[c - EX], yb = P[c + EX];
+        float2 o;
+        o.x = j.z * cc.x + j.x * cc.y - tx * (xa.y + xb.y) - ty * (ya.y + yb.y);
+        o.y = -j.y * cc.x - j.z * cc.y + tx * (xa.x + xb.x) + ty * (ya.x + yb.x);
+        dst[i * EA + c] = o;
+      }
+    }
+    __syncthreads();
+    // interior of level a to global
+    for (int ly = ty0; ly < kPowTY; ly += kPowThreads / 32) {
+      const int lx = tx0;
+      const int gx = blockIdx.x * kPowTX + lx, gy = blockIdx.y * kPowTY + ly;
+      if (gx < nx && gy < ny) {
+        const int c = (ly + SK) * EX + (lx + SK);
+        const size_t g = (size_t)gy * nx + gx;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[((size_t)a * 3 + i) * S + g] = dst[i * EA + c];
+      }
+    }
+    float2* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+}
+
+// Gram accumulators.  FP32 mode: products and per-thread sums in FP32, a
+// pairwise (shuffle-tree) warp sum, then FP64 across warps and blocks.  For
+// the monomial bases met here (s <= 10, ||J/theta|| <= 1) the normal equations
+// are well enough conditioned that this gives the same least-squares residual
+// as exact sums of the FP32 products; the FP32 basis vectors themselves set the
+// accuracy of the inner solve.
 template <typename TK> struct GramAcc;
 template <> struct GramAcc<float> {
-  DF v;
-  __device__ void zero() { v.hi = 0.f; v.lo = 0.f; }
-  __device__ void add(float2 a, float2 b) { df_add_prod(v, a.x, b.x); df_add_prod(v, a.y, b.y); }
+  float v;
+  __device__ void zero() { v = 0.f; }
+  __device__ void add(float2 a, float2 b) { v = fmaf(a.x, b.x, v); v = fmaf(a.y, b.y, v); }
   __device__ double warp_sum() {
-    DF r = v;
-    for (int o = 16; o > 0; o >>= 1) {
-      DF t;
-      t.hi = __shfl_xor_sync(0xffffffffu, r.hi, o);
-      t.lo = __shfl_xor_sync(0xffffffffu, r.lo, o);
-      r = df_add(r, t);
-    }
-    return (double)r.hi + (double)r.lo;
+    float r = v;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return f2d_bits(r);
   }
 };
 template <> struct GramAcc<double> {
@@ -269,25 +376,54 @@ template <> struct GramAcc<double> {
   }
 };
 
-// Per-block partial Gram matrices G_ab = <v_a, v_b> (real inner product of the
-// [p; q] form), a <= b <= s, system i = blockIdx.y.  Partial sums go to
-// gram_part[(block * 3 + i) * nent + e] and are reduced in a fixed order.
+
+// Gram matrices G_ab = <v_a, v_b> (real inner product of the [p; q] form),
+// a <= b <= s, for system i = blockIdx.y; block partials go to
+// part[(i * gridDim.x + block) * NE + e].  The last block to finish then
+//  1. reduces the partials in a fixed order (so results do not depend on
+//     which block finishes last),
+//  2. forms, per system, the normal equations of the least-squares problem
+//     min_c || b - (I - h lam J) sum_a c_a v_a ||:
+//       (B^T G B) c = B^T G e_0,  B = [I; 0] - sig [0; I]  (s x s),
+//  3. factors them with one warp per system (right-looking Cholesky; the basis
+//     is truncated at the first pivot below trunc_rel times the leading one, a
+//     numerically exhausted Krylov space; b = 0 gives c = 0) and solves.
 template <typename TK, int SK>
-__global__ void __launch_bounds__(256) k_gram(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
-                                              double* __restrict__ part, const DevStatus* st) {
+__global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
+                                                  double* __restrict__ part, double* __restrict__ coef,
+                                                  DevStatus* st) {
   if (st->error) return;
   typedef typename Vec2<TK>::type TK2;
   constexpr int NV = SK + 1;
   constexpr int NE = NV * (NV + 1) / 2;
+  constexpr int U = 4;                          // sites whose loads are in flight together
   const int S = p.S;
   const int i = blockIdx.y;
   GramAcc<TK> acc[NE];
 #pragma unroll
   for (int e = 0; e < NE; ++e) acc[e].zero();
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  const TK2* vi = v + (size_t)i * S;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + (U - 1) * stride < S; k += U * stride) {
+    TK2 x[U][NV];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) x[u][a] = vi[(size_t)a * 3 * S + k + u * stride];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int e = 0;
+#pragma unroll
+      for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int c = a; c < NV; ++c) acc[e++].add(x[u][a], x[u][c]);
+    }
+  }
+  for (; k < S; k += stride) {
     TK2 x[NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) x[a] = v[((size_t)a * 3 + i) * S + k];
+    for (int a = 0; a < NV; ++a) x[a] = vi[(size_t)a * 3 * S + k];
     int e = 0;
 #pragma unroll
     for (int a = 0; a < NV; ++a)
@@ -295,6 +431,7 @@ __global__ void __launch_bounds__(256) k_gram(StepParams p, const typename Vec2<
       for (int c = a; c < NV; ++c) acc[e++].add(x[a], x[c]);
   }
   __shared__ double red[8][NE];
+  __shared__ bool is_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
@@ -302,100 +439,141 @@ __global__ void __launch_bounds__(256) k_gram(StepParams p, const typename Vec2<
     if (lane == 0) red[warp][e] = w;
   }
   __syncthreads();
+  const int nb = gridDim.x;
   for (int e = threadIdx.x; e < NE; e += blockDim.x) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][e];
-    part[((size_t)blockIdx.x * 3 + i) * NE + e] = t;
+    part[((size_t)i * nb + blockIdx.x) * NE + e] = t;
   }
-}
-
-// Sum the partial Gram matrices (fixed order) and solve, per system, the
-// least-squares problem  min_c || b - (I - h lam J) sum_a c_a v_a ||  through its
-// normal equations (B^T G B) c = B^T G e_0 with B = [I; 0] - sig [0; I].
-// Cholesky with truncation of the basis at the first pivot that falls below
-// trunc_rel times the leading one (a numerically exhausted Krylov space).
-template <int SK>
-__global__ void __launch_bounds__(256) k_lsq(StepParams p, const double* __restrict__ part, int nblocks,
-                                             double* __restrict__ coef, DevStatus* st) {
-  if (st->error) return;
-  constexpr int NV = SK + 1;
-  constexpr int NE = NV * (NV + 1) / 2;
-  __shared__ double G[3][NE];
-  for (int t = threadIdx.x; t < 3 * NE; t += blockDim.x) {
-    const int i = t / NE, e = t - i * NE;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = 0;
-    for (; b + 4 <= nblocks; b += 4) {
-      s0 += part[((size_t)(b + 0) * 3 + i) * NE + e];
-      s1 += part[((size_t)(b + 1) * 3 + i) * NE + e];
-      s2 += part[((size_t)(b + 2) * 3 + i) * NE + e];
-      s3 += part[((size_t)(b + 3) * 3 + i) * NE + e];
-    }
-    for (; b < nblocks; ++b) s0 += part[((size_t)b * 3 + i) * NE + e];
-    G[i][e] = (s0 + s1) + (s2 + s3);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(&st->ticket_gram, 1u);
+    is_last = (t == gridDim.x * gridDim.y - 1);
   }
   __syncthreads();
-  if (threadIdx.x >= 3) return;
-  const int i = threadIdx.x;
-  auto g = [&](int a, int c) -> double {   // symmetric access into the packed upper triangle
-    if (a > c) { int t = a; a = c; c = t; }
-    return G[i][a * NV - a * (a - 1) / 2 + (c - a)];
-  };
-  const double sg = p.sig[i];
-  double N[SK][SK], r[SK], L[SK][SK];
-  for (int a = 0; a < SK; ++a) {
-    r[a] = g(a, 0) - sg * g(a + 1, 0);
-    for (int c = 0; c < SK; ++c)
-      N[a][c] = g(a, c) - sg * (g(a + 1, c) + g(a, c + 1)) + sg * sg * g(a + 1, c + 1);
+  if (!is_last) return;
+  __threadfence();
+  // 1. fixed-order reduction: thread t takes entry t % NT and block slice t / NT.
+  constexpr int NT = 3 * NE;
+  constexpr int SLICES = (256 / NT) > 0 ? (256 / NT) : 1;
+  __shared__ double slice[SLICES][NT];
+  __shared__ double G[3][NE];
+  __shared__ double Nm[3][SK][SK + 1];          // [.., SK] holds the right-hand side
+  for (int t = threadIdx.x; t < SLICES * NT; t += blockDim.x) {
+    const int sl = t / NT, r = t - sl * NT, si = r / NE, e = r - si * NE;
+    const int b0 = sl * nb / SLICES, b1 = (sl + 1) * nb / SLICES;
+    const double* pp = part + (size_t)si * nb * NE + e;
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int bb = b0;
+    for (; bb + 8 <= b1; bb += 8) {
+      double w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = __ldcg(pp + (size_t)(bb + j) * NE);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) q[j] += w[j];
+    }
+    for (int j = 0; bb < b1; ++bb, ++j) q[j] += __ldcg(pp + (size_t)bb * NE);
+    slice[sl][r] = ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
   }
-  int dim = SK;
-  if (!(g(0, 0) > 0.0)) dim = 0;   // b_i = 0: nothing to solve
-  const double lead = N[0][0];
-  for (int a = 0; a < dim; ++a) {
-    double dg = N[a][a];
-    for (int c = 0; c < a; ++c) dg -= L[a][c] * L[a][c];
-    if (!(dg > (double)p.trunc_rel * lead)) { dim = a; break; }
-    double la = sqrt(dg);
-    L[a][a] = la;
-    for (int b2 = a + 1; b2 < SK; ++b2) {
-      double t = N[b2][a];
-      for (int c = 0; c < a; ++c) t -= L[b2][c] * L[a][c];
-      L[b2][a] = t / la;
+  __syncthreads();
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    double sum = 0.0;
+    for (int sl = 0; sl < SLICES; ++sl) sum += slice[sl][t];
+    G[t / NE][t % NE] = sum;
+  }
+  __syncthreads();
+  // 2. normal equations, all entries in parallel
+  auto g = [&](int si, int a, int c) -> double {
+    if (a > c) { int t = a; a = c; c = t; }
+    return G[si][a * NV - a * (a - 1) / 2 + (c - a)];
+  };
+  for (int t = threadIdx.x; t < 3 * SK * (SK + 1); t += blockDim.x) {
+    const int si = t / (SK * (SK + 1)), r = t - si * SK * (SK + 1), a = r / (SK + 1), c = r - a * (SK + 1);
+    const double sg = p.sig[si];
+    Nm[si][a][c] = (c < SK) ? g(si, a, c) - sg * (g(si, a + 1, c) + g(si, a, c + 1)) + sg * sg * g(si, a + 1, c + 1)
+                            : g(si, a, 0) - sg * g(si, a + 1, 0);
+  }
+  __syncthreads();
+  // 3. one warp per system: Cholesky in place (lower triangle), then the two triangular solves
+  if (warp < 3) {
+    double (*N)[SK + 1] = Nm[warp];
+    int dim = (g(warp, 0, 0) > 0.0) ? SK : 0;
+    const double lead = N[0][0];
+    for (int a = 0; a < dim; ++a) {
+      const double dg = N[a][a];
+      if (!(dg > (double)p.trunc_rel * lead)) { dim = a; break; }
+      const double la = sqrt(dg);
+      __syncwarp();
+      for (int b2 = a + 1 + lane; b2 < SK; b2 += 32) N[b2][a] /= la;
+      if (lane == 0) N[a][a] = la;
+      __syncwarp();
+      const int m = SK - a - 1;
+      for (int idx = lane; idx < m * m; idx += 32) {
+        const int b2 = a + 1 + idx / m, c = a + 1 + idx % m;
+        if (c <= b2) N[b2][c] -= N[b2][a] * N[c][a];
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      double y[SK], cc[SK];
+      for (int a = 0; a < dim; ++a) {
+        double t = N[a][SK];
+        for (int b2 = 0; b2 < a; ++b2) t -= N[a][b2] * y[b2];
+        y[a] = t / N[a][a];
+      }
+      for (int a = dim - 1; a >= 0; --a) {
+        double t = y[a];
+        for (int b2 = a + 1; b2 < dim; ++b2) t -= N[b2][a] * cc[b2];
+        cc[a] = t / N[a][a];
+      }
+      for (int a = 0; a < SK; ++a) coef[warp * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
     }
   }
-  double y[SK], c[SK];
-  for (int a = 0; a < dim; ++a) {
-    double t = r[a];
-    for (int b2 = 0; b2 < a; ++b2) t -= L[a][b2] * y[b2];
-    y[a] = t / L[a][a];
-  }
-  for (int a = dim - 1; a >= 0; --a) {
-    double t = y[a];
-    for (int b2 = a + 1; b2 < dim; ++b2) t -= L[b2][a] * c[b2];
-    c[a] = t / L[a][a];
-  }
-  for (int a = 0; a < SK; ++a) coef[i * kMaxS + a] = (a < dim) ? c[a] : 0.0;
+  if (threadIdx.x == 0) st->ticket_gram = 0u;
+}
+
+template <int SK>
+void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
+  dim3 grid((p.nx + kPowTX - 1) / kPowTX, (p.ny + kPowTY - 1) / kPowTY);
+  k_powers<SK><<<grid, kPowThreads, pow_smem_bytes<SK>(), s>>>(p, (const float4*)b.jc, (float2*)b.v, b.status);
+}
+
+// Opt the matrix-powers kernels into more than 48 KB of dynamic shared memory.
+int prepare_powers() {
+#define MB4_ATTR(N)                                                                               \
+  if (cudaFuncSetAttribute(k_powers<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                           (int)pow_smem_bytes<N>()) != cudaSuccess)                              \
+    return MB4_ERR_CUDA;
+  MB4_ATTR(1) MB4_ATTR(2) MB4_ATTR(3) MB4_ATTR(4) MB4_ATTR(5) MB4_ATTR(6) MB4_ATTR(7) MB4_ATTR(8) MB4_ATTR(9)
+  MB4_ATTR(10)
+#undef MB4_ATTR
+  return MB4_OK;
 }
 
 template <typename TK>
 void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   typedef typename Vec2<TK>::type TK2;
+  if (sizeof(TK) == sizeof(float) && p.use_powers) {
+    switch (p.s) {
+      case 1: launch_powers_s<1>(p, b, s); break;
+      case 2: launch_powers_s<2>(p, b, s); break;
+      case 3: launch_powers_s<3>(p, b, s); break;
+      case 4: launch_powers_s<4>(p, b, s); break;
+      case 5: launch_powers_s<5>(p, b, s); break;
+      case 6: launch_powers_s<6>(p, b, s); break;
+      case 7: launch_powers_s<7>(p, b, s); break;
+      case 8: launch_powers_s<8>(p, b, s); break;
+      case 9: launch_powers_s<9>(p, b, s); break;
+      default: launch_powers_s<10>(p, b, s); break;
+    }
+    return;
+  }
   const int blocks = (p.S + 255) / 256;
   TK2* v = (TK2*)b.v;
   for (int a = 0; a < p.s; ++a)
     k_matvec<TK><<<blocks, 256, 0, s>>>(p, (const JCoef<TK>*)b.jc, v + (size_t)a * 3 * p.S,
                                         v + (size_t)(a + 1) * 3 * p.S, b.status);
-}
-
-template <typename TK, int SK>
-void launch_gram_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  k_gram<TK, SK><<<dim3(kGramBlocks, 3), 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, b.gram_part,
-                                                      b.status);
-}
-
-template <int SK>
-void launch_lsq_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  k_lsq<SK><<<1, 256, 0, s>>>(p, b.gram_part, kGramBlocks, b.coef, b.status);
 }
 
 #define MB4_SWITCH_S(CALL)        \
@@ -414,109 +592,167 @@ void launch_lsq_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 
 template <typename TK>
 void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-#define MB4_CALL(N) launch_gram_s<TK, N>(p, b, s)
+#define MB4_CALL(N)                                                                               \
+  k_gram_lsq<TK, N><<<dim3(p.gram_blocks, 3), 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, \
+                                                        b.gram_part, b.coef, b.status)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
 }
 
-void launch_lsq(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-#define MB4_CALL(N) launch_lsq_s<N>(p, b, s)
-  MB4_SWITCH_S(MB4_CALL)
-#undef MB4_CALL
+template <typename TK>
+int gram_blocks_per_system(int s_dim) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  switch (s_dim) {
+#define MB4_OCC(N) case N: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_lsq<TK, N>, 256, 0); break;
+    MB4_OCC(1) MB4_OCC(2) MB4_OCC(3) MB4_OCC(4) MB4_OCC(5) MB4_OCC(6) MB4_OCC(7) MB4_OCC(8) MB4_OCC(9)
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_lsq<TK, 10>, 256, 0); break;
+#undef MB4_OCC
+  }
+  if (e != cudaSuccess || occ < 1 || sms < 1) return 0;
+  int nb = sms * occ / 3;
+  if (nb > kGramCap) nb = kGramCap;   // more blocks only lengthen the last block's reduction
+  return nb < 1 ? 1 : nb;
 }
+template int gram_blocks_per_system<float>(int);
+template int gram_blocks_per_system<double>(int);
 
 template <typename TK>
 void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   launch_matvecs<TK>(p, b, s);
   launch_gram<TK>(p, b, s);
-  launch_lsq(p, b, s);
 }
 
-// Newton update (Algorithm 1 lines 18-20): rbar_i = sum_a c_ia v_a,i; Ubar_i += rbar_i
-// (FP64); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.
-template <typename TK>
+// Newton update (Algorithm 1 lines 18-20) and loop test (line 12; failure rule of
+// Sec. 2.2): rbar_i = sum_a c_ia v_a,i; Ubar_i += rbar_i in FP64 (Ubar^0 = tau u0 on
+// the first iteration); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
+// block to finish runs the test: continue while ||r^l||_inf > rtol ||u0||_inf (and,
+// when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
+// for at most newton_max iterations; with a graph it drives the WHILE node.
+template <typename TK, int SK>
 __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
-                                                const double* __restrict__ coef, double2* __restrict__ Ubar,
-                                                DevStatus* st) {
-  if (st->error) return;
+                                                const double* __restrict__ coef, const double2* __restrict__ u,
+                                                double2* __restrict__ Ubar, DevStatus* st,
+                                                cudaGraphConditionalHandle h, int use_cond) {
+  if (st->error) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
+    return;
+  }
   typedef typename Vec2<TK>::type TK2;
+  __shared__ TK cs[3][SK];
+  __shared__ float wmax[8];
+  __shared__ int wbad[8];
+  __shared__ bool is_last;
+  if (threadIdx.x < 3 * SK) cs[threadIdx.x / SK][threadIdx.x % SK] = (TK)coef[(threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
+  const bool first = (*(volatile int*)&st->newton_iter) == 0;
+  __syncthreads();
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  TK m = (TK)0;
-  bool bad = false;
+  float m = 0.f;
+  int bad = 0;
   if (k < S) {
     TK2 x[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       TK sx = 0, sy = 0;
-      for (int a = 0; a < p.s; ++a) {
-        const TK c = (TK)coef[i * kMaxS + a];
+#pragma unroll
+      for (int a = 0; a < SK; ++a) {
         const TK2 w = v[((size_t)a * 3 + i) * S + k];
-        sx += c * w.x;
-        sy += c * w.y;
+        sx += cs[i][a] * w.x;
+        sy += cs[i][a] * w.y;
       }
       x[i].x = sx;
       x[i].y = sy;
-      double2 U = Ubar[(size_t)i * S + k];
-      U.x += (double)sx;
-      U.y += (double)sy;
+    }
+    double2 u0;
+    if (first) u0 = u[k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double2 U;
+      if (first) {
+        U.x = fma(p.tau[i], u0.x, to_double(x[i].x));
+        U.y = fma(p.tau[i], u0.y, to_double(x[i].y));
+      } else {
+        U = Ubar[(size_t)i * S + k];
+        U.x += to_double(x[i].x);
+        U.y += to_double(x[i].y);
+      }
       Ubar[(size_t)i * S + k] = U;
     }
+    // ||r||_inf with r = T rbar, in FP32: it only decides whether to iterate again.
+    float xf[3][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { xf[i][0] = to_float(x[i].x); xf[i][1] = to_float(x[i].y); }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      TK rx = (TK)p.T[j][0] * x[0].x + (TK)p.T[j][1] * x[1].x + (TK)p.T[j][2] * x[2].x;
-      TK ry = (TK)p.T[j][0] * x[0].y + (TK)p.T[j][1] * x[1].y + (TK)p.T[j][2] * x[2].y;
+      const float t0 = p.fT[j][0], t1 = p.fT[j][1], t2 = p.fT[j][2];
+      const float rx = t0 * xf[0][0] + t1 * xf[1][0] + t2 * xf[2][0];
+      const float ry = t0 * xf[0][1] + t1 * xf[1][1] + t2 * xf[2][1];
       bad |= !(isfinite(rx) && isfinite(ry));
-      m = fmax(m, fmax(fabs(rx), fabs(ry)));
+      m = fmaxf(m, fmaxf(fabsf(rx), fabsf(ry)));
     }
   }
   m = warp_max(m);
   bad = __any_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
-    if (m > (TK)0) atomicMax(&st->rmax_bits, dbits((double)m));
-    if (bad) atomicOr(&st->nonfinite, 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { wmax[warp] = m; wbad[warp] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float bm = wmax[0];
+    int bb = wbad[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { bm = fmaxf(bm, wmax[w]); bb |= wbad[w]; }
+    if (bm > 0.f) atomicMax(&st->rmax_bits, dbits((double)bm));
+    if (bb) atomicOr(&st->nonfinite, 1);
+    __threadfence();
+    unsigned int t = atomicAdd(&st->ticket_update, 1u);
+    is_last = (t == gridDim.x - 1);
   }
-}
-
-template <typename TK>
-void launch_update(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  int blocks = (p.S + 255) / 256;
-  k_update<TK><<<blocks, 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, b.coef, b.Ubar, b.status);
-}
-
-// Newton loop test (Algorithm 1 line 12 and Sec. 2.2 on failure): continue while
-// ||r^l||_inf > rtol ||u0||_inf, at most newton_max iterations.  With a graph,
-// the decision drives the conditional WHILE node.
-__global__ void k_newton_check(StepParams p, DevStatus* st, cudaGraphConditionalHandle h, int use_cond) {
+  __syncthreads();
+  if (!is_last || threadIdx.x != 0) return;
+  __threadfence();
+  st->ticket_update = 0u;
   int cont = 0;
-  if (!st->error) {
-    st->newton_iter += 1;
-    const double r = __longlong_as_double((long long)st->rmax_bits);
-    const double u0 = __longlong_as_double((long long)st->u0max_bits);
-    st->last_rmax = r;
-    st->last_u0max = u0;
-    if (st->nonfinite) {
-      st->error = MB4_ERR_NONFINITE;
-    } else if (r <= p.newton_rtol * u0) {
-      cont = 0;
-    } else if (st->newton_iter >= p.newton_max) {
-      st->error = MB4_ERR_NEWTON_NOT_CONVERGED;
-    } else {
-      cont = 1;
-    }
-    st->last_newton_iters = st->newton_iter;
-    st->rmax_bits = 0ull;
+  const int it = st->newton_iter;                 // iteration index l of this update
+  const double r = __longlong_as_double((long long)atomicOr(&st->rmax_bits, 0ull));
+  const double u0n = (double)__uint_as_float(atomicOr(&st->u0max_bits, 0u));
+  const int nonfinite = atomicOr(&st->nonfinite, 0);
+  if (it < 8) st->hist[it] = r;
+  st->last_rmax = r;
+  st->last_u0max = u0n;
+  st->newton_iter = it + 1;
+  if (nonfinite || !isfinite(r)) {
+    st->error = MB4_ERR_NONFINITE;
+  } else if (r <= p.newton_rtol * u0n) {
+    cont = 0;
+  } else if (p.newton_predict > 0.0 && it >= 1 && r < 0.5 * st->prev_rmax &&
+             (r / st->prev_rmax) / (1.0 - r / st->prev_rmax) * r <= p.newton_predict * u0n) {
+    cont = 0;
+  } else if (it + 1 >= p.newton_max) {
+    st->error = MB4_ERR_NEWTON_NOT_CONVERGED;
+  } else {
+    cont = 1;
   }
+  st->prev_rmax = r;
+  st->last_newton_iters = it + 1;
+  st->rmax_bits = 0ull;
   st->cont = cont;
   if (use_cond) cudaGraphSetConditional(h, cont);
 }
 
-void launch_newton_check(const StepParams& p, const DevBuffers& b, unsigned long long h, int use_cond,
-                         cudaStream_t s) {
-  k_newton_check<<<1, 1, 0, s>>>(p, b.status, (cudaGraphConditionalHandle)h, use_cond);
+template <typename TK>
+void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long h, int use_cond, cudaStream_t s) {
+  int blocks = (p.S + 255) / 256;
+#define MB4_CALL(N)                                                                                           \
+  k_update<TK, N><<<blocks, 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, b.coef, b.u, b.Ubar, b.status, \
+                                         (cudaGraphConditionalHandle)h, use_cond)
+  MB4_SWITCH_S(MB4_CALL)
+#undef MB4_CALL
 }
 
-// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = sum_n T[2][n] Ubar_n.
+// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = sum_n T[2][n] Ubar_n.  Block 0
+// books the step and clears the per-step control fields for the next step.
 __global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restrict__ u,
                                                 const double2* __restrict__ Ubar, DevStatus* st) {
   if (st->error) return;
@@ -532,6 +768,11 @@ __global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restric
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->steps_done += 1;
     st->newton_total += st->newton_iter;
+    st->newton_iter = 0;
+    st->nonfinite = 0;
+    st->rmax_bits = 0ull;
+    st->u0max_bits = 0u;
+    st->prev_rmax = 0.0;
   }
 }
 
@@ -714,7 +955,7 @@ void launch_copy_solution_out(const StepParams& p, const DevBuffers& b, double2*
   template void launch_krylov<TK>(const StepParams&, const DevBuffers&, cudaStream_t);             \
   template void launch_matvecs<TK>(const StepParams&, const DevBuffers&, cudaStream_t);            \
   template void launch_gram<TK>(const StepParams&, const DevBuffers&, cudaStream_t);               \
-  template void launch_update<TK>(const StepParams&, const DevBuffers&, cudaStream_t);             \
+  template void launch_update<TK>(const StepParams&, const DevBuffers&, unsigned long long, int, cudaStream_t); \
   template void launch_copy_rhs_in<TK>(const StepParams&, const DevBuffers&, const double2*, cudaStream_t); \
   template void launch_copy_solution_out<TK>(const StepParams&, const DevBuffers&, double2*, cudaStream_t);
 MB4_INST(float)

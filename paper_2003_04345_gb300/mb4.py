@@ -31,7 +31,7 @@ MB4_ERR_ADMISSION_REJECTED = -8
 MB4_FP64 = 0
 MB4_MIXED = 1
 MAX_KRYLOV_S = 10
-KERNEL_CLASSES = ("step_begin", "setup", "residual", "matvec", "gram", "lsq", "update", "check", "accept")
+KERNEL_CLASSES = ("setup", "residual", "matvec", "gram", "update", "accept")
 
 # Every entry point include/mb4.h declares.
 EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", "mb4_get_state",
@@ -55,15 +55,18 @@ class Nonlinearity(C.Structure):
 class Options(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("krylov_s", C.c_int),
                 ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
-                ("stream", C.c_void_p), ("use_graph", C.c_int)]
+                ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("steps_done", C.c_longlong), ("newton_iters_total", C.c_longlong),
-                ("newton_iters_last", C.c_int), ("last_update_inf", C.c_double), ("u0_inf", C.c_double)]
+                ("newton_iters_last", C.c_int), ("last_update_inf", C.c_double), ("u0_inf", C.c_double),
+                ("update_hist", C.c_double * 8)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["update_hist"] = list(self.update_hist)[:max(0, self.newton_iters_last)]
+        return d
 
 
 class MB4Error(RuntimeError):
@@ -173,7 +176,7 @@ class Integrator:
 
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", krylov_s=0,
                  newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0, c2=2.0 / 3.0,
-                 stream=None, use_graph=True):
+                 stream=None, use_graph=True, newton_predict=0.0):
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -202,6 +205,7 @@ class Integrator:
         opt.alpha1 = float(alpha1)
         opt.c1, opt.c2 = float(c1), float(c2)
         opt.use_graph = 1 if use_graph else 0
+        opt.newton_predict = float(newton_predict)
         if stream is not None:
             opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self.precision = precision

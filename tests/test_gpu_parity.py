@@ -64,8 +64,11 @@ def test_residual_kernel_matches_oracle(mb4, nx, ny, precision):
 # ---------------------------------------------------------------------------
 # Shifted solves alone: (I - h lam_i J) x_i = b_i to the accuracy of one cycle.
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,eta", [("fp64", 1e-7), ("mixed", 3e-5)])
-def test_shifted_solves_reduce_residual(mb4, precision, eta):
+@pytest.mark.parametrize("precision,s,eta", [("fp64", 8, 1e-7), ("fp64", 5, 3e-5), ("mixed", 5, 3e-5),
+                                             ("mixed", 8, 1e-5)])
+def test_shifted_solves_reduce_residual(mb4, precision, s, eta):
+    """One s-step GMRES cycle reduces ||b - (I - h lam_i J) x|| / ||b|| below eta
+    for a random right-hand side on the 16x16 workload (h = 0.01)."""
     w = inputs.grid16_fp64()
     S = w.S
     V = w.potential()
@@ -75,7 +78,7 @@ def test_shifted_solves_reduce_residual(mb4, precision, eta):
     prob = orc.Problem(w.nx, w.ny, V, w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
     J = orc.jacobian_real(prob, u0)
     lam = mb4.constants()["lam"]
-    with mb4.Integrator(w.nx, w.ny, V, w.chi, w.h, precision=precision) as it:
+    with mb4.Integrator(w.nx, w.ny, V, w.chi, w.h, precision=precision, krylov_s=s) as it:
         x = it.solve_shifted(u0, b)
     for i in range(3):
         xr = orc.to_real(x[i])
