@@ -196,6 +196,33 @@ int mb4_solve_shifted(mb4_ctx* ctx, const double* u0_re, const double* u0_im,
 int mb4_constants(double alpha1, double c1, double c2, double* E34, double* lam3,
                   double* T9, double* Tinv9, double* gauss_x6, double* gauss_w6);
 
+/* Largest grid (nx*ny sites) that mb4_observables_noalloc accepts. */
+#define MB4_NOALLOC_MAX_SITES (1 << 30)
+
+/* The six observables of mb4_observables for a state given directly as device
+ * planes, for callers that cannot allocate device memory: code that runs under
+ * an allocator or memory pool owning all device memory, or where a cudaMalloc
+ * (and the synchronisation it may cause) is not allowed at that moment.  The
+ * paper has no counterpart: this is a service entry point of the library.
+ *
+ * It needs no context and allocates nothing.  re, im, v (S = nx*ny doubles
+ * each, row-major) and out6 (6 doubles: H, U_K, U_E, U_nl, sum|u|^2, sum|u|^4)
+ * are device memory of the current device, supplied by the caller; the call
+ * only enqueues two kernels on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and returns; synchronise the stream before reading out6.  Its scratch
+ * is a fixed 24 KiB array of block partial sums inside the library image,
+ * which every GPU that loads the library holds until the process exits.  The
+ * first call on a device looks up that array's device address (once per device,
+ * with the device current), so make the first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (different streams,
+ * other host threads) race and give wrong results; serialise them.  Every call
+ * overwrites the whole part of the array it reads, so no clearing is needed.
+ * Returns MB4_ERR_INVALID_ARG for nx or ny < 3, nx*ny > MB4_NOALLOC_MAX_SITES
+ * or a NULL pointer, MB4_ERR_CUDA if the set-up or a launch fails. */
+int mb4_observables_noalloc(int nx, int ny, double tx, double ty, double onsite, double chi,
+                            const double* re, const double* im, const double* v, double* out6,
+                            void* stream);
+
 const char* mb4_status_string(int status);
 
 /* Library version, for diagnostics. */

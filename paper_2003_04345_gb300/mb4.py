@@ -106,6 +106,8 @@ def lib():
         L.mb4_status_string.argtypes = [C.c_int]
         L.mb4_status_string.restype = C.c_char_p
         L.mb4_version.restype = C.c_char_p
+        L.mb4_observables_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                              _P, _P, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -312,6 +314,15 @@ class Integrator:
         _check(lib().mb4_solve_shifted(self._ctx, a.pre, a.pim, b.pre, b.pim, re.ctypes.data, im.ctypes.data,
                                        0), "mb4_solve_shifted")
         return (re + 1j * im).reshape(3, self.S)
+
+
+def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.0, stream=None):
+    """mb4_observables_noalloc on torch CUDA tensors (float64; re, im, V of nx*ny
+    elements, out6 of 6): enqueues the reduction on ``stream`` without allocating."""
+    sp = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().mb4_observables_noalloc(int(nx), int(ny), float(tx), float(tx if ty is None else ty),
+                                         float(onsite), float(chi), re.data_ptr(), im.data_ptr(), V.data_ptr(),
+                                         out6.data_ptr(), sp), "mb4_observables_noalloc")
 
 
 def from_workload(w, precision="fp64", **kw):
