@@ -188,6 +188,59 @@ int mb4_solve_shifted(mb4_ctx* ctx, const double* u0_re, const double* u0_im,
                       const double* b_re3, const double* b_im3,
                       double* x_re3, double* x_im3, int on_device);
 
+/* ---- batches: many independent instances of one grid shape per launch -----
+ * A batch holds `batch` instances that share the grid (nx, ny, tx, ty, onsite),
+ * h and the options; each has its own potential, nonlinearity chi, state and
+ * Newton status.  Every kernel of a step covers all instances in one launch;
+ * an instance whose Newton iteration has converged (or failed) is masked while
+ * the others continue, so one slow or failing instance neither blocks nor
+ * corrupts the rest.  Instance-major arrays: instance b's S values start at
+ * offset b*S.  A single context (mb4_create) is a batch of one. */
+typedef struct mb4_batch mb4_batch;
+
+/* Create a batch.  pot->v holds batch*S doubles (instance-major); chi is a host
+ * array of batch values.  All instances start enabled with a zero state. */
+int mb4_batch_create(const mb4_grid* grid, int batch, const mb4_potential* pot, const double* chi, double h,
+                     const mb4_options* opt, mb4_batch** out);
+
+void mb4_batch_destroy(mb4_batch* b);
+
+/* State of one instance (instance >= 0: S doubles each) or of all of them
+ * (instance = -1: batch*S doubles each). */
+int mb4_batch_set_state(mb4_batch* b, int instance, const double* re, const double* im, int on_device);
+int mb4_batch_get_state(const mb4_batch* b, int instance, double* re, double* im, int on_device);
+
+/* Reuse one slot: new potential (S doubles), chi and state; clears the
+ * instance's error and counters and enables it. */
+int mb4_batch_load(mb4_batch* b, int instance, const double* v, double chi, const double* re, const double* im,
+                   int on_device);
+
+/* Enable (1) or disable (0) stepping of one instance; a disabled instance keeps
+ * its state and takes no part in later steps. */
+int mb4_batch_enable(mb4_batch* b, int instance, int enabled);
+
+/* Enqueue nsteps MB4 steps for every enabled instance without an error, on the
+ * batch's stream, without waiting.  Counters restart at zero. */
+int mb4_batch_step_async(mb4_batch* b, int nsteps);
+
+/* Wait for the batch's stream; per-instance stats (`batch` entries) and status
+ * codes (MB4_OK or the instance's error) for the steps enqueued since the last
+ * mb4_batch_step_async.  Either pointer may be NULL.  Returns MB4_OK if every
+ * enabled instance is error-free, else the first instance error. */
+int mb4_batch_wait(mb4_batch* b, mb4_stats* stats, int* status);
+
+/* mb4_batch_step_async followed by mb4_batch_wait. */
+int mb4_batch_step(mb4_batch* b, int nsteps, mb4_stats* stats, int* status);
+
+/* Observables of every instance: out[b*6 + k], k as in mb4_observables. */
+int mb4_batch_observables(const mb4_batch* b, double* out);
+
+/* Clear the error of every instance (the state is the last accepted one). */
+int mb4_batch_clear_errors(mb4_batch* b);
+
+/* Device bytes a batch of this shape and options would allocate (for admission). */
+long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt);
+
 /* Host-only: the MB4 constants the library computes for (alpha1, c1, c2), c3 = 1.
  * E34: 12 doubles, row-major E[i][j], i = 1..3, j = 0..3 (j = 0 is E_i0, eq. Ei0).
  * lam3: eigenvalues of E(1:3,1:3), ascending.  T9, Tinv9: row-major 3x3.

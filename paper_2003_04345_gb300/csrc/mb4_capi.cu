@@ -1,7 +1,8 @@
-// libmb4 C ABI: contexts, device buffers, the step graph and the entry points
-// declared in include/mb4.h.
+// libmb4 C ABI: batches and single contexts, device buffers, the step graph
+// and the entry points declared in include/mb4.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -12,25 +13,30 @@
 
 using namespace mb4;
 
-struct mb4_ctx {
+struct mb4_batch {
   int device = 0;
   cudaStream_t stream = nullptr;
   int precision = MB4_FP64;
   int use_graph = 1;
+  int B = 1;
+  double theta = 1.0;
   Constants k{};
   StepParams p{};
   DevBuffers b{};
   size_t tk = 8;                  // sizeof(TK)
-  // step graph (one launch = one MB4 step)
+  // step graph (one launch = one MB4 step of every instance)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle handle = 0;
   // scratch for state I/O and the test entry points (allocated on first use)
   double2* tmp3a = nullptr;
   double2* tmp3b = nullptr;
-  double* io = nullptr;
+  double* io = nullptr;           // 6*max(B*S, S) doubles
   std::vector<void*> allocs;
+  std::vector<InstStatus> host_status;
 };
+
+struct mb4_ctx : mb4_batch {};
 
 namespace {
 
@@ -46,10 +52,17 @@ int cuda_rc(cudaError_t e) {
     if (_rc != MB4_OK) return _rc;           \
   } while (0)
 
-int dalloc(mb4_ctx* c, void** ptr, size_t bytes) {
-  // 256-byte aligned by cudaMalloc; bytes rounded up so every plane keeps that alignment.
-  bytes = (bytes + 255) & ~size_t(255);
-  cudaError_t e = cudaMalloc(ptr, bytes);
+#define MB4_CHECK(call)                      \
+  do {                                       \
+    int _rc = (call);                        \
+    if (_rc != MB4_OK) return _rc;           \
+  } while (0)
+
+size_t round256(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+
+int dalloc(mb4_batch* c, void** ptr, size_t bytes) {
+  // 256-byte aligned by cudaMalloc; sizes rounded up so every array keeps that alignment.
+  cudaError_t e = cudaMalloc(ptr, round256(bytes));
   if (e != cudaSuccess) {
     *ptr = nullptr;
     return cuda_rc(e);
@@ -58,25 +71,122 @@ int dalloc(mb4_ctx* c, void** ptr, size_t bytes) {
   return MB4_OK;
 }
 
+int validate_options(const mb4_options* in, mb4_options* o) {
+  if (in) *o = *in;
+  else mb4_default_options(o);
+  if (o->precision != MB4_FP64 && o->precision != MB4_MIXED) return MB4_ERR_INVALID_ARG;
+  if (!(o->newton_predict >= 0.0)) return MB4_ERR_INVALID_ARG;
+  // Measured on GB300 at 512x512: with the update test alone the Newton loop takes
+  // 4 iterations for s >= 4, so s = 4 is cheapest; the predicted-error test cuts
+  // it to 3 from s = 5 on.
+  if (o->krylov_s == 0) o->krylov_s = (o->newton_predict > 0.0) ? 5 : 4;
+  if (o->krylov_s < 1 || o->krylov_s > MB4_MAX_KRYLOV_S) return MB4_ERR_INVALID_ARG;
+  if (!(o->newton_rtol > 0.0) || o->newton_max < 1) return MB4_ERR_INVALID_ARG;
+  return MB4_OK;
+}
+
+int validate_grid(const mb4_grid* grid, int B) {
+  if (!grid || B < 1) return MB4_ERR_INVALID_ARG;
+  if (grid->nx < 3 || grid->ny < 3) return MB4_ERR_INVALID_ARG;
+  if ((long long)grid->nx * grid->ny > (1LL << 30)) return MB4_ERR_INVALID_ARG;
+  if ((long long)grid->nx * grid->ny * B > (1LL << 34)) return MB4_ERR_INVALID_ARG;
+  if (!std::isfinite(grid->tx) || !std::isfinite(grid->ty) || !std::isfinite(grid->onsite))
+    return MB4_ERR_INVALID_ARG;
+  return MB4_OK;
+}
+
+void fill_inst_const(const mb4_batch* c, double chi, InstConst* out) {
+  const Constants& K = c->k;
+  std::memset(out, 0, sizeof(*out));
+  for (int q = 0; q < kGauss; ++q) {
+    const double z = K.gx[q];
+    double W[3];
+    for (int j = 0; j < 3; ++j) W[j] = K.gw[q] * ((K.Acoef[j][2] * z + K.Acoef[j][1]) * z + K.Acoef[j][0]);
+    for (int i = 0; i < 3; ++i) {
+      double s = 0;
+      for (int j = 0; j < 3; ++j) s += K.Tinv[i][j] * W[j];
+      out->hchiW[i][q] = c->p.h * chi * s;
+    }
+  }
+  out->chi = chi;
+  out->chi_theta = chi / c->theta;
+  out->f_chi = (float)chi;
+  out->f_chi_theta = (float)(chi / c->theta);
+}
+
+void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options& o) {
+  StepParams& p = c->p;
+  const Constants& K = c->k;
+  p.nx = grid->nx;
+  p.ny = grid->ny;
+  p.S = grid->nx * grid->ny;
+  p.B = c->B;
+  p.s = o.krylov_s;
+  p.tx = grid->tx;
+  p.ty = grid->ty;
+  p.eps0 = grid->onsite;
+  p.h = h;
+  for (int i = 0; i < 3; ++i) {
+    p.hlam[i] = h * K.lam[i];
+    double e0 = 0, tau = 0, tc = 0;
+    for (int j = 0; j < 3; ++j) {
+      e0 += K.Tinv[i][j] * K.E[j][0];
+      tau += K.Tinv[i][j];
+      tc += K.Tinv[i][j] * K.c[j];
+    }
+    p.he0[i] = h * e0;
+    p.tau[i] = tau;
+    p.hTc[i] = h * tc;
+    for (int j = 0; j < 3; ++j) p.T[i][j] = K.T[i][j];
+  }
+  for (int q = 0; q < kGauss; ++q) {
+    const double z = K.gx[q];
+    double l[4];
+    for (int j = 0; j < 4; ++j) l[j] = ((K.lag[j][3] * z + K.lag[j][2]) * z + K.lag[j][1]) * z + K.lag[j][0];
+    p.L0[q] = l[0];
+    for (int n = 0; n < 3; ++n) {
+      double s = 0;
+      for (int m = 0; m < 3; ++m) s += l[m + 1] * K.T[m][n];
+      p.LT[q][n] = s;
+    }
+  }
+  p.inv_theta = 1.0 / c->theta;
+  p.txt = grid->tx / c->theta;
+  p.tyt = grid->ty / c->theta;
+  for (int i = 0; i < 3; ++i) p.sig[i] = h * K.lam[i] * c->theta;
+  p.newton_rtol = o.newton_rtol;
+  p.newton_predict = o.newton_predict;
+  p.newton_max = o.newton_max;
+  p.trunc_rel = (o.precision == MB4_MIXED) ? 1e-12f : 1e-26f;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) p.fT[i][j] = (float)p.T[i][j];
+    p.f_hTc[i] = (float)p.hTc[i];
+  }
+  p.f_inv_theta = (float)p.inv_theta;
+  p.f_txt = (float)p.txt;
+  p.f_tyt = (float)p.tyt;
+}
+
 template <typename TK>
-void enqueue_newton_body(mb4_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+void enqueue_newton_body(mb4_batch* c, cudaStream_t s, unsigned long long handle, int use_cond) {
   launch_residual<TK>(c->p, c->b, true, s);
   launch_krylov<TK>(c->p, c->b, s);
   launch_update<TK>(c->p, c->b, handle, use_cond, s);
 }
 
-void enqueue_body(mb4_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+void enqueue_body(mb4_batch* c, cudaStream_t s, unsigned long long handle, int use_cond) {
   if (c->precision == MB4_MIXED) enqueue_newton_body<float>(c, s, handle, use_cond);
   else enqueue_newton_body<double>(c, s, handle, use_cond);
 }
 
-void enqueue_setup(mb4_ctx* c, cudaStream_t s) {
+void enqueue_setup(mb4_batch* c, cudaStream_t s) {
   if (c->precision == MB4_MIXED) launch_setup<float>(c->p, c->b, s);
   else launch_setup<double>(c->p, c->b, s);
 }
 
-// One MB4 step as a graph: setup -> WHILE(cont){residual, matvecs, gram+lsq, update+test} -> accept.
-int build_graph(mb4_ctx* c) {
+// One MB4 step as a graph: setup -> WHILE(any instance continues){residual, basis, gram+lsq,
+// update+test} -> accept.
+int build_graph(mb4_batch* c) {
   cudaStream_t cap;
   MB4_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   int rc = MB4_OK;
@@ -131,18 +241,17 @@ int build_graph(mb4_ctx* c) {
   return rc;
 }
 
-int ensure_scratch(mb4_ctx* c) {
-  if (c->tmp3a) return MB4_OK;
-  const size_t S = (size_t)c->p.S;
-  int rc;
-  if ((rc = dalloc(c, (void**)&c->tmp3a, 3 * S * sizeof(double2))) != MB4_OK) return rc;
-  if ((rc = dalloc(c, (void**)&c->tmp3b, 3 * S * sizeof(double2))) != MB4_OK) return rc;
-  if ((rc = dalloc(c, (void**)&c->io, 6 * S * sizeof(double))) != MB4_OK) return rc;
+int ensure_scratch(mb4_batch* c) {
+  if (c->io) return MB4_OK;
+  const size_t S = (size_t)c->p.S, BS = (size_t)c->B * S;
+  MB4_CHECK(dalloc(c, (void**)&c->tmp3a, 3 * S * sizeof(double2)));
+  MB4_CHECK(dalloc(c, (void**)&c->tmp3b, 3 * S * sizeof(double2)));
+  MB4_CHECK(dalloc(c, (void**)&c->io, 6 * std::max(BS, S) * sizeof(double)));
   return MB4_OK;
 }
 
-// Bring n doubles (re, im each) onto the device, planar, into c->io[0..2n).
-int stage_in(mb4_ctx* c, const double* re, const double* im, size_t n, int on_device, const double** dre,
+// Bring n (re, im) doubles onto the device, planar; host data is staged through c->io.
+int stage_in(mb4_batch* c, const double* re, const double* im, size_t n, int on_device, const double** dre,
              const double** dim) {
   if (on_device) {
     *dre = re;
@@ -156,14 +265,14 @@ int stage_in(mb4_ctx* c, const double* re, const double* im, size_t n, int on_de
   return MB4_OK;
 }
 
-int stage_out(mb4_ctx* c, const double2* z, double* re, double* im, size_t n, int on_device) {
+int stage_out(mb4_batch* c, const double2* z, double* re, double* im, size_t n, int on_device) {
   if (on_device) {
-    launch_unpack(z, re, im, (int)n, c->stream);
+    launch_unpack(z, re, im, n, c->stream);
     MB4_TRY(cudaGetLastError());
     MB4_TRY(cudaStreamSynchronize(c->stream));
     return MB4_OK;
   }
-  launch_unpack(z, c->io, c->io + n, (int)n, c->stream);
+  launch_unpack(z, c->io, c->io + n, n, c->stream);
   MB4_TRY(cudaGetLastError());
   MB4_TRY(cudaMemcpyAsync(re, c->io, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   MB4_TRY(cudaMemcpyAsync(im, c->io + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -171,8 +280,167 @@ int stage_out(mb4_ctx* c, const double2* z, double* re, double* im, size_t n, in
   return MB4_OK;
 }
 
-int reset_status(mb4_ctx* c) {
-  MB4_TRY(cudaMemsetAsync(c->b.status, 0, sizeof(DevStatus), c->stream));
+int read_status(mb4_batch* c) {
+  c->host_status.resize(c->B);
+  MB4_TRY(cudaMemcpyAsync(c->host_status.data(), c->b.is, sizeof(InstStatus) * c->B, cudaMemcpyDeviceToHost,
+                          c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int write_status(mb4_batch* c) {
+  MB4_TRY(cudaMemcpyAsync(c->b.is, c->host_status.data(), sizeof(InstStatus) * c->B, cudaMemcpyHostToDevice,
+                          c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+void fill_stats(const InstStatus& s, mb4_stats* st) {
+  std::memset(st, 0, sizeof(*st));
+  st->steps_done = s.steps_done;
+  st->newton_iters_total = s.newton_total;
+  st->newton_iters_last = s.last_newton_iters;
+  st->last_update_inf = s.last_rmax;
+  st->u0_inf = s.last_u0max;
+  for (int l = 0; l < 8; ++l) st->update_hist[l] = (l < s.last_newton_iters) ? s.hist[l] : 0.0;
+}
+
+long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
+  const size_t S = (size_t)nx * ny, BS = S * B;
+  const size_t tk = (o.precision == MB4_MIXED) ? 4 : 8;
+  const int nent = (o.krylov_s + 1) * (o.krylov_s + 2) / 2;
+  size_t t = 0;
+  t += round256(BS * 16) + 2 * round256(BS * 8) + round256(BS * 16) + round256(3 * BS * 16);
+  t += round256(BS * 4 * tk) + round256((size_t)(o.krylov_s + 1) * 3 * BS * 2 * tk);
+  t += round256((size_t)B * 3 * kGramCap * nent * 8) + round256((size_t)B * 3 * kMaxS * 8);
+  t += round256((size_t)B * kObsBlocksMax * 12 * 8) + round256((size_t)B * 6 * 8);
+  t += round256(B * sizeof(InstConst)) + round256(B * sizeof(InstStatus)) + round256(sizeof(BatchCtl));
+  t += 2 * round256(3 * S * 16) + round256(6 * std::max(BS, S) * 8);   // I/O scratch
+  return (long long)t;
+}
+
+// Create a batch of B instances; V is host B*S doubles, chi host B doubles.
+int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const double* chi, double h,
+               const mb4_options& o) {
+  MB4_CHECK(compute_constants(o.alpha1, o.c1, o.c2, &c->k));
+  c->precision = o.precision;
+  c->use_graph = o.use_graph ? 1 : 0;
+  c->stream = (cudaStream_t)o.stream;
+  c->tk = (o.precision == MB4_MIXED) ? sizeof(float) : sizeof(double);
+  c->B = B;
+  MB4_TRY(cudaGetDevice(&c->device));
+  const size_t S = (size_t)grid->nx * grid->ny, BS = S * B;
+  double vmax = 0.0;
+  std::vector<double> D(BS);
+  for (size_t k = 0; k < BS; ++k) {
+    if (!std::isfinite(V[k])) return MB4_ERR_INVALID_ARG;
+    D[k] = grid->onsite + V[k];
+    vmax = std::fmax(vmax, std::fabs(D[k]));
+  }
+  for (int b = 0; b < B; ++b)
+    if (!std::isfinite(chi[b])) return MB4_ERR_INVALID_ARG;
+  c->theta = vmax + 2.0 * std::fabs(grid->tx) + 2.0 * std::fabs(grid->ty);
+  if (!(c->theta > 0.0)) c->theta = 1.0;
+  fill_params(c, grid, h, o);
+  StepParams& p = c->p;
+  p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B)
+                                              : gram_blocks_per_system<double>(p.s, B);
+  if (p.gram_blocks < 1) return MB4_ERR_CUDA;
+  p.use_powers = (o.precision == MB4_MIXED) ? 1 : 0;
+  if (p.use_powers) MB4_CHECK(prepare_powers());
+
+  DevBuffers& d = c->b;
+  const size_t tk = c->tk;
+  const int nent = (p.s + 1) * (p.s + 2) / 2;
+  MB4_CHECK(dalloc(c, (void**)&d.u, BS * sizeof(double2)));
+  MB4_CHECK(dalloc(c, (void**)&d.V, BS * sizeof(double)));
+  MB4_CHECK(dalloc(c, (void**)&d.d, BS * sizeof(double)));
+  MB4_CHECK(dalloc(c, (void**)&d.S0, BS * sizeof(double2)));
+  MB4_CHECK(dalloc(c, (void**)&d.Ubar, 3 * BS * sizeof(double2)));
+  MB4_CHECK(dalloc(c, &d.jc, BS * 4 * tk));
+  MB4_CHECK(dalloc(c, &d.v, (size_t)(p.s + 1) * 3 * BS * 2 * tk));
+  MB4_CHECK(dalloc(c, (void**)&d.gram_part, (size_t)B * 3 * p.gram_blocks * nent * sizeof(double)));
+  MB4_CHECK(dalloc(c, (void**)&d.coef, (size_t)B * 3 * kMaxS * sizeof(double)));
+  MB4_CHECK(dalloc(c, (void**)&d.obs_part, (size_t)B * obs_blocks_per_instance(B) * 12 * sizeof(double)));
+  MB4_CHECK(dalloc(c, (void**)&d.obs_out, (size_t)B * 6 * sizeof(double)));
+  MB4_CHECK(dalloc(c, (void**)&d.ic, (size_t)B * sizeof(InstConst)));
+  MB4_CHECK(dalloc(c, (void**)&d.is, (size_t)B * sizeof(InstStatus)));
+  MB4_CHECK(dalloc(c, (void**)&d.bc, sizeof(BatchCtl)));
+  std::vector<InstConst> ic(B);
+  for (int b = 0; b < B; ++b) fill_inst_const(c, chi[b], &ic[b]);
+  c->host_status.assign(B, InstStatus{});
+  for (int b = 0; b < B; ++b) c->host_status[b].enabled = 1;
+  MB4_TRY(cudaMemcpyAsync(d.V, V, BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  MB4_TRY(cudaMemcpyAsync(d.d, D.data(), BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  MB4_TRY(cudaMemcpyAsync(d.ic, ic.data(), B * sizeof(InstConst), cudaMemcpyHostToDevice, c->stream));
+  MB4_TRY(cudaMemsetAsync(d.u, 0, BS * sizeof(double2), c->stream));
+  MB4_TRY(cudaMemsetAsync(d.Ubar, 0, 3 * BS * sizeof(double2), c->stream));
+  MB4_TRY(cudaMemsetAsync(d.coef, 0, (size_t)B * 3 * kMaxS * sizeof(double), c->stream));
+  MB4_TRY(cudaMemsetAsync(d.bc, 0, sizeof(BatchCtl), c->stream));
+  MB4_CHECK(write_status(c));
+  if (c->use_graph) MB4_CHECK(build_graph(c));
+  return MB4_OK;
+}
+
+int potential_to_host(const mb4_potential* pot, size_t n, std::vector<double>* V) {
+  if (!pot || !pot->v) return MB4_ERR_INVALID_ARG;
+  V->resize(n);
+  if (pot->on_device) {
+    MB4_TRY(cudaMemcpy(V->data(), pot->v, n * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(V->data(), pot->v, n * sizeof(double));
+  }
+  return MB4_OK;
+}
+
+int step_async(mb4_batch* c, int nsteps) {
+  launch_arm(c->p, c->b, c->stream);
+  if (c->use_graph) {
+    for (int n = 0; n < nsteps; ++n) MB4_TRY(cudaGraphLaunch(c->exec, c->stream));
+  } else {
+    for (int n = 0; n < nsteps; ++n) {
+      enqueue_setup(c, c->stream);
+      for (;;) {
+        enqueue_body(c, c->stream, 0ull, 0);
+        MB4_TRY(cudaGetLastError());
+        BatchCtl bc;
+        MB4_TRY(cudaMemcpyAsync(&bc, c->b.bc, sizeof(bc), cudaMemcpyDeviceToHost, c->stream));
+        MB4_TRY(cudaStreamSynchronize(c->stream));
+        if (!bc.any_cont) break;
+      }
+      launch_accept(c->p, c->b, c->stream);
+    }
+  }
+  MB4_TRY(cudaGetLastError());
+  return MB4_OK;
+}
+
+int wait_batch(mb4_batch* c, mb4_stats* stats, int* status) {
+  MB4_CHECK(read_status(c));
+  int first = MB4_OK;
+  for (int b = 0; b < c->B; ++b) {
+    const InstStatus& s = c->host_status[b];
+    if (stats) fill_stats(s, stats + b);
+    if (status) status[b] = s.error;
+    if (first == MB4_OK && s.error) first = s.error;
+  }
+  return first;
+}
+
+int clear_errors(mb4_batch* c) {
+  MB4_CHECK(read_status(c));
+  for (auto& s : c->host_status) {
+    s.error = MB4_OK;
+    s.steps_done = 0;
+    s.newton_total = 0;
+  }
+  return write_status(c);
+}
+
+int check_instance(const mb4_batch* c, int instance, bool allow_all) {
+  if (!c) return MB4_ERR_INVALID_ARG;
+  if (instance == -1 && allow_all) return MB4_OK;
+  if (instance < 0 || instance >= c->B) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -196,7 +464,7 @@ int mb4_default_options(mb4_options* o) {
   return MB4_OK;
 }
 
-const char* mb4_version(void) { return "libmb4 0.1 (sm_103a)"; }
+const char* mb4_version(void) { return "libmb4 0.2 (sm_103a)"; }
 
 const char* mb4_status_string(int s) {
   switch (s) {
@@ -213,7 +481,9 @@ const char* mb4_status_string(int s) {
   }
 }
 
-void mb4_destroy(mb4_ctx* c) {
+// ---- batches ---------------------------------------------------------------
+
+void mb4_batch_destroy(mb4_batch* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   if (c->exec) cudaGraphExecDestroy(c->exec);
@@ -222,247 +492,253 @@ void mb4_destroy(mb4_ctx* c) {
   delete c;
 }
 
+long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt) {
+  mb4_options o;
+  if (nx < 3 || ny < 3 || batch < 1 || validate_options(opt, &o) != MB4_OK) return -1;
+  return batch_bytes(nx, ny, batch, o);
+}
+
+int mb4_batch_create(const mb4_grid* grid, int batch, const mb4_potential* pot, const double* chi, double h,
+                     const mb4_options* opt, mb4_batch** out) {
+  if (!out) return MB4_ERR_INVALID_ARG;
+  *out = nullptr;
+  MB4_CHECK(validate_grid(grid, batch));
+  if (!chi || !std::isfinite(h) || h == 0.0) return MB4_ERR_INVALID_ARG;
+  mb4_options o;
+  MB4_CHECK(validate_options(opt, &o));
+  std::vector<double> V;
+  MB4_CHECK(potential_to_host(pot, (size_t)grid->nx * grid->ny * batch, &V));
+  mb4_batch* c = new (std::nothrow) mb4_batch();
+  if (!c) return MB4_ERR_OUT_OF_MEMORY;
+  int rc = make_batch(c, grid, batch, V.data(), chi, h, o);
+  if (rc != MB4_OK) {
+    mb4_batch_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MB4_OK;
+}
+
+int mb4_batch_set_state(mb4_batch* c, int instance, const double* re, const double* im, int on_device) {
+  MB4_CHECK(check_instance(c, instance, true));
+  if (!re || !im) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(ensure_scratch(c));
+  const size_t S = (size_t)c->p.S;
+  const size_t n = (instance < 0) ? S * c->B : S;
+  double2* dst = c->b.u + ((instance < 0) ? 0 : (size_t)instance * S);
+  const double *dre, *dim;
+  MB4_CHECK(stage_in(c, re, im, n, on_device, &dre, &dim));
+  launch_pack(dre, dim, dst, n, c->stream);
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int mb4_batch_get_state(const mb4_batch* cc, int instance, double* re, double* im, int on_device) {
+  mb4_batch* c = const_cast<mb4_batch*>(cc);
+  MB4_CHECK(check_instance(c, instance, true));
+  if (!re || !im) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(ensure_scratch(c));
+  const size_t S = (size_t)c->p.S;
+  const size_t n = (instance < 0) ? S * c->B : S;
+  const double2* src = c->b.u + ((instance < 0) ? 0 : (size_t)instance * S);
+  return stage_out(c, src, re, im, n, on_device);
+}
+
+int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, const double* re, const double* im,
+                   int on_device) {
+  MB4_CHECK(check_instance(c, instance, false));
+  if (!v || !re || !im || !std::isfinite(chi)) return MB4_ERR_INVALID_ARG;
+  const size_t S = (size_t)c->p.S;
+  std::vector<double> V(S), D(S);
+  if (on_device) {
+    MB4_TRY(cudaMemcpy(V.data(), v, S * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(V.data(), v, S * sizeof(double));
+  }
+  for (size_t k = 0; k < S; ++k) {
+    if (!std::isfinite(V[k])) return MB4_ERR_INVALID_ARG;
+    D[k] = c->p.eps0 + V[k];
+  }
+  InstConst ic;
+  fill_inst_const(c, chi, &ic);
+  MB4_TRY(cudaMemcpyAsync(c->b.V + (size_t)instance * S, V.data(), S * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  MB4_TRY(cudaMemcpyAsync(c->b.d + (size_t)instance * S, D.data(), S * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  MB4_TRY(cudaMemcpyAsync(c->b.ic + instance, &ic, sizeof(ic), cudaMemcpyHostToDevice, c->stream));
+  MB4_CHECK(mb4_batch_set_state(c, instance, re, im, on_device));
+  MB4_CHECK(read_status(c));
+  InstStatus fresh{};
+  fresh.enabled = 1;
+  c->host_status[instance] = fresh;
+  return write_status(c);
+}
+
+int mb4_batch_enable(mb4_batch* c, int instance, int enabled) {
+  MB4_CHECK(check_instance(c, instance, false));
+  MB4_CHECK(read_status(c));
+  c->host_status[instance].enabled = enabled ? 1 : 0;
+  return write_status(c);
+}
+
+int mb4_batch_step_async(mb4_batch* c, int nsteps) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  return step_async(c, nsteps);
+}
+
+int mb4_batch_wait(mb4_batch* c, mb4_stats* stats, int* status) {
+  if (!c) return MB4_ERR_INVALID_ARG;
+  return wait_batch(c, stats, status);
+}
+
+int mb4_batch_step(mb4_batch* c, int nsteps, mb4_stats* stats, int* status) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(step_async(c, nsteps));
+  return wait_batch(c, stats, status);
+}
+
+int mb4_batch_observables(const mb4_batch* cc, double* out) {
+  mb4_batch* c = const_cast<mb4_batch*>(cc);
+  if (!c || !out) return MB4_ERR_INVALID_ARG;
+  launch_observables(c->p, c->b, c->stream);
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaMemcpyAsync(out, c->b.obs_out, (size_t)c->B * 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int mb4_batch_clear_errors(mb4_batch* c) {
+  if (!c) return MB4_ERR_INVALID_ARG;
+  return clear_errors(c);
+}
+
+// ---- single contexts: a batch of one -------------------------------------
+
+void mb4_destroy(mb4_ctx* c) { mb4_batch_destroy(c); }
+
 int mb4_create(const mb4_grid* grid, const mb4_potential* pot, const mb4_nonlinearity* nl, double h,
                const mb4_options* opt_in, mb4_ctx** out) {
   if (!out) return MB4_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!grid || !pot || !nl || !pot->v) return MB4_ERR_INVALID_ARG;
-  if (grid->nx < 3 || grid->ny < 3) return MB4_ERR_INVALID_ARG;
-  if ((long long)grid->nx * grid->ny > (1LL << 30)) return MB4_ERR_INVALID_ARG;
+  if (!nl || !std::isfinite(nl->chi)) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(validate_grid(grid, 1));
   if (!std::isfinite(h) || h == 0.0) return MB4_ERR_INVALID_ARG;
-  if (!std::isfinite(grid->tx) || !std::isfinite(grid->ty) || !std::isfinite(grid->onsite) ||
-      !std::isfinite(nl->chi))
-    return MB4_ERR_INVALID_ARG;
   mb4_options o;
-  if (opt_in) o = *opt_in;
-  else mb4_default_options(&o);
-  if (o.precision != MB4_FP64 && o.precision != MB4_MIXED) return MB4_ERR_INVALID_ARG;
-  // Measured on GB300 at 512x512: with the update test alone the Newton loop takes
-  // 4 iterations for s >= 4, so s = 4 is cheapest; the predicted-error test cuts
-  // it to 3 from s = 5 on.
-  if (o.krylov_s == 0) o.krylov_s = (o.newton_predict > 0.0) ? 5 : 4;
-  if (o.krylov_s < 1 || o.krylov_s > MB4_MAX_KRYLOV_S) return MB4_ERR_INVALID_ARG;
-  if (!(o.newton_rtol > 0.0) || o.newton_max < 1 || !(o.newton_predict >= 0.0)) return MB4_ERR_INVALID_ARG;
-
+  MB4_CHECK(validate_options(opt_in, &o));
+  std::vector<double> V;
+  MB4_CHECK(potential_to_host(pot, (size_t)grid->nx * grid->ny, &V));
   mb4_ctx* c = new (std::nothrow) mb4_ctx();
   if (!c) return MB4_ERR_OUT_OF_MEMORY;
-  int rc = compute_constants(o.alpha1, o.c1, o.c2, &c->k);
+  const double chi = nl->chi;
+  int rc = make_batch(c, grid, 1, V.data(), &chi, h, o);
   if (rc != MB4_OK) {
-    delete c;
+    mb4_batch_destroy(c);
     return rc;
-  }
-  c->precision = o.precision;
-  c->use_graph = o.use_graph ? 1 : 0;
-  c->stream = (cudaStream_t)o.stream;
-  c->tk = (o.precision == MB4_MIXED) ? sizeof(float) : sizeof(double);
-  if (cudaGetDevice(&c->device) != cudaSuccess) {
-    delete c;
-    return MB4_ERR_CUDA;
-  }
-  const int nx = grid->nx, ny = grid->ny;
-  const size_t S = (size_t)nx * ny;
-
-  // Potential on the host (to derive d = onsite + V and the Krylov scale).
-  std::vector<double> V(S);
-  if (pot->on_device) {
-    if (cudaMemcpy(V.data(), pot->v, S * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      delete c;
-      return MB4_ERR_CUDA;
-    }
-  } else {
-    std::memcpy(V.data(), pot->v, S * sizeof(double));
-  }
-  double vmax = 0.0;
-  for (size_t k = 0; k < S; ++k) {
-    if (!std::isfinite(V[k])) {
-      delete c;
-      return MB4_ERR_INVALID_ARG;
-    }
-    vmax = std::fmax(vmax, std::fabs(grid->onsite + V[k]));
-  }
-  std::vector<double> D(S);
-  for (size_t k = 0; k < S; ++k) D[k] = grid->onsite + V[k];
-
-  // Kernel constants.
-  StepParams& p = c->p;
-  const Constants& K = c->k;
-  p.nx = nx;
-  p.ny = ny;
-  p.S = (int)S;
-  p.s = o.krylov_s;
-  p.tx = grid->tx;
-  p.ty = grid->ty;
-  p.eps0 = grid->onsite;
-  p.chi = nl->chi;
-  p.h = h;
-  for (int i = 0; i < 3; ++i) {
-    p.hlam[i] = h * K.lam[i];
-    double e0 = 0, tau = 0, tc = 0;
-    for (int j = 0; j < 3; ++j) {
-      e0 += K.Tinv[i][j] * K.E[j][0];
-      tau += K.Tinv[i][j];
-      tc += K.Tinv[i][j] * K.c[j];
-    }
-    p.he0[i] = h * e0;
-    p.tau[i] = tau;
-    p.hTc[i] = h * tc;
-    for (int j = 0; j < 3; ++j) p.T[i][j] = K.T[i][j];
-  }
-  for (int q = 0; q < kGauss; ++q) {
-    const double z = K.gx[q];
-    double l[4];
-    for (int j = 0; j < 4; ++j) l[j] = ((K.lag[j][3] * z + K.lag[j][2]) * z + K.lag[j][1]) * z + K.lag[j][0];
-    p.L0[q] = l[0];
-    for (int n = 0; n < 3; ++n) {
-      double s = 0;
-      for (int m = 0; m < 3; ++m) s += l[m + 1] * K.T[m][n];
-      p.LT[q][n] = s;
-    }
-    double W[3];
-    for (int j = 0; j < 3; ++j) W[j] = K.gw[q] * ((K.Acoef[j][2] * z + K.Acoef[j][1]) * z + K.Acoef[j][0]);
-    for (int i = 0; i < 3; ++i) {
-      double s = 0;
-      for (int j = 0; j < 3; ++j) s += K.Tinv[i][j] * W[j];
-      p.hchiW[i][q] = h * nl->chi * s;
-    }
-  }
-  double theta = vmax + 2.0 * std::fabs(grid->tx) + 2.0 * std::fabs(grid->ty);
-  if (!(theta > 0.0)) theta = 1.0;
-  p.inv_theta = 1.0 / theta;
-  for (int i = 0; i < 3; ++i) p.sig[i] = h * K.lam[i] * theta;
-  p.newton_rtol = o.newton_rtol;
-  p.newton_predict = o.newton_predict;
-  p.newton_max = o.newton_max;
-  p.chi_theta = nl->chi / theta;
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) p.fT[i][j] = (float)p.T[i][j];
-    p.f_hTc[i] = (float)p.hTc[i];
-  }
-  p.f_inv_theta = (float)p.inv_theta;
-  p.f_chi_theta = (float)p.chi_theta;
-  p.f_chi = (float)p.chi;
-  p.f_txt = (float)(p.tx * p.inv_theta);
-  p.f_tyt = (float)(p.ty * p.inv_theta);
-  p.trunc_rel = (o.precision == MB4_MIXED) ? 1e-12f : 1e-26f;
-  p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s) : gram_blocks_per_system<double>(p.s);
-  if (p.gram_blocks < 1) {
-    delete c;
-    return MB4_ERR_CUDA;
-  }
-  p.use_powers = (o.precision == MB4_MIXED) ? 1 : 0;
-  if (p.use_powers && prepare_powers() != MB4_OK) {
-    delete c;
-    return MB4_ERR_CUDA;
-  }
-
-  // Device buffers.
-  DevBuffers& b = c->b;
-  const size_t tk = c->tk;
-  const int nent = (p.s + 1) * (p.s + 2) / 2;
-  if ((rc = dalloc(c, (void**)&b.u, S * sizeof(double2))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.V, S * sizeof(double))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.d, S * sizeof(double))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.S0, S * sizeof(double2))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.Ubar, 3 * S * sizeof(double2))) != MB4_OK ||
-      (rc = dalloc(c, &b.jc, S * 4 * tk)) != MB4_OK ||
-      (rc = dalloc(c, &b.v, (size_t)(p.s + 1) * 3 * S * 2 * tk)) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.gram_part, (size_t)3 * kGramBlocks * nent * sizeof(double))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.coef, 3 * kMaxS * sizeof(double))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.obs_part, 304 * 6 * 2 * sizeof(double))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.obs_out, 16 * sizeof(double))) != MB4_OK ||
-      (rc = dalloc(c, (void**)&b.status, sizeof(DevStatus))) != MB4_OK) {
-    mb4_destroy(c);
-    return rc;
-  }
-  if ((rc = cuda_rc(cudaMemcpyAsync(b.V, V.data(), S * sizeof(double), cudaMemcpyHostToDevice, c->stream))) ||
-      (rc = cuda_rc(cudaMemcpyAsync(b.d, D.data(), S * sizeof(double), cudaMemcpyHostToDevice, c->stream))) ||
-      (rc = cuda_rc(cudaMemsetAsync(b.u, 0, S * sizeof(double2), c->stream))) ||
-      (rc = cuda_rc(cudaMemsetAsync(b.Ubar, 0, 3 * S * sizeof(double2), c->stream))) ||
-      (rc = cuda_rc(cudaMemsetAsync(b.coef, 0, 3 * kMaxS * sizeof(double), c->stream))) ||
-      (rc = reset_status(c)) || (rc = cuda_rc(cudaStreamSynchronize(c->stream)))) {
-    mb4_destroy(c);
-    return rc;
-  }
-  if (c->use_graph) {
-    if ((rc = build_graph(c)) != MB4_OK) {
-      mb4_destroy(c);
-      return rc;
-    }
   }
   *out = c;
   return MB4_OK;
 }
 
 int mb4_set_state(mb4_ctx* c, const double* re, const double* im, int on_device) {
-  if (!c || !re || !im) return MB4_ERR_INVALID_ARG;
-  int rc;
-  if ((rc = ensure_scratch(c)) != MB4_OK) return rc;
-  const size_t S = (size_t)c->p.S;
-  const double *dre, *dim;
-  if ((rc = stage_in(c, re, im, S, on_device, &dre, &dim)) != MB4_OK) return rc;
-  launch_pack(dre, dim, c->b.u, (int)S, c->stream);
-  MB4_TRY(cudaGetLastError());
-  MB4_TRY(cudaStreamSynchronize(c->stream));
-  return MB4_OK;
+  return mb4_batch_set_state(c, 0, re, im, on_device);
 }
 
-int mb4_get_state(const mb4_ctx* cc, double* re, double* im, int on_device) {
-  mb4_ctx* c = const_cast<mb4_ctx*>(cc);
-  if (!c || !re || !im) return MB4_ERR_INVALID_ARG;
-  int rc;
-  if ((rc = ensure_scratch(c)) != MB4_OK) return rc;
-  return stage_out(c, c->b.u, re, im, (size_t)c->p.S, on_device);
+int mb4_get_state(const mb4_ctx* c, double* re, double* im, int on_device) {
+  return mb4_batch_get_state(c, 0, re, im, on_device);
 }
 
 int mb4_get_stages(const mb4_ctx* cc, double* re3, double* im3, int on_device) {
   mb4_ctx* c = const_cast<mb4_ctx*>(cc);
   if (!c || !re3 || !im3) return MB4_ERR_INVALID_ARG;
-  int rc;
-  if ((rc = ensure_scratch(c)) != MB4_OK) return rc;
+  MB4_CHECK(ensure_scratch(c));
   launch_mix3(c->p.S, c->b.Ubar, c->tmp3a, c->p.T, c->stream);
   MB4_TRY(cudaGetLastError());
-  // the io buffer holds 6*S doubles: enough for 3*S re + 3*S im
   return stage_out(c, c->tmp3a, re3, im3, 3 * (size_t)c->p.S, on_device);
 }
 
 int mb4_step(mb4_ctx* c, int nsteps, mb4_stats* stats) {
   if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  int rc0 = reset_status(c);
-  if (rc0 != MB4_OK) return rc0;
-  if (c->use_graph) {
-    for (int n = 0; n < nsteps; ++n) MB4_TRY(cudaGraphLaunch(c->exec, c->stream));
+  MB4_CHECK(clear_errors(c));   // every call starts from the last accepted state
+  MB4_CHECK(step_async(c, nsteps));
+  return wait_batch(c, stats, nullptr);
+}
+
+int mb4_observables(const mb4_ctx* c, double* out6) { return mb4_batch_observables(c, out6); }
+
+int mb4_energy(const mb4_ctx* c, double* H, double* parts3) {
+  if (!c || !H) return MB4_ERR_INVALID_ARG;
+  double o[6];
+  MB4_CHECK(mb4_observables(c, o));
+  *H = o[0];
+  if (parts3) {
+    parts3[0] = o[1];
+    parts3[1] = o[2];
+    parts3[2] = o[3];
+  }
+  return MB4_OK;
+}
+
+int mb4_norm(const mb4_ctx* c, double* norm2) {
+  if (!c || !norm2) return MB4_ERR_INVALID_ARG;
+  double o[6];
+  MB4_CHECK(mb4_observables(c, o));
+  *norm2 = o[4];
+  return MB4_OK;
+}
+
+int mb4_residual(mb4_ctx* c, const double* u0_re, const double* u0_im, const double* U_re3, const double* U_im3,
+                 double* phi_re3, double* phi_im3, int on_device) {
+  if (!c || !u0_re || !u0_im || !U_re3 || !U_im3 || !phi_re3 || !phi_im3) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(mb4_set_state(c, u0_re, u0_im, on_device));
+  MB4_CHECK(clear_errors(c));
+  const size_t S = (size_t)c->p.S;
+  launch_arm(c->p, c->b, c->stream);
+  enqueue_setup(c, c->stream);
+  const double *dre, *dim;
+  MB4_CHECK(stage_in(c, U_re3, U_im3, 3 * S, on_device, &dre, &dim));
+  launch_pack(dre, dim, c->tmp3a, 3 * S, c->stream);
+  launch_mix3((int)S, c->tmp3a, c->b.Ubar, c->k.Tinv, c->stream);
+  if (c->precision == MB4_MIXED) launch_residual_out<float>(c->p, c->b, c->tmp3b, c->stream);
+  else launch_residual_out<double>(c->p, c->b, c->tmp3b, c->stream);
+  // Phi = T Phibar = -T b
+  double mT[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) mT[i][j] = -c->k.T[i][j];
+  launch_mix3((int)S, c->tmp3b, c->tmp3a, mT, c->stream);
+  MB4_TRY(cudaGetLastError());
+  return stage_out(c, c->tmp3a, phi_re3, phi_im3, 3 * S, on_device);
+}
+
+int mb4_solve_shifted(mb4_ctx* c, const double* u0_re, const double* u0_im, const double* b_re3,
+                      const double* b_im3, double* x_re3, double* x_im3, int on_device) {
+  if (!c || !u0_re || !u0_im || !b_re3 || !b_im3 || !x_re3 || !x_im3) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(mb4_set_state(c, u0_re, u0_im, on_device));
+  MB4_CHECK(clear_errors(c));
+  const size_t S = (size_t)c->p.S;
+  launch_arm(c->p, c->b, c->stream);
+  enqueue_setup(c, c->stream);
+  const double *dre, *dim;
+  MB4_CHECK(stage_in(c, b_re3, b_im3, 3 * S, on_device, &dre, &dim));
+  launch_pack(dre, dim, c->tmp3a, 3 * S, c->stream);
+  if (c->precision == MB4_MIXED) {
+    launch_copy_rhs_in<float>(c->p, c->b, c->tmp3a, c->stream);
+    launch_krylov<float>(c->p, c->b, c->stream);
+    launch_copy_solution_out<float>(c->p, c->b, c->tmp3b, c->stream);
   } else {
-    for (int n = 0; n < nsteps; ++n) {
-      enqueue_setup(c, c->stream);
-      DevStatus hs;
-      for (;;) {
-        enqueue_body(c, c->stream, 0ull, 0);
-        MB4_TRY(cudaGetLastError());
-        MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
-        MB4_TRY(cudaStreamSynchronize(c->stream));
-        if (hs.error || !hs.cont) break;
-      }
-      launch_accept(c->p, c->b, c->stream);
-      if (hs.error) break;
-    }
+    launch_copy_rhs_in<double>(c->p, c->b, c->tmp3a, c->stream);
+    launch_krylov<double>(c->p, c->b, c->stream);
+    launch_copy_solution_out<double>(c->p, c->b, c->tmp3b, c->stream);
   }
   MB4_TRY(cudaGetLastError());
-  DevStatus hs;
-  MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
-  MB4_TRY(cudaStreamSynchronize(c->stream));
-  if (stats) {
-    stats->steps_done = hs.steps_done;
-    stats->newton_iters_total = hs.newton_total;
-    stats->newton_iters_last = hs.last_newton_iters;
-    stats->last_update_inf = hs.last_rmax;
-    stats->u0_inf = hs.last_u0max;
-    for (int l = 0; l < 8; ++l) stats->update_hist[l] = (l < hs.last_newton_iters) ? hs.hist[l] : 0.0;
-  }
-  return hs.error;
+  return stage_out(c, c->tmp3b, x_re3, x_im3, 3 * S, on_device);
 }
 
 }  // extern "C"
+
+// ---- profiling: the step with an event pair around every launch -----------
 
 namespace {
 
@@ -504,24 +780,24 @@ struct Prof {
 };
 
 template <typename TK>
-int profiled_steps(mb4_ctx* c, int nsteps, Prof& P) {
+int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
   cudaStream_t s = c->stream;
+  launch_arm(c->p, c->b, s);
   for (int n = 0; n < nsteps; ++n) {
     P.run(MB4_K_SETUP, 1, [&] { launch_setup<TK>(c->p, c->b, s); });
-    DevStatus hs;
     for (;;) {
       P.run(MB4_K_RESIDUAL, 1, [&] { launch_residual<TK>(c->p, c->b, true, s); });
       P.run(MB4_K_MATVEC, c->p.s, [&] { launch_matvecs<TK>(c->p, c->b, s); });
       P.run(MB4_K_GRAM, 1, [&] { launch_gram<TK>(c->p, c->b, s); });
       P.run(MB4_K_UPDATE, 1, [&] { launch_update<TK>(c->p, c->b, 0ull, 0, s); });
       MB4_TRY(cudaGetLastError());
-      MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      BatchCtl bc;
+      MB4_TRY(cudaMemcpyAsync(&bc, c->b.bc, sizeof(bc), cudaMemcpyDeviceToHost, s));
       MB4_TRY(cudaStreamSynchronize(s));
       P.harvest();
-      if (hs.error || !hs.cont) break;
+      if (!bc.any_cont) break;
     }
     P.run(MB4_K_ACCEPT, 1, [&] { launch_accept(c->p, c->b, s); });
-    if (hs.error) break;
   }
   MB4_TRY(cudaStreamSynchronize(s));
   P.harvest();
@@ -530,113 +806,16 @@ int profiled_steps(mb4_ctx* c, int nsteps, Prof& P) {
 
 }  // namespace
 
-extern "C" {
-
-int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches) {
+extern "C" int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches) {
   if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  int rc = reset_status(c);
-  if (rc != MB4_OK) return rc;
+  MB4_CHECK(clear_errors(c));
   Prof P;
   P.s = c->stream;
-  rc = (c->precision == MB4_MIXED) ? profiled_steps<float>(c, nsteps, P) : profiled_steps<double>(c, nsteps, P);
-  if (rc != MB4_OK) return rc;
+  MB4_CHECK((c->precision == MB4_MIXED) ? profiled_steps<float>(c, nsteps, P) : profiled_steps<double>(c, nsteps, P));
   for (int k = 0; k < MB4_K_COUNT; ++k) {
     if (ms) ms[k] += P.ms[k];
     if (launches) launches[k] += P.n[k];
   }
-  DevStatus hs;
-  MB4_TRY(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
-  MB4_TRY(cudaStreamSynchronize(c->stream));
-  if (stats) {
-    stats->steps_done = hs.steps_done;
-    stats->newton_iters_total = hs.newton_total;
-    stats->newton_iters_last = hs.last_newton_iters;
-    stats->last_update_inf = hs.last_rmax;
-    stats->u0_inf = hs.last_u0max;
-    for (int l = 0; l < 8; ++l) stats->update_hist[l] = (l < hs.last_newton_iters) ? hs.hist[l] : 0.0;
-  }
-  return hs.error;
+  return wait_batch(c, stats, nullptr);
 }
-
-int mb4_observables(const mb4_ctx* cc, double* out6) {
-  mb4_ctx* c = const_cast<mb4_ctx*>(cc);
-  if (!c || !out6) return MB4_ERR_INVALID_ARG;
-  launch_observables(c->p, c->b, c->stream);
-  MB4_TRY(cudaGetLastError());
-  MB4_TRY(cudaMemcpyAsync(out6, c->b.obs_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  MB4_TRY(cudaStreamSynchronize(c->stream));
-  return MB4_OK;
-}
-
-int mb4_energy(const mb4_ctx* c, double* H, double* parts3) {
-  if (!c || !H) return MB4_ERR_INVALID_ARG;
-  double o[6];
-  int rc = mb4_observables(c, o);
-  if (rc != MB4_OK) return rc;
-  *H = o[0];
-  if (parts3) {
-    parts3[0] = o[1];
-    parts3[1] = o[2];
-    parts3[2] = o[3];
-  }
-  return MB4_OK;
-}
-
-int mb4_norm(const mb4_ctx* c, double* norm2) {
-  if (!c || !norm2) return MB4_ERR_INVALID_ARG;
-  double o[6];
-  int rc = mb4_observables(c, o);
-  if (rc != MB4_OK) return rc;
-  *norm2 = o[4];
-  return MB4_OK;
-}
-
-int mb4_residual(mb4_ctx* c, const double* u0_re, const double* u0_im, const double* U_re3, const double* U_im3,
-                 double* phi_re3, double* phi_im3, int on_device) {
-  if (!c || !u0_re || !u0_im || !U_re3 || !U_im3 || !phi_re3 || !phi_im3) return MB4_ERR_INVALID_ARG;
-  int rc;
-  if ((rc = mb4_set_state(c, u0_re, u0_im, on_device)) != MB4_OK) return rc;
-  const size_t S = (size_t)c->p.S;
-  if ((rc = reset_status(c)) != MB4_OK) return rc;
-  enqueue_setup(c, c->stream);
-  const double *dre, *dim;
-  if ((rc = stage_in(c, U_re3, U_im3, 3 * S, on_device, &dre, &dim)) != MB4_OK) return rc;
-  launch_pack(dre, dim, c->tmp3a, (int)(3 * S), c->stream);
-  launch_mix3((int)S, c->tmp3a, c->b.Ubar, c->k.Tinv, c->stream);
-  if (c->precision == MB4_MIXED) launch_residual_out<float>(c->p, c->b, c->tmp3b, c->stream);
-  else launch_residual_out<double>(c->p, c->b, c->tmp3b, c->stream);
-  // Phi = T Phibar = -T b
-  double mT[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) mT[i][j] = -c->k.T[i][j];
-  launch_mix3((int)S, c->tmp3b, c->tmp3a, mT, c->stream);
-  MB4_TRY(cudaGetLastError());
-  return stage_out(c, c->tmp3a, phi_re3, phi_im3, 3 * S, on_device);
-}
-
-int mb4_solve_shifted(mb4_ctx* c, const double* u0_re, const double* u0_im, const double* b_re3,
-                      const double* b_im3, double* x_re3, double* x_im3, int on_device) {
-  if (!c || !u0_re || !u0_im || !b_re3 || !b_im3 || !x_re3 || !x_im3) return MB4_ERR_INVALID_ARG;
-  int rc;
-  if ((rc = mb4_set_state(c, u0_re, u0_im, on_device)) != MB4_OK) return rc;
-  const size_t S = (size_t)c->p.S;
-  if ((rc = reset_status(c)) != MB4_OK) return rc;
-  enqueue_setup(c, c->stream);
-  const double *dre, *dim;
-  if ((rc = stage_in(c, b_re3, b_im3, 3 * S, on_device, &dre, &dim)) != MB4_OK) return rc;
-  launch_pack(dre, dim, c->tmp3a, (int)(3 * S), c->stream);
-  if (c->precision == MB4_MIXED) {
-    launch_copy_rhs_in<float>(c->p, c->b, c->tmp3a, c->stream);
-    launch_krylov<float>(c->p, c->b, c->stream);
-    launch_copy_solution_out<float>(c->p, c->b, c->tmp3b, c->stream);
-  } else {
-    launch_copy_rhs_in<double>(c->p, c->b, c->tmp3a, c->stream);
-    launch_krylov<double>(c->p, c->b, c->stream);
-    launch_copy_solution_out<double>(c->p, c->b, c->tmp3b, c->stream);
-  }
-  MB4_TRY(cudaGetLastError());
-  return stage_out(c, c->tmp3b, x_re3, x_im3, 3 * S, on_device);
-}
-
-}  // extern "C"

@@ -12,8 +12,9 @@ namespace mb4 {
 
 constexpr int kGauss = 6;          // Gauss-Legendre nodes: exact for the degree-11 integrand of eq. (fIu2)
 constexpr int kMaxS = MB4_MAX_KRYLOV_S;
-constexpr int kGramBlocks = 304;   // upper bound on the Gram blocks per shifted system
-constexpr int kGramCap = 96;       // Gram blocks per system actually used (at most)
+constexpr int kGramCap = 96;       // Gram blocks per (instance, system), at most
+constexpr int kObsBlocksTotal = 304;   // observables: blocks over the whole batch
+constexpr int kObsBlocksMax = 304;     // ... and per instance, at most
 
 // MB4 constants in FP64, computed on the host (mb4_consts.cpp).
 struct Constants {
@@ -30,14 +31,14 @@ struct Constants {
 // Returns 0 or an MB4_ERR_* code (alpha1 out of range, bad nodes).
 int compute_constants(double alpha1, double c1, double c2, Constants* out);
 
-// Everything a kernel needs, passed by value (kernel parameter space), so that
-// several contexts with different h, grids or potentials can coexist.
+// Constants shared by every instance of a batch (one grid shape and h), passed
+// by value in kernel parameter space.
 struct StepParams {
-  int nx, ny, S;
+  int nx, ny, S, B;
   int s;                   // Krylov subspace dimension
-  int gram_blocks;         // Gram blocks per shifted system (one wave over all SMs)
+  int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
-  double tx, ty, eps0, chi, h;
+  double tx, ty, eps0, h;
   // residual in the eigenbasis of E: Ubar = Tinv U
   double hlam[3];          // h * lambda_i
   double he0[3];           // h * (Tinv E_{.0})_i
@@ -45,56 +46,76 @@ struct StepParams {
   double hTc[3];           // h * (Tinv c)_i : Phibar^0 = i hTc_i f-part at u0
   double L0[kGauss];       // l_0(zeta_q)
   double LT[kGauss][3];    // sum_m l_m(zeta_q) T[m][n]
-  double hchiW[3][kGauss]; // h chi (Tinv W)_iq, W_jq = w_q A_{c_j}(zeta_q)
   double T[3][3];          // r = T rbar ;  u1 = sum_n T[2][n] Ubar_n
   // Krylov (monomial basis of J/theta)
   double inv_theta;        // 1 / theta
+  double txt, tyt;         // tx / theta, ty / theta
   double sig[3];           // h lambda_i theta
   double newton_rtol;
   double newton_predict;   // 0: off; else Hairer-Wanner predicted-error stop
   int newton_max;
   float trunc_rel;         // relative pivot threshold of the Gram Cholesky
-  double chi_theta;        // chi / theta
   // FP32 copies of uniform constants (no per-thread conversions on the FP64 pipe)
-  float fT[3][3];          // T
-  float f_inv_theta, f_chi_theta, f_chi;
+  float fT[3][3];
+  float f_inv_theta;
   float f_hTc[3];
-  float f_txt, f_tyt;      // tx / theta, ty / theta
+  float f_txt, f_tyt;
 };
 
-// Device-resident control block of one context.
-struct DevStatus {
+// Per-instance constants (device array of B).
+struct InstConst {
+  double hchiW[3][kGauss]; // h chi (Tinv W)_iq, W_jq = w_q A_{c_j}(zeta_q)
+  double chi, chi_theta;
+  float f_chi, f_chi_theta;
+};
+
+// Per-instance Newton status (device array of B).
+struct InstStatus {
   int error;                         // MB4_OK or MB4_ERR_*
+  int enabled;                       // set by the host: step this instance
+  int in_step;                       // takes part in the current step
+  int active;                        // still iterating in the current step
   int newton_iter;                   // iterations of the current step
   int nonfinite;                     // set by update kernels
+  int cont;
   int last_newton_iters;
-  long long steps_done;              // accepted steps since the last reset
-  long long newton_total;
-  unsigned long long rmax_bits;      // max |r| of the current iteration (double bits, >= 0)
   unsigned int u0max_bits;           // ||u0||_inf of the current step (float bits, >= 0)
-  double last_rmax;
-  double last_u0max;
-  int cont;                          // 1 while the Newton loop of the current step goes on
   unsigned int ticket_gram;          // last-block tickets (reset by the last block)
   unsigned int ticket_update;
+  unsigned int pad0;
+  unsigned long long rmax_bits;      // max |r| of the current iteration (double bits, >= 0)
+  long long steps_done;              // accepted steps since the last reset
+  long long newton_total;
   double prev_rmax;                  // ||r^(l-1)||_inf
+  double last_rmax;
+  double last_u0max;
   double hist[8];                    // ||r^l||_inf of the current step
 };
 
-// Device buffers of one context.
+// Batch-wide loop control.
+struct BatchCtl {
+  unsigned int ticket_inst;          // instances that finished the current update
+  int n_cont;                        // of which continue
+  int any_cont;
+  int pad;
+};
+
+// Device buffers of one batch.
 struct DevBuffers {
-  double2* u;        // state, S
-  double* V;         // potential, S
-  double* d;         // onsite + V, S
-  double2* S0;       // (K+V) u0, S
-  double2* Ubar;     // transformed stages, 3*S
-  void* jc;          // J coefficients {e1, e2, a, 0} (TK4), S
-  void* v;           // Krylov basis, (s+1)*3*S of TK2; v[0] = right-hand side b
-  double* gram_part; // 3 * kGramBlocks * nent
-  double* coef;      // 3 * kMaxS LSQ coefficients
+  double2* u;        // state, B*S
+  double* V;         // potential, B*S
+  double* d;         // onsite + V, B*S
+  double2* S0;       // (K+V) u0, B*S
+  double2* Ubar;     // transformed stages, B*3*S
+  void* jc;          // J coefficients {e1, e2, a, 0} (TK4), B*S
+  void* v;           // Krylov basis, B*(s+1)*3*S of TK2; level 0 = right-hand side b
+  double* gram_part; // B*3*gram_blocks*nent
+  double* coef;      // B*3*kMaxS least-squares coefficients
   double* obs_part;  // observables partial sums
-  double* obs_out;   // 12 doubles (6 hi/lo pairs reduced)
-  DevStatus* status;
+  double* obs_out;   // B*6
+  InstConst* ic;     // B
+  InstStatus* is;    // B
+  BatchCtl* bc;
 };
 
 // Host launchers (mb4_kernels.cu).  TK = float (mixed) or double (fp64).
@@ -107,12 +128,14 @@ template <typename TK> void launch_matvecs(const StepParams& p, const DevBuffers
 template <typename TK> void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 // Raise the dynamic shared-memory limit of the matrix-powers kernels (once per process/device).
 int prepare_powers();
-// Blocks per system that make the Gram kernel a single wave on this device (0 on error).
-template <typename TK> int gram_blocks_per_system(int s_dim);
+// Blocks per (instance, system) that make the Gram kernel about one wave (0 on error).
+template <typename TK> int gram_blocks_per_system(int s_dim, int B);
 // Newton update and loop test; cond_handle drives the graph's WHILE node when use_cond.
 template <typename TK> void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long cond_handle,
                                           int use_cond, cudaStream_t st);
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+int obs_blocks_per_instance(int B);
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 // Y_j = sum_n M[j][n] X_n on three complex planes of S sites.
 void launch_mix3(int S, const double2* X, double2* Y, const double M[3][3], cudaStream_t st);
@@ -122,7 +145,7 @@ template <typename TK> void launch_copy_solution_out(const StepParams& p, const 
                                                      double2* x3, cudaStream_t st);
 template <typename TK> void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3,
                                                 cudaStream_t st);
-void launch_pack(const double* re, const double* im, double2* z, int n, cudaStream_t st);
-void launch_unpack(const double2* z, double* re, double* im, int n, cudaStream_t st);
+void launch_pack(const double* re, const double* im, double2* z, size_t n, cudaStream_t st);
+void launch_unpack(const double2* z, double* re, double* im, size_t n, cudaStream_t st);
 
 }  // namespace mb4

@@ -1,10 +1,14 @@
-// libmb4 kernels: one MB4 step on the device (sm_103a).
+// libmb4 kernels: MB4 steps for a batch of B independent instances of one grid
+// shape on the device (sm_103a).  A single context is a batch of one.
 //
-// Data layout: complex planes are interleaved (re, im) pairs, site k = y*nx + x.
-// The Newton iteration runs in the eigenbasis of E (Ubar = T^-1 U, Sec. 2.2,
-// eq. MB4_4..MB4_6): the T and T^-1 mixes of Algorithm 1 then fold into
-// per-context constants, the linear part of the residual needs only one
-// stencil per stage (T^-1 E T = Lambda), and the update is Ubar += rbar.
+// Data layout: complex planes are interleaved (re, im) pairs, site k = y*nx + x;
+// every per-instance array is instance-major (instance b's planes are
+// contiguous).  The Newton iteration runs in the eigenbasis of E
+// (Ubar = T^-1 U, Sec. 2.2, eq. MB4_4..MB4_6): the T and T^-1 mixes of
+// Algorithm 1 then fold into constants, the linear part of the residual needs
+// only one stencil per stage (T^-1 E T = Lambda), and the update is
+// Ubar += rbar.  Each instance keeps its own Newton status; an instance that
+// has converged (or failed) is masked while the others iterate.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -98,6 +102,13 @@ template <typename T> __device__ __forceinline__ float to_float(T x);
 template <> __device__ __forceinline__ float to_float<float>(float x) { return x; }
 template <> __device__ __forceinline__ float to_float<double>(double x) { return d2f_trunc(x); }
 
+// Offsets of instance b's data.
+__device__ __forceinline__ size_t plane(int b, int S) { return (size_t)b * S; }
+__device__ __forceinline__ size_t stage(int b, int m, int S) { return ((size_t)b * 3 + m) * S; }
+__device__ __forceinline__ size_t level(int b, int a, int i, int s, int S) {
+  return (((size_t)b * (s + 1) + a) * 3 + i) * S;
+}
+
 // ---------------------------------------------------------------------------
 // Step set-up (Algorithm 1 lines 7-9 and the first residual): u0 = u(t); J at u0
 // as per-site coefficients; (K+V) u0; ||u0||_inf.  At U^0 = e3 (x) u0 every stage
@@ -105,38 +116,41 @@ template <> __device__ __forceinline__ float to_float<double>(double x) { return
 // right-hand side is b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].
 // J and b^0 only feed the Krylov solve, so they are formed in its precision TK;
 // (K+V) u0 is reused by every residual and stays FP64.  Ubar^0 = tau (x) u0 is
-// formed by the first update.
+// formed by the first update.  Grid: (sites / 256, B).
 // ---------------------------------------------------------------------------
 template <typename TK>
 __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
-                                               JCoef<TK>* __restrict__ jc,
-                                               typename Vec2<TK>::type* __restrict__ v0, DevStatus* st) {
-  if (st->error) return;
+                                               JCoef<TK>* __restrict__ jc, typename Vec2<TK>::type* __restrict__ v,
+                                               const InstConst* __restrict__ ic, InstStatus* is) {
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
   typedef typename Vec2<TK>::type TK2;
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const InstConst& C = ic[b];
   float m = 0.f;
   if (k < S) {
     Nbr n = neighbours(k, p.nx, p.ny, S);
-    double2 c = u[k];
-    double2 a = u[n.xm], bb = u[n.xp], e = u[n.ym], f = u[n.yp];
-    double d = D[k];
+    const double2* ub = u + plane(b, S);
+    double2 c = ub[k];
+    double2 a = ub[n.xm], bb = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
+    double d = D[plane(b, S) + k];
     double2 s0;
     s0.x = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
     s0.y = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
-    S0[k] = s0;
+    S0[plane(b, S) + k] = s0;
     const TK pk = from_double<TK>(c.x), qk = from_double<TK>(c.y);
     const TK pp = pk * pk, qq = qk * qk, nn = pp + qq;
     const TK dt = from_double<TK>(d) * kval<TK>(p.inv_theta, p.f_inv_theta);
-    const TK ct = kval<TK>(p.chi_theta, p.f_chi_theta);
+    const TK ct = kval<TK>(C.chi_theta, C.f_chi_theta);
     JCoef<TK> j;
     j.e1 = dt + ct * (pp + (TK)3 * qq);
     j.e2 = dt + ct * ((TK)3 * pp + qq);
     j.a = (TK)2 * ct * pk * qk;
     j.pad = (TK)0;
-    jc[k] = j;
-    const TK cn = kval<TK>(p.chi, p.f_chi) * nn;
+    jc[plane(b, S) + k] = j;
+    const TK cn = kval<TK>(C.chi, C.f_chi) * nn;
     const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -144,19 +158,19 @@ __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __re
       const TK hc = kval<TK>(p.hTc[i], p.f_hTc[i]);
       bi.x = hc * Fy;
       bi.y = -hc * Fx;
-      v0[(size_t)i * S + k] = bi;
+      v[level(b, 0, i, p.s, S) + k] = bi;
     }
     m = fmaxf(absf_of(c.x), absf_of(c.y));
   }
   m = warp_max(m);
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&st->u0max_bits, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&is[b].u0max_bits, __float_as_uint(m));
 }
 
 template <typename TK>
 void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  int blocks = (p.S + 255) / 256;
-  k_setup<TK><<<blocks, 256, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
-                                     b.status);
+  dim3 grid((p.S + 255) / 256, p.B);
+  k_setup<TK><<<grid, 256, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v, b.ic,
+                                   b.is);
 }
 
 // ---------------------------------------------------------------------------
@@ -171,25 +185,28 @@ template <typename TO>
 __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
                                                   const double2* __restrict__ Ubar,
-                                                  typename Vec2<TO>::type* __restrict__ out, int skip_first,
-                                                  const DevStatus* st) {
-  if (st->error) return;
-  if (skip_first && st->newton_iter == 0) return;   // b^0 was written by k_setup
+                                                  typename Vec2<TO>::type* __restrict__ out, long long out_stride,
+                                                  int skip_first, const InstConst* __restrict__ ic,
+                                                  const InstStatus* is) {
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
+  if (skip_first && is[b].newton_iter == 0) return;   // b^0 was written by k_setup
   typedef typename Vec2<TO>::type TO2;
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S) return;
+  const InstConst& C = ic[b];
   Nbr n = neighbours(k, p.nx, p.ny, S);
-  const double2 u0 = u[k];
-  const double2 s0 = S0[k];
-  const double d = D[k];
+  const double2 u0 = u[plane(b, S) + k];
+  const double2 s0 = S0[plane(b, S) + k];
+  const double d = D[plane(b, S) + k];
   // dU_m = Ubar_m - tau_m u0: the departure of the stages from the trivial guess.
   // The stage polynomial at node q is then X_q = u0 + sum_m (L T)_qm dU_m (since
   // l_0(zeta) + sum_m (L T)_qm tau_m = 1), and b_i = -dU_i + i-rotated sums.
   double2 dU[3], acc[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    const double2* P = Ubar + (size_t)m * S;
+    const double2* P = Ubar + stage(b, m, S);
     double2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
     dU[m].x = fma(-p.tau[m], u0.x, c.x);
     dU[m].y = fma(-p.tau[m], u0.y, c.y);
@@ -209,30 +226,32 @@ __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* _
     const double gx = nn * Xx, gy = nn * Xy;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      acc[i].x = fma(p.hchiW[i][q], gx, acc[i].x);
-      acc[i].y = fma(p.hchiW[i][q], gy, acc[i].y);
+      acc[i].x = fma(C.hchiW[i][q], gx, acc[i].x);
+      acc[i].y = fma(C.hchiW[i][q], gy, acc[i].y);
     }
   }
+  TO2* ob = out + (size_t)b * (size_t)out_stride;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     TO2 o;
     o.x = from_double<TO>(acc[i].y - dU[i].x);
     o.y = from_double<TO>(-acc[i].x - dU[i].y);
-    out[(size_t)i * S + k] = o;
+    ob[(size_t)i * S + k] = o;
   }
 }
 
 template <typename TK>
 void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, cudaStream_t s) {
-  int blocks = (p.S + 255) / 256;
-  k_residual<TK><<<blocks, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
-                                        skip_first ? 1 : 0, b.status);
+  dim3 grid((p.S + 255) / 256, p.B);
+  // b_i of instance b goes to its level 0: level(b, 0, i) = b*(s+1)*3*S + i*S
+  k_residual<TK><<<grid, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
+                                      (long long)(p.s + 1) * 3 * p.S, skip_first ? 1 : 0, b.ic, b.is);
 }
 
 template <typename TK>
 void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3, cudaStream_t s) {
-  int blocks = (p.S + 255) / 256;
-  k_residual<double><<<blocks, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 0, b.status);
+  dim3 grid((p.S + 255) / 256, p.B);
+  k_residual<double><<<grid, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.ic, b.is);
 }
 
 // ---------------------------------------------------------------------------
@@ -244,26 +263,27 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 // ---------------------------------------------------------------------------
 template <typename TK>
 __global__ void __launch_bounds__(256) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
-                                                const typename Vec2<TK>::type* __restrict__ vin,
-                                                typename Vec2<TK>::type* __restrict__ vout, const DevStatus* st) {
-  if (st->error) return;
+                                                typename Vec2<TK>::type* __restrict__ v, int a_in,
+                                                const InstStatus* is) {
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
   typedef typename Vec2<TK>::type TK2;
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S) return;
   Nbr n = neighbours(k, p.nx, p.ny, S);
-  const JCoef<TK> j = jc[k];
-  const TK tx = kval<TK>(p.tx * p.inv_theta, p.f_txt), ty = kval<TK>(p.ty * p.inv_theta, p.f_tyt);
+  const JCoef<TK> j = jc[plane(b, S) + k];
+  const TK tx = kval<TK>(p.txt, p.f_txt), ty = kval<TK>(p.tyt, p.f_tyt);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const TK2* P = vin + (size_t)i * S;
+    const TK2* P = v + level(b, a_in, i, p.s, S);
     TK2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
     TK2 o;
     // (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
     // (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
     o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
     o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
-    vout[(size_t)i * S + k] = o;
+    v[level(b, a_in + 1, i, p.s, S) + k] = o;
   }
 }
 
@@ -290,24 +310,28 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 template <int SK>
 __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const float4* __restrict__ jc,
-                                                        float2* __restrict__ v, const DevStatus* st) {
-  if (st->error) return;
+                                                        float2* __restrict__ v, const InstStatus* is) {
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
   constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* sj = reinterpret_cast<float4*>(smem_raw);
   float2* buf0 = reinterpret_cast<float2*>(sj + EA);     // [3][EA]
   float2* buf1 = buf0 + 3 * EA;                           // [3][EA]
   const int S = p.S, nx = p.nx, ny = p.ny;
-  const int x0 = blockIdx.x * kPowTX - SK, y0 = blockIdx.y * kPowTY - SK;
+  const int tiles_x = (nx + kPowTX - 1) / kPowTX;
+  const int tyi = blockIdx.x / tiles_x, txi = blockIdx.x - tyi * tiles_x;
+  const int x0 = txi * kPowTX - SK, y0 = tyi * kPowTY - SK;
+  const float4* jb = jc + plane(b, S);
   const int tx0 = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // 32 x 8 thread layout
   for (int ly = ty0; ly < EY; ly += kPowThreads / 32) {
     const int grow = wrap(y0 + ly, ny) * nx;
     for (int lx = tx0; lx < EX; lx += 32) {
       const int t = ly * EX + lx;
       const int g = grow + wrap(x0 + lx, nx);
-      sj[t] = jc[g];
+      sj[t] = jb[g];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) buf0[i * EA + t] = v[(size_t)i * S + g];
+      for (int i = 0; i < 3; ++i) buf0[i * EA + t] = v[level(b, 0, i, SK, S) + g];
     }
   }
   __syncthreads();
@@ -334,12 +358,12 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
     // interior of level a to global
     for (int ly = ty0; ly < kPowTY; ly += kPowThreads / 32) {
       const int lx = tx0;
-      const int gx = blockIdx.x * kPowTX + lx, gy = blockIdx.y * kPowTY + ly;
+      const int gx = txi * kPowTX + lx, gy = tyi * kPowTY + ly;
       if (gx < nx && gy < ny) {
         const int c = (ly + SK) * EX + (lx + SK);
         const size_t g = (size_t)gy * nx + gx;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) v[((size_t)a * 3 + i) * S + g] = dst[i * EA + c];
+        for (int i = 0; i < 3; ++i) v[level(b, a, i, SK, S) + g] = dst[i * EA + c];
       }
     }
     float2* tmp = src;
@@ -376,10 +400,10 @@ template <> struct GramAcc<double> {
   }
 };
 
-
 // Gram matrices G_ab = <v_a, v_b> (real inner product of the [p; q] form),
-// a <= b <= s, for system i = blockIdx.y; block partials go to
-// part[(i * gridDim.x + block) * NE + e].  The last block to finish then
+// a <= b <= s, of system i = blockIdx.y of instance blockIdx.z; block partials go
+// to part[((inst * 3 + i) * gridDim.x + block) * NE + e].  The last block of the
+// instance to finish then
 //  1. reduces the partials in a fixed order (so results do not depend on
 //     which block finishes last),
 //  2. forms, per system, the normal equations of the least-squares problem
@@ -391,8 +415,9 @@ template <> struct GramAcc<double> {
 template <typename TK, int SK>
 __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                   double* __restrict__ part, double* __restrict__ coef,
-                                                  DevStatus* st) {
-  if (st->error) return;
+                                                  InstStatus* is) {
+  const int inst = blockIdx.z;
+  if (!is[inst].active) return;
   typedef typename Vec2<TK>::type TK2;
   constexpr int NV = SK + 1;
   constexpr int NE = NV * (NV + 1) / 2;
@@ -403,14 +428,15 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
 #pragma unroll
   for (int e = 0; e < NE; ++e) acc[e].zero();
   const int stride = gridDim.x * blockDim.x;
-  const TK2* vi = v + (size_t)i * S;
+  const TK2* vi = v + level(inst, 0, i, SK, S);
+  const size_t lstride = (size_t)3 * S;         // from level a to level a+1 of the same system
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   for (; k + (U - 1) * stride < S; k += U * stride) {
     TK2 x[U][NV];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int a = 0; a < NV; ++a) x[u][a] = vi[(size_t)a * 3 * S + k + u * stride];
+      for (int a = 0; a < NV; ++a) x[u][a] = vi[(size_t)a * lstride + k + u * stride];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int e = 0;
@@ -423,7 +449,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   for (; k < S; k += stride) {
     TK2 x[NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) x[a] = vi[(size_t)a * 3 * S + k];
+    for (int a = 0; a < NV; ++a) x[a] = vi[(size_t)a * lstride + k];
     int e = 0;
 #pragma unroll
     for (int a = 0; a < NV; ++a)
@@ -440,15 +466,16 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   }
   __syncthreads();
   const int nb = gridDim.x;
+  double* pi = part + (size_t)inst * 3 * nb * NE;
   for (int e = threadIdx.x; e < NE; e += blockDim.x) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][e];
-    part[((size_t)i * nb + blockIdx.x) * NE + e] = t;
+    pi[((size_t)i * nb + blockIdx.x) * NE + e] = t;
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int t = atomicAdd(&st->ticket_gram, 1u);
+    unsigned int t = atomicAdd(&is[inst].ticket_gram, 1u);
     is_last = (t == gridDim.x * gridDim.y - 1);
   }
   __syncthreads();
@@ -463,7 +490,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   for (int t = threadIdx.x; t < SLICES * NT; t += blockDim.x) {
     const int sl = t / NT, r = t - sl * NT, si = r / NE, e = r - si * NE;
     const int b0 = sl * nb / SLICES, b1 = (sl + 1) * nb / SLICES;
-    const double* pp = part + (size_t)si * nb * NE + e;
+    const double* pp = pi + (size_t)si * nb * NE + e;
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int bb = b0;
     for (; bb + 8 <= b1; bb += 8) {
@@ -527,16 +554,16 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
         for (int b2 = a + 1; b2 < dim; ++b2) t -= N[b2][a] * cc[b2];
         cc[a] = t / N[a][a];
       }
-      for (int a = 0; a < SK; ++a) coef[warp * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
+      for (int a = 0; a < SK; ++a) coef[((size_t)inst * 3 + warp) * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
     }
   }
-  if (threadIdx.x == 0) st->ticket_gram = 0u;
+  if (threadIdx.x == 0) is[inst].ticket_gram = 0u;
 }
 
 template <int SK>
 void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  dim3 grid((p.nx + kPowTX - 1) / kPowTX, (p.ny + kPowTY - 1) / kPowTY);
-  k_powers<SK><<<grid, kPowThreads, pow_smem_bytes<SK>(), s>>>(p, (const float4*)b.jc, (float2*)b.v, b.status);
+  dim3 grid(((p.nx + kPowTX - 1) / kPowTX) * ((p.ny + kPowTY - 1) / kPowTY), p.B);
+  k_powers<SK><<<grid, kPowThreads, pow_smem_bytes<SK>(), s>>>(p, (const float4*)b.jc, (float2*)b.v, b.is);
 }
 
 // Opt the matrix-powers kernels into more than 48 KB of dynamic shared memory.
@@ -549,31 +576,6 @@ int prepare_powers() {
   MB4_ATTR(10)
 #undef MB4_ATTR
   return MB4_OK;
-}
-
-template <typename TK>
-void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  typedef typename Vec2<TK>::type TK2;
-  if (sizeof(TK) == sizeof(float) && p.use_powers) {
-    switch (p.s) {
-      case 1: launch_powers_s<1>(p, b, s); break;
-      case 2: launch_powers_s<2>(p, b, s); break;
-      case 3: launch_powers_s<3>(p, b, s); break;
-      case 4: launch_powers_s<4>(p, b, s); break;
-      case 5: launch_powers_s<5>(p, b, s); break;
-      case 6: launch_powers_s<6>(p, b, s); break;
-      case 7: launch_powers_s<7>(p, b, s); break;
-      case 8: launch_powers_s<8>(p, b, s); break;
-      case 9: launch_powers_s<9>(p, b, s); break;
-      default: launch_powers_s<10>(p, b, s); break;
-    }
-    return;
-  }
-  const int blocks = (p.S + 255) / 256;
-  TK2* v = (TK2*)b.v;
-  for (int a = 0; a < p.s; ++a)
-    k_matvec<TK><<<blocks, 256, 0, s>>>(p, (const JCoef<TK>*)b.jc, v + (size_t)a * 3 * p.S,
-                                        v + (size_t)(a + 1) * 3 * p.S, b.status);
 }
 
 #define MB4_SWITCH_S(CALL)        \
@@ -591,16 +593,31 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   }
 
 template <typename TK>
+void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
+  typedef typename Vec2<TK>::type TK2;
+  if (sizeof(TK) == sizeof(float) && p.use_powers) {
+#define MB4_CALL(N) launch_powers_s<N>(p, b, s)
+    MB4_SWITCH_S(MB4_CALL)
+#undef MB4_CALL
+    return;
+  }
+  dim3 grid((p.S + 255) / 256, p.B);
+  for (int a = 0; a < p.s; ++a)
+    k_matvec<TK><<<grid, 256, 0, s>>>(p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a, b.is);
+}
+
+template <typename TK>
 void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-#define MB4_CALL(N)                                                                               \
-  k_gram_lsq<TK, N><<<dim3(p.gram_blocks, 3), 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, \
-                                                        b.gram_part, b.coef, b.status)
+#define MB4_CALL(N)                                                                                      \
+  k_gram_lsq<TK, N><<<dim3(p.gram_blocks, 3, p.B), 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, \
+                                                               b.gram_part, b.coef, b.is)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
 }
 
+// Blocks per (instance, system) that keep the Gram kernel about one wave deep.
 template <typename TK>
-int gram_blocks_per_system(int s_dim) {
+int gram_blocks_per_system(int s_dim, int B) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -612,12 +629,12 @@ int gram_blocks_per_system(int s_dim) {
 #undef MB4_OCC
   }
   if (e != cudaSuccess || occ < 1 || sms < 1) return 0;
-  int nb = sms * occ / 3;
+  long long nb = (long long)sms * occ / (3LL * (B > 0 ? B : 1));
   if (nb > kGramCap) nb = kGramCap;   // more blocks only lengthen the last block's reduction
-  return nb < 1 ? 1 : nb;
+  return nb < 1 ? 1 : (int)nb;
 }
-template int gram_blocks_per_system<float>(int);
-template int gram_blocks_per_system<double>(int);
+template int gram_blocks_per_system<float>(int, int);
+template int gram_blocks_per_system<double>(int, int);
 
 template <typename TK>
 void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
@@ -625,19 +642,37 @@ void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   launch_gram<TK>(p, b, s);
 }
 
+// Records instance b's loop decision; the last instance to do so (over the whole
+// batch) sets the WHILE condition: continue while any instance continues.
+__device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaGraphConditionalHandle h,
+                              int use_cond) {
+  if (cont) atomicAdd(&bc->n_cont, 1);
+  __threadfence();
+  const unsigned int t = atomicAdd(&bc->ticket_inst, 1u);
+  if (t == (unsigned int)(p.B - 1)) {
+    __threadfence();
+    const int any = atomicExch(&bc->n_cont, 0) > 0;
+    bc->ticket_inst = 0u;
+    bc->any_cont = any;
+    if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
+}
+
 // Newton update (Algorithm 1 lines 18-20) and loop test (line 12; failure rule of
 // Sec. 2.2): rbar_i = sum_a c_ia v_a,i; Ubar_i += rbar_i in FP64 (Ubar^0 = tau u0 on
 // the first iteration); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
-// block to finish runs the test: continue while ||r^l||_inf > rtol ||u0||_inf (and,
-// when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
-// for at most newton_max iterations; with a graph it drives the WHILE node.
+// block of each instance runs its test: continue while ||r^l||_inf > rtol ||u0||_inf
+// (and, when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
+// for at most newton_max iterations.  Grid: (sites / 256, B).
 template <typename TK, int SK>
 __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                 const double* __restrict__ coef, const double2* __restrict__ u,
-                                                double2* __restrict__ Ubar, DevStatus* st,
+                                                double2* __restrict__ Ubar, InstStatus* is, BatchCtl* bc,
                                                 cudaGraphConditionalHandle h, int use_cond) {
-  if (st->error) {
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
+  const int inst = blockIdx.y;
+  InstStatus& I = is[inst];
+  if (!I.active) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) instance_done(p, bc, 0, h, use_cond);
     return;
   }
   typedef typename Vec2<TK>::type TK2;
@@ -645,8 +680,10 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
   __shared__ float wmax[8];
   __shared__ int wbad[8];
   __shared__ bool is_last;
-  if (threadIdx.x < 3 * SK) cs[threadIdx.x / SK][threadIdx.x % SK] = (TK)coef[(threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
-  const bool first = (*(volatile int*)&st->newton_iter) == 0;
+  if (threadIdx.x < 3 * SK)
+    cs[threadIdx.x / SK][threadIdx.x % SK] =
+        (TK)coef[((size_t)inst * 3 + threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
+  const bool first = (*(volatile int*)&I.newton_iter) == 0;
   __syncthreads();
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -659,7 +696,7 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
       TK sx = 0, sy = 0;
 #pragma unroll
       for (int a = 0; a < SK; ++a) {
-        const TK2 w = v[((size_t)a * 3 + i) * S + k];
+        const TK2 w = v[level(inst, a, i, SK, S) + k];
         sx += cs[i][a] * w.x;
         sy += cs[i][a] * w.y;
       }
@@ -667,7 +704,7 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
       x[i].y = sy;
     }
     double2 u0;
-    if (first) u0 = u[k];
+    if (first) u0 = u[plane(inst, S) + k];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       double2 U;
@@ -675,11 +712,11 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
         U.x = fma(p.tau[i], u0.x, to_double(x[i].x));
         U.y = fma(p.tau[i], u0.y, to_double(x[i].y));
       } else {
-        U = Ubar[(size_t)i * S + k];
+        U = Ubar[stage(inst, i, S) + k];
         U.x += to_double(x[i].x);
         U.y += to_double(x[i].y);
       }
-      Ubar[(size_t)i * S + k] = U;
+      Ubar[stage(inst, i, S) + k] = U;
     }
     // ||r||_inf with r = T rbar, in FP32: it only decides whether to iterate again.
     float xf[3][2];
@@ -703,88 +740,126 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
     float bm = wmax[0];
     int bb = wbad[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { bm = fmaxf(bm, wmax[w]); bb |= wbad[w]; }
-    if (bm > 0.f) atomicMax(&st->rmax_bits, dbits((double)bm));
-    if (bb) atomicOr(&st->nonfinite, 1);
+    if (bm > 0.f) atomicMax(&I.rmax_bits, dbits((double)bm));
+    if (bb) atomicOr(&I.nonfinite, 1);
     __threadfence();
-    unsigned int t = atomicAdd(&st->ticket_update, 1u);
+    unsigned int t = atomicAdd(&I.ticket_update, 1u);
     is_last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!is_last || threadIdx.x != 0) return;
   __threadfence();
-  st->ticket_update = 0u;
+  I.ticket_update = 0u;
   int cont = 0;
-  const int it = st->newton_iter;                 // iteration index l of this update
-  const double r = __longlong_as_double((long long)atomicOr(&st->rmax_bits, 0ull));
-  const double u0n = (double)__uint_as_float(atomicOr(&st->u0max_bits, 0u));
-  const int nonfinite = atomicOr(&st->nonfinite, 0);
-  if (it < 8) st->hist[it] = r;
-  st->last_rmax = r;
-  st->last_u0max = u0n;
-  st->newton_iter = it + 1;
+  const int it = I.newton_iter;                  // iteration index l of this update
+  const double r = __longlong_as_double((long long)atomicOr(&I.rmax_bits, 0ull));
+  const double u0n = (double)__uint_as_float(atomicOr(&I.u0max_bits, 0u));
+  const int nonfinite = atomicOr(&I.nonfinite, 0);
+  if (it < 8) I.hist[it] = r;
+  I.last_rmax = r;
+  I.last_u0max = u0n;
+  I.newton_iter = it + 1;
   if (nonfinite || !isfinite(r)) {
-    st->error = MB4_ERR_NONFINITE;
+    I.error = MB4_ERR_NONFINITE;
   } else if (r <= p.newton_rtol * u0n) {
     cont = 0;
-  } else if (p.newton_predict > 0.0 && it >= 1 && r < 0.5 * st->prev_rmax &&
-             (r / st->prev_rmax) / (1.0 - r / st->prev_rmax) * r <= p.newton_predict * u0n) {
+  } else if (p.newton_predict > 0.0 && it >= 1 && r < 0.5 * I.prev_rmax &&
+             (r / I.prev_rmax) / (1.0 - r / I.prev_rmax) * r <= p.newton_predict * u0n) {
     cont = 0;
   } else if (it + 1 >= p.newton_max) {
-    st->error = MB4_ERR_NEWTON_NOT_CONVERGED;
+    I.error = MB4_ERR_NEWTON_NOT_CONVERGED;
   } else {
     cont = 1;
   }
-  st->prev_rmax = r;
-  st->last_newton_iters = it + 1;
-  st->rmax_bits = 0ull;
-  st->cont = cont;
-  if (use_cond) cudaGraphSetConditional(h, cont);
+  I.prev_rmax = r;
+  I.last_newton_iters = it + 1;
+  I.rmax_bits = 0ull;
+  I.cont = cont;
+  if (!cont) I.active = 0;
+  instance_done(p, bc, cont, h, use_cond);
 }
 
 template <typename TK>
 void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long h, int use_cond, cudaStream_t s) {
-  int blocks = (p.S + 255) / 256;
-#define MB4_CALL(N)                                                                                           \
-  k_update<TK, N><<<blocks, 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, b.coef, b.u, b.Ubar, b.status, \
-                                         (cudaGraphConditionalHandle)h, use_cond)
+  dim3 grid((p.S + 255) / 256, p.B);
+#define MB4_CALL(N)                                                                                      \
+  k_update<TK, N><<<grid, 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, b.coef, b.u, b.Ubar, b.is, \
+                                       b.bc, (cudaGraphConditionalHandle)h, use_cond)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
 }
 
-// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = sum_n T[2][n] Ubar_n.  Block 0
-// books the step and clears the per-step control fields for the next step.
+// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = sum_n T[2][n] Ubar_n, for the
+// instances that took part in the step and did not fail.  Block 0 of each instance
+// books the step and re-arms the instance for the next one.
 __global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restrict__ u,
-                                                const double2* __restrict__ Ubar, DevStatus* st) {
-  if (st->error) return;
+                                                const double2* __restrict__ Ubar, InstStatus* is) {
+  const int inst = blockIdx.y;
+  InstStatus& I = is[inst];
+  const int took_part = I.in_step;
+  const int failed = I.error;
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < S) {
-    double2 a = Ubar[k], b = Ubar[(size_t)S + k], c = Ubar[(size_t)2 * S + k];
+  if (took_part && !failed && k < S) {
+    double2 a = Ubar[stage(inst, 0, S) + k], b = Ubar[stage(inst, 1, S) + k], c = Ubar[stage(inst, 2, S) + k];
     double2 r;
     r.x = fma(p.T[2][2], c.x, fma(p.T[2][1], b.x, p.T[2][0] * a.x));
     r.y = fma(p.T[2][2], c.y, fma(p.T[2][1], b.y, p.T[2][0] * a.y));
-    u[k] = r;
+    u[plane(inst, S) + k] = r;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->steps_done += 1;
-    st->newton_total += st->newton_iter;
-    st->newton_iter = 0;
-    st->nonfinite = 0;
-    st->rmax_bits = 0ull;
-    st->u0max_bits = 0u;
-    st->prev_rmax = 0.0;
+    if (took_part && !failed) {
+      I.steps_done += 1;
+      I.newton_total += I.newton_iter;
+    }
+    I.newton_iter = 0;
+    I.nonfinite = 0;
+    I.rmax_bits = 0ull;
+    I.u0max_bits = 0u;
+    I.prev_rmax = 0.0;
+    const int go = I.enabled && !I.error;
+    I.in_step = go;
+    I.active = go;
   }
 }
 
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  int blocks = (p.S + 255) / 256;
-  k_accept<<<blocks, 256, 0, s>>>(p, b.u, b.Ubar, b.status);
+  dim3 grid((p.S + 255) / 256, p.B);
+  k_accept<<<grid, 256, 0, s>>>(p, b.u, b.Ubar, b.is);
+}
+
+// Arms every enabled instance without an error for the next step (start of a call).
+__global__ void k_arm(int B, InstStatus* is, BatchCtl* bc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) {
+    bc->ticket_inst = 0u;
+    bc->n_cont = 0;
+    bc->any_cont = 0;
+  }
+  if (b >= B) return;
+  InstStatus& I = is[b];
+  I.newton_iter = 0;
+  I.nonfinite = 0;
+  I.rmax_bits = 0ull;
+  I.u0max_bits = 0u;
+  I.prev_rmax = 0.0;
+  I.ticket_gram = 0u;
+  I.ticket_update = 0u;
+  I.steps_done = 0;
+  I.newton_total = 0;
+  const int go = I.enabled && !I.error;
+  I.in_step = go;
+  I.active = go;
+}
+
+void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
+  k_arm<<<(p.B + 255) / 256, 256, 0, s>>>(p.B, b.is, b.bc);
 }
 
 // ---------------------------------------------------------------------------
-// Observables (Sec. 2.1 energy terms, Sec. 3.2 participation ratio) with
-// compensated FP64 sums (TwoSum) in a fixed order: per-thread, per-warp,
-// per-block, then one block over the block partials.
+// Observables (Sec. 2.1 energy terms, Sec. 3.2 participation ratio) per instance,
+// with compensated FP64 sums (TwoSum) in a fixed order: per-thread, per-warp,
+// per-block, then one block per instance over its block partials.
 // ---------------------------------------------------------------------------
 struct DD { double s, c; };
 __device__ __forceinline__ void two_sum_add(DD& a, double x) {
@@ -802,23 +877,27 @@ __device__ __forceinline__ DD dd_add(DD a, DD b) {
 }
 
 constexpr int kObs = 6;            // H, U_K, U_E, U_nl, sum|u|^2, sum|u|^4
-constexpr int kObsBlocks = 304;
 
 __global__ void __launch_bounds__(256) k_observables(StepParams p, const double2* __restrict__ u,
-                                                     const double* __restrict__ Vp, double* __restrict__ part) {
+                                                     const double* __restrict__ Vp,
+                                                     const InstConst* __restrict__ ic, double* __restrict__ part) {
+  const int inst = blockIdx.y;
   const int S = p.S;
+  const double chi = ic[inst].chi;
+  const double2* ub = u + plane(inst, S);
+  const double* vb = Vp + plane(inst, S);
   DD acc[kObs];
 #pragma unroll
   for (int o = 0; o < kObs; ++o) acc[o].s = acc[o].c = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
     Nbr n = neighbours(k, p.nx, p.ny, S);
-    double2 c = u[k], a = u[n.xm], b = u[n.xp], e = u[n.ym], f = u[n.yp];
+    double2 c = ub[k], a = ub[n.xm], b = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
     double Kx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + b.x, p.eps0 * c.x));
     double Ky = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + b.y, p.eps0 * c.y));
     double tK = fma(c.x, Kx, c.y * Ky);
     double nn = fma(c.x, c.x, c.y * c.y);
-    double tE = Vp[k] * nn;
-    double tI = 0.5 * p.chi * nn * nn;
+    double tE = vb[k] * nn;
+    double tI = 0.5 * chi * nn * nn;
     two_sum_add(acc[0], tK);
     two_sum_add(acc[0], tE);
     two_sum_add(acc[0], tI);
@@ -845,54 +924,65 @@ __global__ void __launch_bounds__(256) k_observables(StepParams p, const double2
   if (threadIdx.x < kObs) {
     DD r = red[0][threadIdx.x];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = dd_add(r, red[w][threadIdx.x]);
-    part[((size_t)blockIdx.x * kObs + threadIdx.x) * 2 + 0] = r.s;
-    part[((size_t)blockIdx.x * kObs + threadIdx.x) * 2 + 1] = r.c;
+    double* pb = part + ((size_t)inst * gridDim.x + blockIdx.x) * kObs * 2;
+    pb[threadIdx.x * 2 + 0] = r.s;
+    pb[threadIdx.x * 2 + 1] = r.c;
   }
 }
 
 __global__ void k_observables_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  const int inst = blockIdx.x;
   const int o = threadIdx.x;
   if (o >= kObs) return;
   DD r;
   r.s = r.c = 0.0;
+  const double* pb = part + (size_t)inst * nblocks * kObs * 2;
   for (int b = 0; b < nblocks; ++b) {
     DD t;
-    t.s = part[((size_t)b * kObs + o) * 2 + 0];
-    t.c = part[((size_t)b * kObs + o) * 2 + 1];
+    t.s = pb[((size_t)b * kObs + o) * 2 + 0];
+    t.c = pb[((size_t)b * kObs + o) * 2 + 1];
     r = dd_add(r, t);
   }
-  out[o] = r.s + r.c;
+  out[(size_t)inst * kObs + o] = r.s + r.c;
+}
+
+int obs_blocks_per_instance(int B) {
+  int nb = kObsBlocksTotal / (B > 0 ? B : 1);
+  if (nb > kObsBlocksMax) nb = kObsBlocksMax;
+  return nb < 1 ? 1 : nb;
 }
 
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  k_observables<<<kObsBlocks, 256, 0, s>>>(p, b.u, b.V, b.obs_part);
-  k_observables_final<<<1, 32, 0, s>>>(b.obs_part, kObsBlocks, b.obs_out);
+  const int nb = obs_blocks_per_instance(p.B);
+  k_observables<<<dim3(nb, p.B), 256, 0, s>>>(p, b.u, b.V, b.ic, b.obs_part);
+  k_observables_final<<<p.B, 32, 0, s>>>(b.obs_part, nb, b.obs_out);
 }
 
 // ---------------------------------------------------------------------------
 // Packing and basis changes used by state I/O and the test entry points.
 // ---------------------------------------------------------------------------
 __global__ void k_pack(const double* __restrict__ re, const double* __restrict__ im, double2* __restrict__ z,
-                       int n) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+                       size_t n) {
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) z[k] = make_double2(re[k], im[k]);
 }
-__global__ void k_unpack(const double2* __restrict__ z, double* __restrict__ re, double* __restrict__ im, int n) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_unpack(const double2* __restrict__ z, double* __restrict__ re, double* __restrict__ im,
+                         size_t n) {
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) {
     double2 v = z[k];
     re[k] = v.x;
     im[k] = v.y;
   }
 }
-void launch_pack(const double* re, const double* im, double2* z, int n, cudaStream_t s) {
-  k_pack<<<(n + 255) / 256, 256, 0, s>>>(re, im, z, n);
+void launch_pack(const double* re, const double* im, double2* z, size_t n, cudaStream_t s) {
+  if (n) k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(re, im, z, n);
 }
-void launch_unpack(const double2* z, double* re, double* im, int n, cudaStream_t s) {
-  k_unpack<<<(n + 255) / 256, 256, 0, s>>>(z, re, im, n);
+void launch_unpack(const double2* z, double* re, double* im, size_t n, cudaStream_t s) {
+  if (n) k_unpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(z, re, im, n);
 }
 
-// Y_j = sum_n M[j][n] X_n on three planes.
+// Y_j = sum_n M[j][n] X_n on three planes of S sites.
 __global__ void k_mix3(int S, const double2* __restrict__ X, double2* __restrict__ Y, double m00, double m01,
                        double m02, double m10, double m11, double m12, double m20, double m21, double m22) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -908,6 +998,7 @@ void launch_mix3(int S, const double2* X, double2* Y, const double M[3][3], cuda
                                          M[2][0], M[2][1], M[2][2]);
 }
 
+// Instance 0's level 0 <- b (3 planes), and x = sum_a c_a v_a of instance 0 -> x3.
 template <typename TK>
 __global__ void k_rhs_in(int S, const double2* __restrict__ b3, typename Vec2<TK>::type* __restrict__ v0) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -934,7 +1025,7 @@ __global__ void k_solution_out(StepParams p, const typename Vec2<TK>::type* __re
     double sx = 0, sy = 0;
     for (int a = 0; a < p.s; ++a) {
       const double c = coef[i * kMaxS + a];
-      const typename Vec2<TK>::type w = v[((size_t)a * 3 + i) * S + k];
+      const typename Vec2<TK>::type w = v[level(0, a, i, p.s, S) + k];
       sx += c * (double)w.x;
       sy += c * (double)w.y;
     }

@@ -36,7 +36,10 @@ KERNEL_CLASSES = ("setup", "residual", "matvec", "gram", "update", "accept")
 # Every entry point include/mb4.h declares.
 EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", "mb4_get_state",
            "mb4_get_stages", "mb4_step", "mb4_step_profiled", "mb4_energy", "mb4_norm", "mb4_observables", "mb4_residual",
-           "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version")
+           "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
+           "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
+           "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
+           "mb4_batch_clear_errors", "mb4_batch_bytes")
 
 
 class Grid(C.Structure):
@@ -108,6 +111,21 @@ def lib():
         L.mb4_version.restype = C.c_char_p
         L.mb4_observables_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                               _P, _P, _P, _P, _P]
+        L.mb4_batch_create.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(Potential), _D, C.c_double,
+                                       C.POINTER(Options), C.POINTER(_P)]
+        L.mb4_batch_destroy.argtypes = [_P]
+        L.mb4_batch_destroy.restype = None
+        L.mb4_batch_set_state.argtypes = [_P, C.c_int, _P, _P, C.c_int]
+        L.mb4_batch_get_state.argtypes = [_P, C.c_int, _P, _P, C.c_int]
+        L.mb4_batch_load.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, C.c_int]
+        L.mb4_batch_enable.argtypes = [_P, C.c_int, C.c_int]
+        L.mb4_batch_step_async.argtypes = [_P, C.c_int]
+        L.mb4_batch_wait.argtypes = [_P, C.POINTER(Stats), C.POINTER(C.c_int)]
+        L.mb4_batch_step.argtypes = [_P, C.c_int, C.POINTER(Stats), C.POINTER(C.c_int)]
+        L.mb4_batch_observables.argtypes = [_P, _D]
+        L.mb4_batch_clear_errors.argtypes = [_P]
+        L.mb4_batch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(Options)]
+        L.mb4_batch_bytes.restype = C.c_longlong
         _lib = L
     return _lib
 
@@ -323,6 +341,113 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
     _check(lib().mb4_observables_noalloc(int(nx), int(ny), float(tx), float(tx if ty is None else ty),
                                          float(onsite), float(chi), re.data_ptr(), im.data_ptr(), V.data_ptr(),
                                          out6.data_ptr(), sp), "mb4_observables_noalloc")
+
+
+def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
+             c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0):
+    opt = Options()
+    lib().mb4_default_options(C.byref(opt))
+    opt.newton_rtol = float(newton_rtol)
+    opt.newton_max = int(newton_max)
+    opt.krylov_s = int(krylov_s)
+    opt.precision = {"fp64": MB4_FP64, "mixed": MB4_MIXED}[precision] if isinstance(precision, str) \
+        else int(precision)
+    opt.alpha1 = float(alpha1)
+    opt.c1, opt.c2 = float(c1), float(c2)
+    opt.use_graph = 1 if use_graph else 0
+    opt.newton_predict = float(newton_predict)
+    if stream is not None:
+        opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return opt
+
+
+def batch_bytes(nx, ny, batch, **opts):
+    """Device bytes a batch of this shape would allocate (mb4_batch_bytes)."""
+    return int(lib().mb4_batch_bytes(int(nx), int(ny), int(batch), C.byref(_options(**opts))))
+
+
+class Batch:
+    """B independent instances of one grid shape and h (mb4_batch_*).  V is
+    (B, S) or B*S host values; chi holds B values."""
+
+    def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, **opts):
+        L = lib()
+        self.nx, self.ny = int(nx), int(ny)
+        self.S = self.nx * self.ny
+        chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(-1))
+        self.B = chi.size
+        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+        if Vh.size != self.B * self.S:
+            raise ValueError("V must hold B*nx*ny values")
+        self._ctx = _P()
+        grid = Grid(self.nx, self.ny, float(tx), float(tx if ty is None else ty), float(onsite))
+        _check(L.mb4_batch_create(C.byref(grid), self.B, C.byref(Potential(Vh.ctypes.data, 0)),
+                                  chi.ctypes.data_as(_D), float(h), C.byref(_options(**opts)),
+                                  C.byref(self._ctx)), "mb4_batch_create")
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().mb4_batch_destroy(self._ctx)
+            self._ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, psi, instance=-1):
+        n = self.S * (self.B if instance < 0 else 1)
+        p = _Planar(psi, n)
+        _check(lib().mb4_batch_set_state(self._ctx, int(instance), p.pre, p.pim, p.on_device), "mb4_batch_set_state")
+
+    def get_state(self, instance=-1):
+        n = self.S * (self.B if instance < 0 else 1)
+        re = np.empty(n)
+        im = np.empty(n)
+        _check(lib().mb4_batch_get_state(self._ctx, int(instance), re.ctypes.data, im.ctypes.data, 0),
+               "mb4_batch_get_state")
+        z = re + 1j * im
+        return z.reshape(self.B, self.S) if instance < 0 else z
+
+    def load(self, instance, V, chi, psi):
+        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+        p = _Planar(psi, self.S)
+        if p.on_device:
+            raise ValueError("load takes host arrays")
+        _check(lib().mb4_batch_load(self._ctx, int(instance), Vh.ctypes.data, float(chi), p.pre, p.pim, 0),
+               "mb4_batch_load")
+
+    def enable(self, instance, enabled=True):
+        _check(lib().mb4_batch_enable(self._ctx, int(instance), 1 if enabled else 0), "mb4_batch_enable")
+
+    def step_async(self, nsteps=1):
+        _check(lib().mb4_batch_step_async(self._ctx, int(nsteps)), "mb4_batch_step_async")
+
+    def wait(self):
+        """(per-instance stats list, per-instance status codes)."""
+        st = (Stats * self.B)()
+        codes = (C.c_int * self.B)()
+        lib().mb4_batch_wait(self._ctx, st, codes)
+        return [s.as_dict() for s in st], list(codes)
+
+    def step(self, nsteps=1):
+        self.step_async(nsteps)
+        return self.wait()
+
+    def observables(self):
+        out = np.zeros(self.B * 6)
+        _check(lib().mb4_batch_observables(self._ctx, out.ctypes.data_as(_D)), "mb4_batch_observables")
+        return out.reshape(self.B, 6)
+
+    def clear_errors(self):
+        _check(lib().mb4_batch_clear_errors(self._ctx), "mb4_batch_clear_errors")
 
 
 def from_workload(w, precision="fp64", **kw):
