@@ -215,8 +215,8 @@ int mb4_batch_get_state(const mb4_batch* b, int instance, double* re, double* im
 int mb4_batch_load(mb4_batch* b, int instance, const double* v, double chi, const double* re, const double* im,
                    int on_device);
 
-/* Enable (1) or disable (0) stepping of one instance; a disabled instance keeps
- * its state and takes no part in later steps. */
+/* Enable (1) or disable (0) stepping of one instance (instance = -1: all); a
+ * disabled instance keeps its state and takes no part in later steps. */
 int mb4_batch_enable(mb4_batch* b, int instance, int enabled);
 
 /* Enqueue nsteps MB4 steps for every enabled instance without an error, on the
@@ -240,6 +240,60 @@ int mb4_batch_clear_errors(mb4_batch* b);
 
 /* Device bytes a batch of this shape and options would allocate (for admission). */
 long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt);
+
+/* ---- serving: continuous batching of simulation requests ------------------
+ * A server keeps one batch per shape class (nx, ny, tx, ty, onsite, h), each on
+ * its own CUDA stream, inside an HBM budget.  Requests carry their own grid,
+ * potential, chi, initial state, step count and arrival time.  The serving loop
+ * admits every request that has arrived into a free slot of its class (creating
+ * the class's batch when the budget allows, and releasing idle batches when it
+ * does not), advances all classes concurrently (their kernels overlap on the
+ * GPU), and retires each request after exactly its step count, freeing the slot
+ * for the next.  States stay on the GPU from admission to completion.  Latency
+ * is completion time minus arrival time on the server's clock. */
+typedef struct mb4_server mb4_server;
+
+typedef struct {
+    mb4_grid grid;
+    double h;
+    double chi;
+    int nsteps;               /* MB4 steps to run (>= 1)                                        */
+    const double* v;          /* host, S doubles, copied at submit                             */
+    const double* re;         /* host, S doubles: initial state, copied at submit              */
+    const double* im;
+    double arrival;           /* seconds on the server clock; not admitted before this time    */
+} mb4_request;
+
+typedef struct {
+    int status;               /* MB4_OK, or the error that stopped the request                  */
+    int done;                 /* 1 once completed (or failed)                                   */
+    long long steps_done;
+    long long newton_iters_total;
+    double arrival, admitted, completed;   /* server clock, seconds                           */
+    double energy_start, energy_end;       /* H at admission and at completion               */
+} mb4_result;
+
+/* hbm_budget_bytes: device memory the server's batches may hold together;
+ * max_slots: instances per class batch, at most; keep_states: 1 to keep each
+ * final state for mb4_server_result.  opt applies to every batch. */
+int mb4_server_create(long long hbm_budget_bytes, int max_slots, int keep_states, const mb4_options* opt,
+                      mb4_server** out);
+void mb4_server_destroy(mb4_server* s);
+
+/* Queue a request; *id receives its index (0, 1, ...).  MB4_ERR_ADMISSION_REJECTED
+ * if a single instance of its class cannot fit the budget at all. */
+int mb4_server_submit(mb4_server* s, const mb4_request* req, long long* id);
+
+/* Run the serving loop until every submitted request is done or the server clock
+ * reaches `until` seconds; *n_done (nullable) receives the number done so far. */
+int mb4_server_run(mb4_server* s, double until, long long* n_done);
+
+/* Result of request id; re/im (nullable, S doubles each, host) receive the final
+ * state when the server keeps states. */
+int mb4_server_result(const mb4_server* s, long long id, mb4_result* out, double* re, double* im);
+
+/* Seconds on the server clock (0 at creation). */
+double mb4_server_clock(const mb4_server* s);
 
 /* Host-only: the MB4 constants the library computes for (alpha1, c1, c2), c3 = 1.
  * E34: 12 doubles, row-major E[i][j], i = 1..3, j = 0..3 (j = 0 is E_i0, eq. Ei0).

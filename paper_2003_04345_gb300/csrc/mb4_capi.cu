@@ -19,7 +19,6 @@ struct mb4_batch {
   int precision = MB4_FP64;
   int use_graph = 1;
   int B = 1;
-  double theta = 1.0;
   Constants k{};
   StepParams p{};
   DevBuffers b{};
@@ -95,7 +94,15 @@ int validate_grid(const mb4_grid* grid, int B) {
   return MB4_OK;
 }
 
-void fill_inst_const(const mb4_batch* c, double chi, InstConst* out) {
+// theta for one instance: a Gershgorin bound on the spectral radius of J (onsite+V part).
+double instance_theta(const StepParams& p, const double* V, size_t S) {
+  double vmax = 0.0;
+  for (size_t k = 0; k < S; ++k) vmax = std::fmax(vmax, std::fabs(p.eps0 + V[k]));
+  double theta = vmax + 2.0 * std::fabs(p.tx) + 2.0 * std::fabs(p.ty);
+  return (theta > 0.0) ? theta : 1.0;
+}
+
+void fill_inst_const(const mb4_batch* c, double chi, double theta, InstConst* out) {
   const Constants& K = c->k;
   std::memset(out, 0, sizeof(*out));
   for (int q = 0; q < kGauss; ++q) {
@@ -109,9 +116,16 @@ void fill_inst_const(const mb4_batch* c, double chi, InstConst* out) {
     }
   }
   out->chi = chi;
-  out->chi_theta = chi / c->theta;
+  out->chi_theta = chi / theta;
+  out->inv_theta = 1.0 / theta;
+  out->txt = c->p.tx / theta;
+  out->tyt = c->p.ty / theta;
+  for (int i = 0; i < 3; ++i) out->sig[i] = c->p.h * K.lam[i] * theta;
   out->f_chi = (float)chi;
-  out->f_chi_theta = (float)(chi / c->theta);
+  out->f_chi_theta = (float)(chi / theta);
+  out->f_inv_theta = (float)(1.0 / theta);
+  out->f_txt = (float)(c->p.tx / theta);
+  out->f_tyt = (float)(c->p.ty / theta);
 }
 
 void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options& o) {
@@ -150,10 +164,6 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
       p.LT[q][n] = s;
     }
   }
-  p.inv_theta = 1.0 / c->theta;
-  p.txt = grid->tx / c->theta;
-  p.tyt = grid->ty / c->theta;
-  for (int i = 0; i < 3; ++i) p.sig[i] = h * K.lam[i] * c->theta;
   p.newton_rtol = o.newton_rtol;
   p.newton_predict = o.newton_predict;
   p.newton_max = o.newton_max;
@@ -162,9 +172,6 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
     for (int j = 0; j < 3; ++j) p.fT[i][j] = (float)p.T[i][j];
     p.f_hTc[i] = (float)p.hTc[i];
   }
-  p.f_inv_theta = (float)p.inv_theta;
-  p.f_txt = (float)p.txt;
-  p.f_tyt = (float)p.tyt;
 }
 
 template <typename TK>
@@ -330,17 +337,13 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   c->B = B;
   MB4_TRY(cudaGetDevice(&c->device));
   const size_t S = (size_t)grid->nx * grid->ny, BS = S * B;
-  double vmax = 0.0;
   std::vector<double> D(BS);
   for (size_t k = 0; k < BS; ++k) {
     if (!std::isfinite(V[k])) return MB4_ERR_INVALID_ARG;
     D[k] = grid->onsite + V[k];
-    vmax = std::fmax(vmax, std::fabs(D[k]));
   }
   for (int b = 0; b < B; ++b)
     if (!std::isfinite(chi[b])) return MB4_ERR_INVALID_ARG;
-  c->theta = vmax + 2.0 * std::fabs(grid->tx) + 2.0 * std::fabs(grid->ty);
-  if (!(c->theta > 0.0)) c->theta = 1.0;
   fill_params(c, grid, h, o);
   StepParams& p = c->p;
   p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B)
@@ -367,7 +370,7 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(dalloc(c, (void**)&d.is, (size_t)B * sizeof(InstStatus)));
   MB4_CHECK(dalloc(c, (void**)&d.bc, sizeof(BatchCtl)));
   std::vector<InstConst> ic(B);
-  for (int b = 0; b < B; ++b) fill_inst_const(c, chi[b], &ic[b]);
+  for (int b = 0; b < B; ++b) fill_inst_const(c, chi[b], instance_theta(c->p, V + (size_t)b * S, S), &ic[b]);
   c->host_status.assign(B, InstStatus{});
   for (int b = 0; b < B; ++b) c->host_status[b].enabled = 1;
   MB4_TRY(cudaMemcpyAsync(d.V, V, BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -561,7 +564,7 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
     D[k] = c->p.eps0 + V[k];
   }
   InstConst ic;
-  fill_inst_const(c, chi, &ic);
+  fill_inst_const(c, chi, instance_theta(c->p, V.data(), S), &ic);
   MB4_TRY(cudaMemcpyAsync(c->b.V + (size_t)instance * S, V.data(), S * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream));
   MB4_TRY(cudaMemcpyAsync(c->b.d + (size_t)instance * S, D.data(), S * sizeof(double), cudaMemcpyHostToDevice,
@@ -576,9 +579,10 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
 }
 
 int mb4_batch_enable(mb4_batch* c, int instance, int enabled) {
-  MB4_CHECK(check_instance(c, instance, false));
+  MB4_CHECK(check_instance(c, instance, true));
   MB4_CHECK(read_status(c));
-  c->host_status[instance].enabled = enabled ? 1 : 0;
+  for (int b = 0; b < c->B; ++b)
+    if (instance < 0 || b == instance) c->host_status[b].enabled = enabled ? 1 : 0;
   return write_status(c);
 }
 

@@ -47,26 +47,25 @@ struct StepParams {
   double L0[kGauss];       // l_0(zeta_q)
   double LT[kGauss][3];    // sum_m l_m(zeta_q) T[m][n]
   double T[3][3];          // r = T rbar ;  u1 = sum_n T[2][n] Ubar_n
-  // Krylov (monomial basis of J/theta)
-  double inv_theta;        // 1 / theta
-  double txt, tyt;         // tx / theta, ty / theta
-  double sig[3];           // h lambda_i theta
   double newton_rtol;
   double newton_predict;   // 0: off; else Hairer-Wanner predicted-error stop
   int newton_max;
   float trunc_rel;         // relative pivot threshold of the Gram Cholesky
   // FP32 copies of uniform constants (no per-thread conversions on the FP64 pipe)
   float fT[3][3];
-  float f_inv_theta;
   float f_hTc[3];
-  float f_txt, f_tyt;
 };
 
-// Per-instance constants (device array of B).
+// Per-instance constants (device array of B).  theta bounds the spectral radius
+// of J (Gershgorin: max|onsite + V| + 2|tx| + 2|ty|); the Krylov basis is built
+// from J/theta so that its vectors stay O(1).
 struct InstConst {
   double hchiW[3][kGauss]; // h chi (Tinv W)_iq, W_jq = w_q A_{c_j}(zeta_q)
   double chi, chi_theta;
-  float f_chi, f_chi_theta;
+  double inv_theta;        // 1 / theta
+  double txt, tyt;         // tx / theta, ty / theta
+  double sig[3];           // h lambda_i theta
+  float f_chi, f_chi_theta, f_inv_theta, f_txt, f_tyt;
 };
 
 // Per-instance Newton status (device array of B).

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __re
     S0[plane(b, S) + k] = s0;
     const TK pk = from_double<TK>(c.x), qk = from_double<TK>(c.y);
     const TK pp = pk * pk, qq = qk * qk, nn = pp + qq;
-    const TK dt = from_double<TK>(d) * kval<TK>(p.inv_theta, p.f_inv_theta);
+    const TK dt = from_double<TK>(d) * kval<TK>(C.inv_theta, C.f_inv_theta);
     const TK ct = kval<TK>(C.chi_theta, C.f_chi_theta);
     JCoef<TK> j;
     j.e1 = dt + ct * (pp + (TK)3 * qq);
@@ -264,7 +264,7 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 template <typename TK>
 __global__ void __launch_bounds__(256) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
-                                                const InstStatus* is) {
+                                                const InstConst* __restrict__ ic, const InstStatus* is) {
   const int b = blockIdx.y;
   if (!is[b].active) return;
   typedef typename Vec2<TK>::type TK2;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) k_matvec(StepParams p, const JCoef<TK>* _
   if (k >= S) return;
   Nbr n = neighbours(k, p.nx, p.ny, S);
   const JCoef<TK> j = jc[plane(b, S) + k];
-  const TK tx = kval<TK>(p.txt, p.f_txt), ty = kval<TK>(p.tyt, p.f_tyt);
+  const TK tx = kval<TK>(ic[b].txt, ic[b].f_txt), ty = kval<TK>(ic[b].tyt, ic[b].f_tyt);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const TK2* P = v + level(b, a_in, i, p.s, S);
@@ -310,7 +310,8 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 template <int SK>
 __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const float4* __restrict__ jc,
-                                                        float2* __restrict__ v, const InstStatus* is) {
+                                                        float2* __restrict__ v, const InstConst* __restrict__ ic,
+                                                        const InstStatus* is) {
   const int b = blockIdx.y;
   if (!is[b].active) return;
   constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
     }
   }
   __syncthreads();
-  const float tx = p.f_txt, ty = p.f_tyt;
+  const float tx = ic[b].f_txt, ty = ic[b].f_tyt;
   float2* src = buf0;
   float2* dst = buf1;
 #pragma unroll 1
@@ -415,7 +416,7 @@ template <> struct GramAcc<double> {
 template <typename TK, int SK>
 __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                   double* __restrict__ part, double* __restrict__ coef,
-                                                  InstStatus* is) {
+                                                  const InstConst* __restrict__ ic, InstStatus* is) {
   const int inst = blockIdx.z;
   if (!is[inst].active) return;
   typedef typename Vec2<TK>::type TK2;
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   };
   for (int t = threadIdx.x; t < 3 * SK * (SK + 1); t += blockDim.x) {
     const int si = t / (SK * (SK + 1)), r = t - si * SK * (SK + 1), a = r / (SK + 1), c = r - a * (SK + 1);
-    const double sg = p.sig[si];
+    const double sg = ic[inst].sig[si];
     Nm[si][a][c] = (c < SK) ? g(si, a, c) - sg * (g(si, a + 1, c) + g(si, a, c + 1)) + sg * sg * g(si, a + 1, c + 1)
                             : g(si, a, 0) - sg * g(si, a + 1, 0);
   }
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
 template <int SK>
 void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   dim3 grid(((p.nx + kPowTX - 1) / kPowTX) * ((p.ny + kPowTY - 1) / kPowTY), p.B);
-  k_powers<SK><<<grid, kPowThreads, pow_smem_bytes<SK>(), s>>>(p, (const float4*)b.jc, (float2*)b.v, b.is);
+  k_powers<SK><<<grid, kPowThreads, pow_smem_bytes<SK>(), s>>>(p, (const float4*)b.jc, (float2*)b.v, b.ic, b.is);
 }
 
 // Opt the matrix-powers kernels into more than 48 KB of dynamic shared memory.
@@ -603,14 +604,14 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   }
   dim3 grid((p.S + 255) / 256, p.B);
   for (int a = 0; a < p.s; ++a)
-    k_matvec<TK><<<grid, 256, 0, s>>>(p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a, b.is);
+    k_matvec<TK><<<grid, 256, 0, s>>>(p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a, b.ic, b.is);
 }
 
 template <typename TK>
 void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 #define MB4_CALL(N)                                                                                      \
   k_gram_lsq<TK, N><<<dim3(p.gram_blocks, 3, p.B), 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, \
-                                                               b.gram_part, b.coef, b.is)
+                                                               b.gram_part, b.coef, b.ic, b.is)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
 }

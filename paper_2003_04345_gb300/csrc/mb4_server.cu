@@ -1,0 +1,353 @@
+// libmb4 serving loop: continuous batching of MB4 simulation requests.
+//
+// One batch per shape class (nx, ny, tx, ty, onsite, h), each on its own CUDA
+// stream, inside an HBM budget.  Every pass of the loop
+//   1. admits each request that has arrived into a free slot of its class
+//      (creating the class's batch when the budget allows, releasing idle
+//      batches when it does not),
+//   2. enqueues the next chunk of steps of every class with running requests
+//      on that class's stream (so different classes overlap on the GPU; a
+//      chunk never runs past the earliest finishing request of its class),
+//   3. waits, books the steps, and retires the requests that reached their
+//      step count, freeing their slots for the queue.
+// States stay on the GPU from admission to completion.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "mb4_internal.h"
+
+namespace {
+
+constexpr long long kMaxChunk = 32;   // steps per pass: bounds the wait before new admissions
+
+struct ServerReq {
+  mb4_grid grid{};
+  double h = 0, chi = 0, arrival = 0;
+  int nsteps = 0;
+  std::vector<double> v, re, im;
+  mb4_result res{};
+  int cls = -1, slot = -1;
+  long long remaining = 0;
+  bool queued = true;
+  bool need_h0 = false;
+  std::vector<double> out_re, out_im;
+};
+
+struct ClassBatch {
+  mb4_grid grid{};
+  double h = 0;
+  mb4_batch* b = nullptr;
+  cudaStream_t stream = nullptr;
+  int slots = 0;
+  long long bytes = 0;
+  std::vector<long long> slot_req;   // request in each slot, -1 = free
+  int running = 0;
+  long long chunk = 0;
+};
+
+bool same_class(const ClassBatch& c, const mb4_grid& g, double h) {
+  return c.grid.nx == g.nx && c.grid.ny == g.ny && c.grid.tx == g.tx && c.grid.ty == g.ty &&
+         c.grid.onsite == g.onsite && c.h == h;
+}
+
+}  // namespace
+
+struct mb4_server {
+  long long budget = 0;
+  int max_slots = 1;
+  int keep = 0;
+  mb4_options opt{};
+  std::vector<ServerReq> reqs;
+  std::deque<long long> queue;
+  std::vector<ClassBatch*> classes;
+  long long used = 0;
+  long long n_done = 0;
+  std::chrono::steady_clock::time_point t0;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+void release_class(mb4_server* s, size_t idx) {
+  ClassBatch* c = s->classes[idx];
+  if (c->b) mb4_batch_destroy(c->b);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  s->used -= c->bytes;
+  delete c;
+  s->classes.erase(s->classes.begin() + idx);
+}
+
+// A batch for (grid, h) with as many slots as the budget allows (at most max_slots),
+// releasing idle batches first if needed.  Returns nullptr if not even one slot fits now.
+ClassBatch* create_class(mb4_server* s, const mb4_grid& g, double h, int want) {
+  const long long one = mb4_batch_bytes(g.nx, g.ny, 1, &s->opt);
+  if (one <= 0) return nullptr;
+  if (s->used + one > s->budget) {
+    for (size_t i = 0; i < s->classes.size();) {
+      if (s->classes[i]->running == 0) release_class(s, i);
+      else ++i;
+      if (s->used + one <= s->budget) break;
+    }
+  }
+  if (s->used + one > s->budget) return nullptr;
+  int slots = std::max(1, std::min(s->max_slots, want));
+  while (slots > 1 && s->used + mb4_batch_bytes(g.nx, g.ny, slots, &s->opt) > s->budget) slots /= 2;
+  ClassBatch* c = new (std::nothrow) ClassBatch();
+  if (!c) return nullptr;
+  c->grid = g;
+  c->h = h;
+  c->slots = slots;
+  c->bytes = mb4_batch_bytes(g.nx, g.ny, slots, &s->opt);
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return nullptr;
+  }
+  mb4_options o = s->opt;
+  o.stream = c->stream;
+  const size_t S = (size_t)g.nx * g.ny;
+  std::vector<double> V(S * slots, 0.0), chi(slots, 0.0);
+  mb4_potential pot{V.data(), 0};
+  if (mb4_batch_create(&g, slots, &pot, chi.data(), h, &o, &c->b) != MB4_OK ||
+      mb4_batch_enable(c->b, -1, 0) != MB4_OK) {
+    if (c->b) mb4_batch_destroy(c->b);
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return nullptr;
+  }
+  c->slot_req.assign(slots, -1);
+  s->used += c->bytes;
+  s->classes.push_back(c);
+  return c;
+}
+
+void complete(mb4_server* s, ClassBatch* c, int slot, int status, double energy_end) {
+  const long long id = c->slot_req[slot];
+  ServerReq& r = s->reqs[id];
+  r.res.status = status;
+  r.res.done = 1;
+  r.res.completed = s->now();
+  r.res.energy_end = energy_end;
+  if (s->keep) {
+    const size_t S = (size_t)r.grid.nx * r.grid.ny;
+    r.out_re.resize(S);
+    r.out_im.resize(S);
+    mb4_batch_get_state(c->b, slot, r.out_re.data(), r.out_im.data(), 0);
+  }
+  mb4_batch_enable(c->b, slot, 0);
+  c->slot_req[slot] = -1;
+  c->running -= 1;
+  s->n_done += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mb4_server_create(long long budget, int max_slots, int keep_states, const mb4_options* opt,
+                      mb4_server** out) {
+  if (!out || budget <= 0 || max_slots < 1) return MB4_ERR_INVALID_ARG;
+  *out = nullptr;
+  mb4_server* s = new (std::nothrow) mb4_server();
+  if (!s) return MB4_ERR_OUT_OF_MEMORY;
+  if (opt) s->opt = *opt;
+  else mb4_default_options(&s->opt);
+  if (mb4_batch_bytes(8, 8, 1, &s->opt) <= 0) {
+    delete s;
+    return MB4_ERR_INVALID_ARG;
+  }
+  s->budget = budget;
+  s->max_slots = max_slots;
+  s->keep = keep_states ? 1 : 0;
+  s->t0 = std::chrono::steady_clock::now();
+  *out = s;
+  return MB4_OK;
+}
+
+void mb4_server_destroy(mb4_server* s) {
+  if (!s) return;
+  while (!s->classes.empty()) release_class(s, s->classes.size() - 1);
+  delete s;
+}
+
+double mb4_server_clock(const mb4_server* s) { return s ? s->now() : 0.0; }
+
+int mb4_server_submit(mb4_server* s, const mb4_request* q, long long* id) {
+  if (!s || !q || !q->v || !q->re || !q->im || q->nsteps < 1) return MB4_ERR_INVALID_ARG;
+  const mb4_grid& g = q->grid;
+  if (g.nx < 3 || g.ny < 3 || (long long)g.nx * g.ny > (1LL << 30)) return MB4_ERR_INVALID_ARG;
+  if (!std::isfinite(q->h) || q->h == 0.0 || !std::isfinite(q->chi) || !std::isfinite(q->arrival))
+    return MB4_ERR_INVALID_ARG;
+  const long long one = mb4_batch_bytes(g.nx, g.ny, 1, &s->opt);
+  if (one <= 0) return MB4_ERR_INVALID_ARG;
+  if (one > s->budget) return MB4_ERR_ADMISSION_REJECTED;
+  ServerReq r;
+  r.grid = g;
+  r.h = q->h;
+  r.chi = q->chi;
+  r.nsteps = q->nsteps;
+  r.arrival = q->arrival;
+  const size_t S = (size_t)g.nx * g.ny;
+  r.v.assign(q->v, q->v + S);
+  r.re.assign(q->re, q->re + S);
+  r.im.assign(q->im, q->im + S);
+  r.res.arrival = q->arrival;
+  s->reqs.push_back(std::move(r));
+  const long long k = (long long)s->reqs.size() - 1;
+  s->queue.push_back(k);
+  if (id) *id = k;
+  return MB4_OK;
+}
+
+int mb4_server_run(mb4_server* s, double until, long long* n_done) {
+  if (!s) return MB4_ERR_INVALID_ARG;
+  std::vector<mb4_stats> stats;
+  std::vector<int> codes;
+  std::vector<double> obs;
+  for (;;) {
+    const double t = s->now();
+    if (t >= until) break;
+    // 1. admission (first come, first served among the requests that have arrived)
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+      ServerReq& r = s->reqs[*it];
+      if (r.arrival > t) {
+        ++it;
+        continue;
+      }
+      ClassBatch* c = nullptr;
+      for (ClassBatch* cb : s->classes)
+        if (same_class(*cb, r.grid, r.h) && cb->running < cb->slots) {
+          c = cb;
+          break;
+        }
+      if (!c) {
+        int want = 0;   // requests of this class that have arrived and wait
+        for (long long q : s->queue)
+          if (s->reqs[q].arrival <= t && s->reqs[q].grid.nx == r.grid.nx && s->reqs[q].grid.ny == r.grid.ny &&
+              s->reqs[q].h == r.h)
+            ++want;
+        c = create_class(s, r.grid, r.h, want);
+      }
+      if (!c) {
+        ++it;
+        continue;
+      }
+      int slot = -1;
+      for (int k = 0; k < c->slots; ++k)
+        if (c->slot_req[k] < 0) {
+          slot = k;
+          break;
+        }
+      if (slot < 0) {
+        ++it;
+        continue;
+      }
+      int rc = mb4_batch_load(c->b, slot, r.v.data(), r.chi, r.re.data(), r.im.data(), 0);
+      if (rc != MB4_OK) return rc;
+      c->slot_req[slot] = *it;
+      c->running += 1;
+      r.cls = 0;
+      r.slot = slot;
+      r.remaining = r.nsteps;
+      r.queued = false;
+      r.need_h0 = true;
+      r.res.admitted = s->now();
+      std::vector<double>().swap(r.v);
+      std::vector<double>().swap(r.re);
+      std::vector<double>().swap(r.im);
+      it = s->queue.erase(it);
+    }
+    // energy at admission
+    for (ClassBatch* c : s->classes) {
+      bool any = false;
+      for (int k = 0; k < c->slots; ++k)
+        if (c->slot_req[k] >= 0 && s->reqs[c->slot_req[k]].need_h0) any = true;
+      if (!any) continue;
+      obs.resize((size_t)c->slots * 6);
+      int rc = mb4_batch_observables(c->b, obs.data());
+      if (rc != MB4_OK) return rc;
+      for (int k = 0; k < c->slots; ++k)
+        if (c->slot_req[k] >= 0 && s->reqs[c->slot_req[k]].need_h0) {
+          s->reqs[c->slot_req[k]].res.energy_start = obs[(size_t)k * 6];
+          s->reqs[c->slot_req[k]].need_h0 = false;
+        }
+    }
+    // 2. enqueue one chunk per class with running requests
+    bool stepped = false;
+    for (ClassBatch* c : s->classes) {
+      c->chunk = 0;
+      if (c->running == 0) continue;
+      long long k = kMaxChunk;
+      for (int sl = 0; sl < c->slots; ++sl)
+        if (c->slot_req[sl] >= 0) k = std::min(k, s->reqs[c->slot_req[sl]].remaining);
+      int rc = mb4_batch_step_async(c->b, (int)k);
+      if (rc != MB4_OK) return rc;
+      c->chunk = k;
+      stepped = true;
+    }
+    if (!stepped) {
+      if (s->queue.empty()) break;
+      double next = 1e300;
+      for (long long q : s->queue) next = std::min(next, s->reqs[q].arrival);
+      if (next > s->now()) {
+        const double dt = std::min(next - s->now(), until - s->now());
+        if (dt > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(dt, 0.01)));
+      } else if (s->classes.empty()) {
+        return MB4_ERR_ADMISSION_REJECTED;   // arrived requests, nothing running, nothing creatable
+      }
+      continue;
+    }
+    // 3. wait and retire
+    for (ClassBatch* c : s->classes) {
+      if (c->chunk == 0) continue;
+      stats.resize(c->slots);
+      codes.resize(c->slots);
+      mb4_batch_wait(c->b, stats.data(), codes.data());
+      bool finished = false;
+      for (int sl = 0; sl < c->slots; ++sl) {
+        const long long id = c->slot_req[sl];
+        if (id < 0) continue;
+        ServerReq& r = s->reqs[id];
+        r.res.steps_done += stats[sl].steps_done;
+        r.res.newton_iters_total += stats[sl].newton_iters_total;
+        r.remaining -= stats[sl].steps_done;
+        if (codes[sl] != MB4_OK || r.remaining <= 0) finished = true;
+      }
+      if (!finished) continue;
+      obs.resize((size_t)c->slots * 6);
+      mb4_batch_observables(c->b, obs.data());
+      for (int sl = 0; sl < c->slots; ++sl) {
+        const long long id = c->slot_req[sl];
+        if (id < 0) continue;
+        if (codes[sl] != MB4_OK || s->reqs[id].remaining <= 0) complete(s, c, sl, codes[sl], obs[(size_t)sl * 6]);
+      }
+      if (codes.size() && std::any_of(codes.begin(), codes.end(), [](int x) { return x != MB4_OK; }))
+        mb4_batch_clear_errors(c->b);
+    }
+  }
+  if (n_done) *n_done = s->n_done;
+  return MB4_OK;
+}
+
+int mb4_server_result(const mb4_server* s, long long id, mb4_result* out, double* re, double* im) {
+  if (!s || id < 0 || id >= (long long)s->reqs.size() || !out) return MB4_ERR_INVALID_ARG;
+  const ServerReq& r = s->reqs[id];
+  *out = r.res;
+  if ((re || im) && r.res.done) {
+    if (!s->keep || r.out_re.empty()) return MB4_ERR_INVALID_ARG;
+    if (re) std::memcpy(re, r.out_re.data(), r.out_re.size() * sizeof(double));
+    if (im) std::memcpy(im, r.out_im.data(), r.out_im.size() * sizeof(double));
+  }
+  return MB4_OK;
+}
+
+}  // extern "C"

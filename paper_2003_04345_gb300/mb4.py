@@ -39,7 +39,8 @@ EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", 
            "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
            "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
            "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
-           "mb4_batch_clear_errors", "mb4_batch_bytes")
+           "mb4_batch_clear_errors", "mb4_batch_bytes", "mb4_server_create", "mb4_server_destroy",
+           "mb4_server_submit", "mb4_server_run", "mb4_server_result", "mb4_server_clock")
 
 
 class Grid(C.Structure):
@@ -70,6 +71,20 @@ class Stats(C.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["update_hist"] = list(self.update_hist)[:max(0, self.newton_iters_last)]
         return d
+
+
+class Request(C.Structure):
+    _fields_ = [("grid", Grid), ("h", C.c_double), ("chi", C.c_double), ("nsteps", C.c_int),
+                ("v", C.c_void_p), ("re", C.c_void_p), ("im", C.c_void_p), ("arrival", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("done", C.c_int), ("steps_done", C.c_longlong),
+                ("newton_iters_total", C.c_longlong), ("arrival", C.c_double), ("admitted", C.c_double),
+                ("completed", C.c_double), ("energy_start", C.c_double), ("energy_end", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class MB4Error(RuntimeError):
@@ -126,6 +141,14 @@ def lib():
         L.mb4_batch_clear_errors.argtypes = [_P]
         L.mb4_batch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(Options)]
         L.mb4_batch_bytes.restype = C.c_longlong
+        L.mb4_server_create.argtypes = [C.c_longlong, C.c_int, C.c_int, C.POINTER(Options), C.POINTER(_P)]
+        L.mb4_server_destroy.argtypes = [_P]
+        L.mb4_server_destroy.restype = None
+        L.mb4_server_submit.argtypes = [_P, C.POINTER(Request), C.POINTER(C.c_longlong)]
+        L.mb4_server_run.argtypes = [_P, C.c_double, C.POINTER(C.c_longlong)]
+        L.mb4_server_result.argtypes = [_P, C.c_longlong, C.POINTER(Result), _P, _P]
+        L.mb4_server_clock.argtypes = [_P]
+        L.mb4_server_clock.restype = C.c_double
         _lib = L
     return _lib
 
@@ -448,6 +471,64 @@ class Batch:
 
     def clear_errors(self):
         _check(lib().mb4_batch_clear_errors(self._ctx), "mb4_batch_clear_errors")
+
+
+class Server:
+    """Continuous-batching server (mb4_server_*): requests of different grids, h,
+    step counts and potentials share the GPU inside an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=64, keep_states=False, **opts):
+        self._ctx = _P()
+        _check(lib().mb4_server_create(int(hbm_budget_bytes), int(max_slots), 1 if keep_states else 0,
+                                       C.byref(_options(**opts)), C.byref(self._ctx)), "mb4_server_create")
+        self.sizes = {}
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().mb4_server_destroy(self._ctx)
+            self._ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, nx, ny, V, chi, psi, h, nsteps, arrival=0.0, tx=1.0, ty=None, onsite=0.0):
+        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+        p = _Planar(psi, nx * ny)
+        req = Request(Grid(int(nx), int(ny), float(tx), float(tx if ty is None else ty), float(onsite)),
+                      float(h), float(chi), int(nsteps), Vh.ctypes.data, p.pre, p.pim, float(arrival))
+        rid = C.c_longlong()
+        _check(lib().mb4_server_submit(self._ctx, C.byref(req), C.byref(rid)), "mb4_server_submit")
+        self.sizes[rid.value] = nx * ny
+        return rid.value
+
+    def run(self, until=1e300):
+        n = C.c_longlong()
+        _check(lib().mb4_server_run(self._ctx, float(until), C.byref(n)), "mb4_server_run")
+        return n.value
+
+    def result(self, rid, state=False):
+        res = Result()
+        if state:
+            S = self.sizes[rid]
+            re = np.empty(S)
+            im = np.empty(S)
+            _check(lib().mb4_server_result(self._ctx, int(rid), C.byref(res), re.ctypes.data, im.ctypes.data),
+                   "mb4_server_result")
+            return res.as_dict(), re + 1j * im
+        _check(lib().mb4_server_result(self._ctx, int(rid), C.byref(res), None, None), "mb4_server_result")
+        return res.as_dict()
+
+    def clock(self):
+        return lib().mb4_server_clock(self._ctx)
 
 
 def from_workload(w, precision="fp64", **kw):

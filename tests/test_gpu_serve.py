@@ -1,0 +1,100 @@
+"""Continuous-batching server (mb4_server_*): requests of different grid sizes,
+step sizes, step counts and potentials arrive over time, share the GPU inside an
+HBM budget, and each result equals the same simulation run alone."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_04345_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mb4():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2003_04345_gb300 import mb4 as m
+    m.lib()
+    return m
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def _trace(n_req, seed=0, span=0.05):
+    rng = np.random.default_rng(seed)
+    sizes = [(16, 16), (24, 24), (32, 20)]
+    hs = [0.01, 0.005]
+    reqs = []
+    for r in range(n_req):
+        nx, ny = sizes[rng.integers(len(sizes))]
+        h = hs[rng.integers(len(hs))]
+        steps = int(rng.integers(3, 41))
+        chi = float(rng.uniform(0, 2))
+        V = inputs.potential(nx, ny, 1.0, 2, 20.0, 100 + r)
+        psi = inputs.wavepacket(nx, ny, 2.5, math.pi / 4, 0.2 * (r % 3))
+        reqs.append(dict(nx=nx, ny=ny, h=h, nsteps=steps, chi=chi, V=V, psi=psi, arrival=float(span * r / n_req)))
+    return reqs
+
+
+def _solo(mb4, q, **opts):
+    with mb4.Integrator(q["nx"], q["ny"], q["V"], q["chi"], q["h"], **opts) as it:
+        it.set_state(q["psi"])
+        it.step(q["nsteps"])
+        return it.get_state()
+
+
+def test_served_results_equal_solo_runs(mb4):
+    reqs = _trace(14)
+    with mb4.Server(2 << 30, max_slots=4, keep_states=True, precision="mixed") as srv:
+        ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], q["arrival"])
+               for q in reqs]
+        done = srv.run()
+        assert done == len(reqs)
+        results = [srv.result(i, state=True) for i in ids]
+    spans = []
+    for q, (res, u) in zip(reqs, results):
+        assert res["done"] == 1 and res["status"] == 0
+        assert res["steps_done"] == q["nsteps"]
+        assert res["admitted"] >= res["arrival"] - 1e-9 and res["completed"] >= res["admitted"]
+        assert abs(res["energy_end"] - res["energy_start"]) <= 1e-13 * abs(res["energy_start"])
+        assert _rel(u, _solo(mb4, q, precision="mixed")) <= 1e-12
+        spans.append((res["admitted"], res["completed"]))
+    # continuous batching: some requests were on the GPU at the same time
+    overlaps = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
+                   if spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1])
+    assert overlaps > 0
+
+
+def test_budget_limits_concurrency(mb4):
+    reqs = [dict(q, nx=32, ny=20) for q in _trace(5, seed=1)]
+    for q in reqs:
+        q["V"] = inputs.potential(32, 20, 1.0, 2, 20.0, 7)
+        q["psi"] = inputs.wavepacket(32, 20, 2.5, math.pi / 4, 0.0)
+    one = mb4.batch_bytes(32, 20, 1, precision="mixed")
+    with mb4.Server(one + one // 2, max_slots=8, keep_states=True, precision="mixed") as srv:
+        ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], 0.0) for q in reqs]
+        assert srv.run() == len(reqs)
+        results = [srv.result(i, state=True) for i in ids]
+    by_h = {}
+    for q, (res, u) in zip(reqs, results):
+        assert res["status"] == 0 and res["steps_done"] == q["nsteps"]
+        assert _rel(u, _solo(mb4, q, precision="mixed")) <= 1e-12
+        by_h.setdefault(q["h"], []).append((res["admitted"], res["completed"]))
+    for spans in by_h.values():        # one slot fits: a class never runs two requests at once
+        spans.sort()
+        for a, b in zip(spans, spans[1:]):
+            assert b[0] >= a[1] - 1e-9
+
+
+def test_request_larger_than_budget_is_rejected(mb4):
+    V = np.zeros(64 * 64)
+    psi = inputs.wavepacket(64, 64, 4.0, 0.0, 0.0)
+    with mb4.Server(1 << 16, max_slots=2) as srv:
+        with pytest.raises(mb4.MB4Error) as e:
+            srv.submit(64, 64, V, 1.0, psi, 0.01, 10)
+        assert e.value.code == mb4.MB4_ERR_ADMISSION_REJECTED
