@@ -142,14 +142,8 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.h = h;
   for (int i = 0; i < 3; ++i) {
     p.hlam[i] = h * K.lam[i];
-    double e0 = 0, tau = 0, tc = 0;
-    for (int j = 0; j < 3; ++j) {
-      e0 += K.Tinv[i][j] * K.E[j][0];
-      tau += K.Tinv[i][j];
-      tc += K.Tinv[i][j] * K.c[j];
-    }
-    p.he0[i] = h * e0;
-    p.tau[i] = tau;
+    double tc = 0;
+    for (int j = 0; j < 3; ++j) tc += K.Tinv[i][j] * K.c[j];
     p.hTc[i] = h * tc;
     for (int j = 0; j < 3; ++j) p.T[i][j] = K.T[i][j];
   }
@@ -157,7 +151,6 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
     const double z = K.gx[q];
     double l[4];
     for (int j = 0; j < 4; ++j) l[j] = ((K.lag[j][3] * z + K.lag[j][2]) * z + K.lag[j][1]) * z + K.lag[j][0];
-    p.L0[q] = l[0];
     for (int n = 0; n < 3; ++n) {
       double s = 0;
       for (int m = 0; m < 3; ++m) s += l[m + 1] * K.T[m][n];
@@ -657,7 +650,12 @@ int mb4_get_stages(const mb4_ctx* cc, double* re3, double* im3, int on_device) {
   mb4_ctx* c = const_cast<mb4_ctx*>(cc);
   if (!c || !re3 || !im3) return MB4_ERR_INVALID_ARG;
   MB4_CHECK(ensure_scratch(c));
-  launch_mix3(c->p.S, c->b.Ubar, c->tmp3a, c->p.T, c->stream);
+  // U_j = u0 + sum_n T[j][n] dU_n and u1 = u0 + sum_n T[2][n] dU_n, so U_j = u1 + sum_n (T[j][n] - T[2][n]) dU_n
+  double M[3][3];
+  for (int j = 0; j < 3; ++j)
+    for (int n = 0; n < 3; ++n) M[j][n] = c->k.T[j][n] - c->k.T[2][n];
+  launch_mix3(c->p.S, c->b.Ubar, c->tmp3a, M, c->stream);
+  launch_add_plane3(c->p.S, c->tmp3a, c->b.u, 1.0, c->stream);
   MB4_TRY(cudaGetLastError());
   return stage_out(c, c->tmp3a, re3, im3, 3 * (size_t)c->p.S, on_device);
 }
@@ -704,6 +702,7 @@ int mb4_residual(mb4_ctx* c, const double* u0_re, const double* u0_im, const dou
   const double *dre, *dim;
   MB4_CHECK(stage_in(c, U_re3, U_im3, 3 * S, on_device, &dre, &dim));
   launch_pack(dre, dim, c->tmp3a, 3 * S, c->stream);
+  launch_add_plane3((int)S, c->tmp3a, c->b.u, -1.0, c->stream);   // U_j - u0
   launch_mix3((int)S, c->tmp3a, c->b.Ubar, c->k.Tinv, c->stream);
   if (c->precision == MB4_MIXED) launch_residual_out<float>(c->p, c->b, c->tmp3b, c->stream);
   else launch_residual_out<double>(c->p, c->b, c->tmp3b, c->stream);

@@ -39,14 +39,11 @@ struct StepParams {
   int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   double tx, ty, eps0, h;
-  // residual in the eigenbasis of E: Ubar = Tinv U
+  // residual in the eigenbasis of E on the increments dU = Tinv (U - e3 (x) u0)
   double hlam[3];          // h * lambda_i
-  double he0[3];           // h * (Tinv E_{.0})_i
-  double tau[3];           // (Tinv 1)_i : Ubar^0 = tau (x) u0
-  double hTc[3];           // h * (Tinv c)_i : Phibar^0 = i hTc_i f-part at u0
-  double L0[kGauss];       // l_0(zeta_q)
-  double LT[kGauss][3];    // sum_m l_m(zeta_q) T[m][n]
-  double T[3][3];          // r = T rbar ;  u1 = sum_n T[2][n] Ubar_n
+  double hTc[3];           // h * (Tinv c)_i : the (K+V) u0 coefficient, and Phibar^0 = i hTc_i f(u0)-part
+  double LT[kGauss][3];    // sum_m l_m(zeta_q) T[m][n]:  X_q = u0 + sum_n LT[q][n] dU_n
+  double T[3][3];          // r = T rbar ;  u1 = u0 + sum_n T[2][n] dU_n
   double newton_rtol;
   double newton_predict;   // 0: off; else Hairer-Wanner predicted-error stop
   int newton_max;
@@ -105,7 +102,7 @@ struct DevBuffers {
   double* V;         // potential, B*S
   double* d;         // onsite + V, B*S
   double2* S0;       // (K+V) u0, B*S
-  double2* Ubar;     // transformed stages, B*3*S
+  double2* Ubar;     // transformed stage increments dU, B*3*S
   void* jc;          // J coefficients {e1, e2, a, 0} (TK4), B*S
   void* v;           // Krylov basis, B*(s+1)*3*S of TK2; level 0 = right-hand side b
   double* gram_part; // B*3*gram_blocks*nent
@@ -136,6 +133,8 @@ void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 int obs_blocks_per_instance(int B);
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// Y_j += sign * x on three complex planes of S sites.
+void launch_add_plane3(int S, double2* Y, const double2* x, double sign, cudaStream_t st);
 // Y_j = sum_n M[j][n] X_n on three complex planes of S sites.
 void launch_mix3(int S, const double2* X, double2* Y, const double M[3][3], cudaStream_t st);
 template <typename TK> void launch_copy_rhs_in(const StepParams& p, const DevBuffers& b, const double2* b3,

@@ -3,12 +3,16 @@
 //
 // Data layout: complex planes are interleaved (re, im) pairs, site k = y*nx + x;
 // every per-instance array is instance-major (instance b's planes are
-// contiguous).  The Newton iteration runs in the eigenbasis of E
-// (Ubar = T^-1 U, Sec. 2.2, eq. MB4_4..MB4_6): the T and T^-1 mixes of
-// Algorithm 1 then fold into constants, the linear part of the residual needs
-// only one stencil per stage (T^-1 E T = Lambda), and the update is
-// Ubar += rbar.  Each instance keeps its own Newton status; an instance that
-// has converged (or failed) is masked while the others iterate.
+// contiguous).  The Newton iteration runs in the eigenbasis of E on the stage
+// increments dU = T^-1 (U - e3 (x) u0) (Sec. 2.2, eq. MB4_4..MB4_6): the T and
+// T^-1 mixes of Algorithm 1 then fold into constants, the linear part of the
+// residual needs only one stencil per stage (T^-1 E T = Lambda), the update is
+// dU += rbar, and the step is u1 = u0 + sum_n T[2][n] dU_n.  Carrying
+// increments keeps the identity part of the step exact: with the constants
+// rounded to FP64, u1 = sum_n T[2][n] Ubar_n would scale every step by
+// T[2] . T^-1 1 = 1 - O(1e-16) and the energy would drift linearly in time.
+// Each instance keeps its own Newton status; an instance that has converged
+// (or failed) is masked while the others iterate.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -115,8 +119,8 @@ __device__ __forceinline__ size_t level(int b, int a, int i, int s, int S) {
 // polynomial value equals u0, so Phi_i(U^0) = -h c_i f(u0) and the first
 // right-hand side is b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].
 // J and b^0 only feed the Krylov solve, so they are formed in its precision TK;
-// (K+V) u0 is reused by every residual and stays FP64.  Ubar^0 = tau (x) u0 is
-// formed by the first update.  Grid: (sites / 256, B).
+// (K+V) u0 is reused by every residual and stays FP64.  The increments start at
+// dU^0 = 0 (the first update writes them).  Grid: (sites / 256, B).
 // ---------------------------------------------------------------------------
 template <typename TK>
 __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __restrict__ u,
@@ -175,16 +179,17 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Residual (Algorithm 1 lines 13-14, eq. Phidefinition, eq. fKu2, eq. fIu2) in
-// the eigenbasis: b = -Phibar with
-//   Phibar_i = Ubar_i - tau_i u0 + i [ h lam_i (K+V) Ubar_i + h e0_i (K+V) u0
-//                                      + sum_q h chi W~_iq |X_q|^2 X_q ],
-//   X_q = l_0(zeta_q) u0 + sum_n (L T)_qn Ubar_n   (the stage polynomial at the
-// 6 Gauss nodes; exact for the degree-11 integrand).  All FP64.
+// the eigenbasis, on the increments dU: b = -Phibar with
+//   Phibar_i = dU_i + i [ h lam_i (K+V) dU_i + h (T^-1 c)_i (K+V) u0
+//                         + sum_q h chi W~_iq |X_q|^2 X_q ],
+//   X_q = u0 + sum_n (L T)_qn dU_n   (the stage polynomial at the 6 Gauss nodes;
+// exact for the degree-11 integrand).  (The u0 terms: T^-1 E T = Lambda and
+// T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
 // ---------------------------------------------------------------------------
 template <typename TO>
 __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
-                                                  const double2* __restrict__ Ubar,
+                                                  const double2* __restrict__ dUb,
                                                   typename Vec2<TO>::type* __restrict__ out, long long out_stride,
                                                   int skip_first, const InstConst* __restrict__ ic,
                                                   const InstStatus* is) {
@@ -200,20 +205,16 @@ __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* _
   const double2 u0 = u[plane(b, S) + k];
   const double2 s0 = S0[plane(b, S) + k];
   const double d = D[plane(b, S) + k];
-  // dU_m = Ubar_m - tau_m u0: the departure of the stages from the trivial guess.
-  // The stage polynomial at node q is then X_q = u0 + sum_m (L T)_qm dU_m (since
-  // l_0(zeta) + sum_m (L T)_qm tau_m = 1), and b_i = -dU_i + i-rotated sums.
   double2 dU[3], acc[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    const double2* P = Ubar + stage(b, m, S);
+    const double2* P = dUb + stage(b, m, S);
     double2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-    dU[m].x = fma(-p.tau[m], u0.x, c.x);
-    dU[m].y = fma(-p.tau[m], u0.y, c.y);
+    dU[m] = c;
     double sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
     double sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
-    acc[m].x = fma(p.hlam[m], sx, p.he0[m] * s0.x);
-    acc[m].y = fma(p.hlam[m], sy, p.he0[m] * s0.y);
+    acc[m].x = fma(p.hlam[m], sx, p.hTc[m] * s0.x);
+    acc[m].y = fma(p.hlam[m], sy, p.hTc[m] * s0.y);
   }
 #pragma unroll
   for (int q = 0; q < kGauss; ++q) {
@@ -660,8 +661,8 @@ __device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaG
 }
 
 // Newton update (Algorithm 1 lines 18-20) and loop test (line 12; failure rule of
-// Sec. 2.2): rbar_i = sum_a c_ia v_a,i; Ubar_i += rbar_i in FP64 (Ubar^0 = tau u0 on
-// the first iteration); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
+// Sec. 2.2): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (dU^0 = 0, so the
+// first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
 // block of each instance runs its test: continue while ||r^l||_inf > rtol ||u0||_inf
 // (and, when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
 // for at most newton_max iterations.  Grid: (sites / 256, B).
@@ -704,14 +705,12 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
       x[i].x = sx;
       x[i].y = sy;
     }
-    double2 u0;
-    if (first) u0 = u[plane(inst, S) + k];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       double2 U;
       if (first) {
-        U.x = fma(p.tau[i], u0.x, to_double(x[i].x));
-        U.y = fma(p.tau[i], u0.y, to_double(x[i].y));
+        U.x = to_double(x[i].x);
+        U.y = to_double(x[i].y);
       } else {
         U = Ubar[stage(inst, i, S) + k];
         U.x += to_double(x[i].x);
@@ -790,7 +789,7 @@ void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long 
 #undef MB4_CALL
 }
 
-// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = sum_n T[2][n] Ubar_n, for the
+// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = u0 + sum_n T[2][n] dU_n, for the
 // instances that took part in the step and did not fail.  Block 0 of each instance
 // books the step and re-arms the instance for the next one.
 __global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restrict__ u,
@@ -803,9 +802,9 @@ __global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restric
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (took_part && !failed && k < S) {
     double2 a = Ubar[stage(inst, 0, S) + k], b = Ubar[stage(inst, 1, S) + k], c = Ubar[stage(inst, 2, S) + k];
-    double2 r;
-    r.x = fma(p.T[2][2], c.x, fma(p.T[2][1], b.x, p.T[2][0] * a.x));
-    r.y = fma(p.T[2][2], c.y, fma(p.T[2][1], b.y, p.T[2][0] * a.y));
+    double2 r = u[plane(inst, S) + k];
+    r.x = fma(p.T[2][2], c.x, fma(p.T[2][1], b.x, fma(p.T[2][0], a.x, r.x)));
+    r.y = fma(p.T[2][2], c.y, fma(p.T[2][1], b.y, fma(p.T[2][0], a.y, r.y)));
     u[plane(inst, S) + k] = r;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -992,6 +991,24 @@ __global__ void k_mix3(int S, const double2* __restrict__ X, double2* __restrict
   Y[k] = make_double2(m00 * a.x + m01 * b.x + m02 * c.x, m00 * a.y + m01 * b.y + m02 * c.y);
   Y[(size_t)S + k] = make_double2(m10 * a.x + m11 * b.x + m12 * c.x, m10 * a.y + m11 * b.y + m12 * c.y);
   Y[(size_t)2 * S + k] = make_double2(m20 * a.x + m21 * b.x + m22 * c.x, m20 * a.y + m21 * b.y + m22 * c.y);
+}
+
+// Z_j = Y_j + sign * x on three planes (adds or removes u0 from stage values).
+__global__ void k_add_plane3(int S, double2* __restrict__ Y, const double2* __restrict__ x, double sign) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= S) return;
+  const double2 a = x[k];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double2 y = Y[(size_t)j * S + k];
+    y.x = fma(sign, a.x, y.x);
+    y.y = fma(sign, a.y, y.y);
+    Y[(size_t)j * S + k] = y;
+  }
+}
+
+void launch_add_plane3(int S, double2* Y, const double2* x, double sign, cudaStream_t s) {
+  k_add_plane3<<<(S + 255) / 256, 256, 0, s>>>(S, Y, x, sign);
 }
 
 void launch_mix3(int S, const double2* X, double2* Y, const double M[3][3], cudaStream_t s) {

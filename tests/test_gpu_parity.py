@@ -296,3 +296,46 @@ def test_grid512_translation_equivariance(mb4):
         ua = a.get_state().reshape(w.ny, w.nx)
         ub = b.get_state().reshape(w.ny, w.nx)
     assert _rel(ub, roll(ua)) <= 1e-13
+
+
+def test_grid2048_mixed_matches_fp64(mb4):
+    """2048x2048 (W = 2, 1% defects, chi = 2, h = 0.002): FP32 inner solves do not
+    move the root -- mixed and FP64 agree to the parity tolerance after 3 steps."""
+    w = inputs.grid2048_mixed()
+    finals = {}
+    for precision in PRECISIONS:
+        with mb4.from_workload(w, precision=precision) as it:
+            H0 = it.energy()[0]
+            it.step(3)
+            finals[precision] = it.get_state()
+            assert abs(it.energy()[0] - H0) <= 1e-13 * abs(H0)
+    assert _rel(finals["mixed"], finals["fp64"]) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_grid128_with_2048_physics_matches_oracle(mb4, precision):
+    """The 128x128 instance with the 2048x2048 physics, 10 steps, against the oracle."""
+    w = inputs.grid128_crop_of_2048()
+    prob = orc.Problem(w.nx, w.ny, w.potential(), w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
+    u, _ = orc.run(prob, w.psi0(), w.h, 10)
+    with mb4.from_workload(w, precision=precision) as it:
+        it.step(10)
+        got = it.get_state()
+    assert _rel(got, u) <= 1e-11
+    assert _rel2(got, u) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_energy_drift_long_run(mb4, precision):
+    """4000 steps (64x64, h = 0.01, 2% defects, chi = 1): |dH/H| stays at the
+    1e-13 level with no drift proportional to the step count (a systematic
+    per-step bias of 1e-16 would reach 4e-13 here)."""
+    w = inputs.Workload("long64", 64, 64, h=0.01, steps=4000, chi=1.0, W=1.0, defect_fraction=0.02,
+                        sigma=6.0, seed=17)
+    with mb4.from_workload(w, precision=precision, newton_predict=1e-16) as it:
+        H0 = it.energy()[0]
+        worst = 0.0
+        for _ in range(8):
+            it.step(w.steps // 8)
+            worst = max(worst, abs(it.energy()[0] - H0) / abs(H0))
+    assert worst <= 1e-13, worst
