@@ -18,6 +18,7 @@ path has no exchange step); rank 0 prints the line with the max over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -33,6 +34,7 @@ if ROOT not in sys.path:
 METRIC = "MB4 site-steps/s at |ΔH/H|≤1e-13, mixed vs FP64 path; served p50/p99 latency"
 UNIT = "site-steps/s"
 FP64_PEAK_DERIVED = 152 * 2070e6 * 2 * 2   # SMs x max SM clock x 2 DFMA/clk/SM x 2 flop (GB300, FP64)
+FP64_ISSUE_PEAK = 152 * 2070e6 * 2         # FP64 instructions (per thread) per second
 LOG_EVERY = 10
 
 
@@ -46,21 +48,54 @@ def _peaks():
 
 # Algorithmic work per kernel launch, per site (flops: FMA = 2), and bytes per site.
 def kernel_model(kclass, precision, s):
+    """Algorithmic work of one launch per site: flops (FMA = 2), FP64 instructions
+    (DFMA, DADD and DMUL one each: what occupies the FP64 pipe) and bytes (each
+    array read or written once)."""
     tk = 8 if precision == "fp64" else 4
     ne = (s + 1) * (s + 2) // 2
+    f64 = precision == "fp64"
     if kclass == "residual":
-        return {"flops": 264, "bytes": 16 + 16 + 8 + 48 + 6 * tk, "fp64": True}
+        return {"flops": 264, "fp64_ops": 144, "bytes": 16 + 16 + 8 + 48 + 6 * tk, "fp64": True}
     if kclass == "matvec":
-        return {"flops": 54, "bytes": 6 * tk + 4 * tk + 6 * tk, "fp64": precision == "fp64"}
+        return {"flops": 54, "fp64_ops": 36 if f64 else 0, "bytes": 6 * tk + 4 * tk + 6 * tk, "fp64": f64}
     if kclass == "gram":   # Gram partial sums (+ the last block's reduction and least squares)
-        return {"flops": 3 * ne * 4, "bytes": (s + 1) * 6 * tk, "fp64": precision == "fp64"}
+        return {"flops": 3 * ne * 4, "fp64_ops": 3 * ne * 2 if f64 else 0, "bytes": (s + 1) * 6 * tk, "fp64": f64}
     if kclass == "update":
-        return {"flops": 3 * s * 4 + 6 + 36, "bytes": s * 6 * tk + 48 + 48, "fp64": precision == "fp64"}
+        return {"flops": 3 * s * 4 + 6 + 36, "fp64_ops": 6 * (s + 1) if f64 else 6,
+                "bytes": s * 6 * tk + 48 + 48, "fp64": f64}
     if kclass == "setup":
-        return {"flops": 40, "bytes": 16 + 8 + 16 + 48 + 4 * tk + 6 * tk, "fp64": True}
+        return {"flops": 40, "fp64_ops": 0, "bytes": 16 + 8 + 16 + 48 + 4 * tk + 6 * tk, "fp64": True}
     if kclass == "accept":
-        return {"flops": 12, "bytes": 48 + 16, "fp64": True}
-    return {"flops": 0, "bytes": 0, "fp64": False}
+        return {"flops": 12, "fp64_ops": 0, "bytes": 48 + 16, "fp64": True}
+    return {"flops": 0, "fp64_ops": 0, "bytes": 0, "fp64": False}
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_grid512.txt")
+KERNEL_SOURCES = ("paper_2003_04345_gb300/csrc/mb4_kernels.cu", "paper_2003_04345_gb300/csrc/mb4_internal.h")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kclass, precision):
+    """DRAM bytes (read + write) per launch of a kernel class on the 512x512
+    workload, from the committed ncu summary; None when the summary has no such
+    line or was taken from other kernel sources than the ones built here."""
+    try:
+        digest = kernel_source_hash()
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                f = line.split()
+                if len(f) >= 5 and f[0] == "traffic" and f[1] == kclass and f[2] == precision:
+                    return float(f[3]) if f[4] == digest else None
+    except OSError:
+        pass
+    return None
 
 
 class ClockSampler:
@@ -135,27 +170,30 @@ def max_over_ranks(x, world, device):
 
 
 def timed_steps(it, K, flush, log_every=LOG_EVERY):
-    """K MB4 steps; each bracketed by CUDA events on the library's stream (the
-    current torch stream); L2 flushed between steps outside the brackets."""
+    """K MB4 steps queued with mb4_step_async, each bracketed by CUDA events on
+    the library's stream (the current torch stream); L2 flushed between steps
+    outside the brackets; energy and norm read back every log_every steps (inside
+    the bracket of that step).  Returns (ms, Newton iterations, observable calls, H)."""
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    newton = 0
     obs_calls = 0
     H = []
     for k in range(K):
         a, b = evs[k]
         a.record()
-        st = it.step(1)
+        it.step_async(1)
         if log_every and (k + 1) % log_every == 0:
             o = it.observables()
             H.append(o["H"])
             obs_calls += 1
         b.record()
-        newton += st["newton_iters_total"]
         flush()
+    st = it.wait()
     torch.cuda.synchronize()
+    if st["steps_done"] != K:
+        raise RuntimeError(f"{st['steps_done']} of {K} steps done")
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    return ms, newton, obs_calls, H
+    return ms, st["newton_iters_total"], obs_calls, H
 
 
 def run_ours(args):
@@ -201,7 +239,10 @@ def run_ours(args):
             "value": world * S * K / (ms_max / 1e3), "ms_per_step": ms_max / K, "wall_s": wall,
             "newton_per_step": newton / K, "energy_drift": drift,
             "norm_drift": abs(o1["norm2"] - o0["norm2"]), "krylov_s": s_dim,
-            "launches": K * 2 + newton * (s_dim + 3) + 2 * obs_calls, "obs_calls": obs_calls,
+            # per step: arm, setup, accept; per Newton iteration: residual, s basis
+            # launches (one matrix-powers launch in mixed mode), Gram, update; 2 per log
+            "launches": K * 3 + newton * ((s_dim if precision == "fp64" else 1) + 3) + 2 * obs_calls,
+            "obs_calls": obs_calls,
         }
         # per-kernel device times from the event-instrumented run of the same steps
         kp = min(K, 100)
@@ -255,7 +296,13 @@ def run_ours(args):
         roof = {"bound": "hbm", "kernel": dom, "achieved": bytes_per_launch / (us * 1e-6) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    if model["fp64_ops"]:
+        # the same launch against the FP64 pipe's instruction rate (an add or a
+        # multiply takes a DFMA's slot, so the flop fraction understates pipe use)
+        ops = model["fp64_ops"] * S / (us * 1e-6)
+        roof["fp64_issue"] = {"ops_per_site": model["fp64_ops"], "achieved_gops": ops / 1e9,
+                              "peak_gops": FP64_ISSUE_PEAK / 1e9, "frac": ops / FP64_ISSUE_PEAK}
+    roof["traffic"] = measured_traffic(dom, "fp64")
     roof["algorithmic_per_site"] = {"flops": model["flops"], "bytes": model["bytes"]}
 
     line = {
@@ -281,6 +328,10 @@ def run_ours(args):
         "gpu_launches": fp["launches"],
         "clocks": clocks,
     }
+    if not args.no_extra:
+        line["ensemble"] = bench_ensemble(args, flush)
+        line["grid2048"] = bench_grid2048(args, flush)
+        line["served"] = bench_served(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0:
@@ -288,6 +339,110 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _timed_batch_steps(bt, K, flush):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        evs[k][0].record()
+        bt.step_async(1)
+        evs[k][1].record()
+        flush()
+    stats, codes = bt.wait()
+    torch.cuda.synchronize()
+    if any(codes):
+        raise RuntimeError(f"batch step failed: {sorted(set(codes))}")
+    return sum(a.elapsed_time(b) for a, b in evs), sum(st["newton_iters_total"] for st in stats)
+
+
+def bench_ensemble(args, flush, K=20):
+    """The 1024-member 128x128 ensemble (chi ~ U[0, 2] per seed, 1% defects,
+    sigma = 8, h = 0.01) as one batch, mixed precision: every launch covers all
+    members (16.8M sites per step)."""
+    import numpy as np
+    import torch
+    from paper_2003_04345_gb300 import inputs, mb4
+    B, n = 1024, 128
+    ws = [inputs.ensemble128(seed) for seed in range(B)]
+    V = np.stack([w.potential() for w in ws])
+    chi = np.array([w.chi for w in ws])
+    psi = np.stack([w.psi0() for w in ws])
+    out = {"workload": "ensemble1024_grid128", "members": B, "nx": n, "ny": n, "h": ws[0].h}
+    for precision in ("mixed", "fp64"):
+        with mb4.Batch(n, n, V, chi, ws[0].h, precision=precision,
+                       stream=torch.cuda.current_stream()) as bt:
+            bt.set_state(psi)
+            H0 = bt.observables()[:, 0]
+            bt.step(3)
+            ms, newton = _timed_batch_steps(bt, K, flush)
+            H1 = bt.observables()[:, 0]
+        out[precision] = {"value": B * n * n * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
+                          "newton_per_member_step": newton / (B * K),
+                          "energy_drift_max": float(np.max(np.abs(H1 - H0) / np.abs(H0)))}
+    return out
+
+
+def bench_grid2048(args, flush, K=20):
+    """2048x2048, disorder in [-1, 1], 1% defects, chi = 2, h = 0.002: mixed and
+    FP64 on the same inputs, and their difference after K steps."""
+    import numpy as np
+    import torch
+    from paper_2003_04345_gb300 import inputs, mb4
+    w = inputs.grid2048_mixed()
+    out = {"workload": "grid2048_mixed", "nx": w.nx, "ny": w.ny, "h": w.h}
+    finals = {}
+    for precision in ("mixed", "fp64"):
+        with mb4.from_workload(w, precision=precision, stream=torch.cuda.current_stream()) as it:
+            H0 = it.energy()[0]
+            it.step(3)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            newton = 0
+            for k in range(K):
+                evs[k][0].record()
+                st = it.step(1)
+                evs[k][1].record()
+                newton += st["newton_iters_total"]
+                flush()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs)
+            finals[precision] = it.get_state()
+            H1 = it.energy()[0]
+        out[precision] = {"value": w.S * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+                          "newton_per_step": newton / K, "energy_drift": abs(H1 - H0) / abs(H0)}
+    a, b = finals["mixed"], finals["fp64"]
+    out["mixed_vs_fp64_rel_linf"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    out["steps_compared"] = K + 3
+    return out
+
+
+def bench_served(args, n_requests=24, rate=200.0):
+    """The served stream: Poisson arrivals at 200 req/s of simulations with grid
+    sizes in {64^2 .. 1024^2}, step counts in [100, 5000], h in {0.002, 0.005,
+    0.01}, per-request seed and defect density 0-2%, replayed for the first
+    n_requests arrivals through the continuous-batching server (mixed precision,
+    64 GiB HBM budget).  Latency = completion - arrival."""
+    import numpy as np
+    from paper_2003_04345_gb300 import inputs, mb4
+    trace = inputs.served_trace(n_requests, rate, seed=0)
+    site_steps = 0
+    with mb4.Server(64 << 30, max_slots=64, keep_states=False, precision="mixed") as srv:
+        ids = []
+        for t, w in trace:
+            ids.append(srv.submit(w.nx, w.ny, w.potential(), w.chi, w.psi0(), w.h, w.steps, arrival=t))
+            site_steps += w.S * w.steps
+        t0 = srv.clock()
+        done = srv.run()
+        makespan = srv.clock() - min(t for t, _ in trace)
+        res = [srv.result(i) for i in ids]
+    lat = np.array([r["completed"] - r["arrival"] for r in res])
+    drift = max(abs(r["energy_end"] - r["energy_start"]) / abs(r["energy_start"]) for r in res)
+    return {"workload": "served_poisson200", "requests": n_requests, "completed": int(done),
+            "rate_req_per_s": rate, "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)), "latency_max_s": float(lat.max()),
+            "value": site_steps / makespan, "unit": UNIT, "makespan_s": makespan,
+            "site_steps": site_steps, "energy_drift_max": drift,
+            "errors": int(sum(1 for r in res if r["status"] != 0)), "setup_s": t0}
 
 
 def _oracle_sample(n=64):
@@ -345,6 +500,20 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_case(precision):
+    """A few steps of the 512x512 workload with the host-driven Newton loop, so
+    that every kernel is its own launch (the form ncu captures kernel by kernel)."""
+    import torch
+    from paper_2003_04345_gb300 import inputs, mb4
+    w = inputs.grid512_fp64()
+    with mb4.from_workload(w, precision=precision, use_graph=False) as it:
+        it.step(5)
+        torch.cuda.synchronize()
+        st = it.step(1)
+        it.observables()
+    print(json.dumps({"profile_case": precision, "newton_iters_last": st["newton_iters_last"]}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,7 +522,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=["fp64", "mixed"],
+                    help="run 6 host-driven steps of the 512x512 workload for ncu and exit")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the ensemble, 2048^2 and served-stream lines")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -102,6 +102,10 @@ typedef struct {
                             Sec. IV.8); the iterate is then accurate to that bound, so a value at
                             the rounding level (1e-16) skips only an iteration that changes U by
                             less than rounding                                                */
+    int    overlap_launches; /* 1 (default): the kernels inside the Newton loop use programmatic
+                            dependent launch, so each one's blocks are resident while its
+                            predecessor drains (they wait for its completion before reading
+                            its results; same arithmetic, same results); 0: plain launches    */
 } mb4_options;
 
 #define MB4_MAX_KRYLOV_S 10
@@ -144,6 +148,18 @@ int mb4_get_stages(const mb4_ctx* ctx, double* re3, double* im3, int on_device);
  * state stays at the last accepted step and the code is returned; stats
  * (nullable) reports what was done.  Synchronises the context's stream. */
 int mb4_step(mb4_ctx* ctx, int nsteps, mb4_stats* stats);
+
+/* Enqueues nsteps MB4 steps on the context's stream and returns at once: no
+ * host synchronisation, no read-back.  Several calls queue back to back with any
+ * other work on the stream.  A step that fails stops the context where mb4_step
+ * would; the queued steps after it do nothing.  Not part of the paper's method:
+ * the asynchronous form of mb4_step for callers that overlap their own work. */
+int mb4_step_async(mb4_ctx* ctx, int nsteps);
+
+/* Waits for the context's queued steps.  stats (nullable) covers every step
+ * since the previous mb4_wait / mb4_step; returns the code of a failed step (and
+ * then clears it, so that later steps start from the last accepted state). */
+int mb4_wait(mb4_ctx* ctx, mb4_stats* stats);
 
 /* Kernel classes reported by mb4_step_profiled. */
 #define MB4_K_SETUP        0   /* u0, (K+V)u0, J coefficients, first right-hand side          */

@@ -33,6 +33,8 @@ struct mb4_batch {
   double* io = nullptr;           // 6*max(B*S, S) doubles
   std::vector<void*> allocs;
   std::vector<InstStatus> host_status;
+  // device step counters at the last wait: stats report the steps since then
+  std::vector<long long> base_steps, base_newton;
 };
 
 struct mb4_ctx : mb4_batch {};
@@ -81,6 +83,7 @@ int validate_options(const mb4_options* in, mb4_options* o) {
   if (o->krylov_s == 0) o->krylov_s = (o->newton_predict > 0.0) ? 5 : 4;
   if (o->krylov_s < 1 || o->krylov_s > MB4_MAX_KRYLOV_S) return MB4_ERR_INVALID_ARG;
   if (!(o->newton_rtol > 0.0) || o->newton_max < 1) return MB4_ERR_INVALID_ARG;
+  if (o->overlap_launches != 0 && o->overlap_launches != 1) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -136,6 +139,7 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.S = grid->nx * grid->ny;
   p.B = c->B;
   p.s = o.krylov_s;
+  p.pdl = o.overlap_launches;
   p.tx = grid->tx;
   p.ty = grid->ty;
   p.eps0 = grid->onsite;
@@ -366,6 +370,8 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   for (int b = 0; b < B; ++b) fill_inst_const(c, chi[b], instance_theta(c->p, V + (size_t)b * S, S), &ic[b]);
   c->host_status.assign(B, InstStatus{});
   for (int b = 0; b < B; ++b) c->host_status[b].enabled = 1;
+  c->base_steps.assign(B, 0);
+  c->base_newton.assign(B, 0);
   MB4_TRY(cudaMemcpyAsync(d.V, V, BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(d.d, D.data(), BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(d.ic, ic.data(), B * sizeof(InstConst), cudaMemcpyHostToDevice, c->stream));
@@ -415,7 +421,11 @@ int wait_batch(mb4_batch* c, mb4_stats* stats, int* status) {
   MB4_CHECK(read_status(c));
   int first = MB4_OK;
   for (int b = 0; b < c->B; ++b) {
-    const InstStatus& s = c->host_status[b];
+    InstStatus s = c->host_status[b];
+    s.steps_done -= c->base_steps[b];
+    s.newton_total -= c->base_newton[b];
+    c->base_steps[b] = c->host_status[b].steps_done;
+    c->base_newton[b] = c->host_status[b].newton_total;
     if (stats) fill_stats(s, stats + b);
     if (status) status[b] = s.error;
     if (first == MB4_OK && s.error) first = s.error;
@@ -430,6 +440,8 @@ int clear_errors(mb4_batch* c) {
     s.steps_done = 0;
     s.newton_total = 0;
   }
+  std::fill(c->base_steps.begin(), c->base_steps.end(), 0LL);
+  std::fill(c->base_newton.begin(), c->base_newton.end(), 0LL);
   return write_status(c);
 }
 
@@ -457,6 +469,7 @@ int mb4_default_options(mb4_options* o) {
   o->stream = nullptr;
   o->use_graph = 1;
   o->newton_predict = 0.0;
+  o->overlap_launches = 1;
   return MB4_OK;
 }
 
@@ -568,6 +581,8 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
   InstStatus fresh{};
   fresh.enabled = 1;
   c->host_status[instance] = fresh;
+  c->base_steps[instance] = 0;
+  c->base_newton[instance] = 0;
   return write_status(c);
 }
 
@@ -666,6 +681,20 @@ int mb4_step(mb4_ctx* c, int nsteps, mb4_stats* stats) {
   MB4_CHECK(clear_errors(c));   // every call starts from the last accepted state
   MB4_CHECK(step_async(c, nsteps));
   return wait_batch(c, stats, nullptr);
+}
+
+int mb4_step_async(mb4_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  return step_async(c, nsteps);
+}
+
+int mb4_wait(mb4_ctx* c, mb4_stats* stats) {
+  if (!c) return MB4_ERR_INVALID_ARG;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int rc = wait_batch(c, stats, nullptr);
+  if (rc != MB4_OK && c->host_status[0].error != MB4_OK)
+    MB4_CHECK(clear_errors(c));   // the next steps start from the last accepted state
+  return rc;
 }
 
 int mb4_observables(const mb4_ctx* c, double* out6) { return mb4_batch_observables(c, out6); }

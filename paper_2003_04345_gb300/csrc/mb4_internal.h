@@ -12,9 +12,10 @@ namespace mb4 {
 
 constexpr int kGauss = 6;          // Gauss-Legendre nodes: exact for the degree-11 integrand of eq. (fIu2)
 constexpr int kMaxS = MB4_MAX_KRYLOV_S;
-constexpr int kGramCap = 96;       // Gram blocks per (instance, system), at most
-constexpr int kObsBlocksTotal = 304;   // observables: blocks over the whole batch
-constexpr int kObsBlocksMax = 304;     // ... and per instance, at most
+constexpr int kGramCap = 152;      // Gram blocks per (instance, system), at most
+constexpr int kGramCluster = 8;    // thread-block cluster size of the Gram reduction
+constexpr int kObsBlocksTotal = 152;   // observables: blocks over the whole batch
+constexpr int kObsBlocksMax = 152;     // ... and per instance, at most
 
 // MB4 constants in FP64, computed on the host (mb4_consts.cpp).
 struct Constants {
@@ -38,6 +39,7 @@ struct StepParams {
   int s;                   // Krylov subspace dimension
   int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
+  int pdl;                 // programmatic dependent launch inside the Newton loop
   double tx, ty, eps0, h;
   // residual in the eigenbasis of E on the increments dU = Tinv (U - e3 (x) u0)
   double hlam[3];          // h * lambda_i
@@ -76,9 +78,8 @@ struct InstStatus {
   int cont;
   int last_newton_iters;
   unsigned int u0max_bits;           // ||u0||_inf of the current step (float bits, >= 0)
-  unsigned int ticket_gram;          // last-block tickets (reset by the last block)
+  unsigned int ticket_gram[3];       // last-block tickets, one per shifted system (reset by the last block)
   unsigned int ticket_update;
-  unsigned int pad0;
   unsigned long long rmax_bits;      // max |r| of the current iteration (double bits, >= 0)
   long long steps_done;              // accepted steps since the last reset
   long long newton_total;
@@ -105,7 +106,7 @@ struct DevBuffers {
   double2* Ubar;     // transformed stage increments dU, B*3*S
   void* jc;          // J coefficients {e1, e2, a, 0} (TK4), B*S
   void* v;           // Krylov basis, B*(s+1)*3*S of TK2; level 0 = right-hand side b
-  double* gram_part; // B*3*gram_blocks*nent
+  double* gram_part; // B*3*gram_blocks*nent (per-cluster partials use the first part)
   double* coef;      // B*3*kMaxS least-squares coefficients
   double* obs_part;  // observables partial sums
   double* obs_out;   // B*6

@@ -13,12 +13,15 @@
 // T[2] . T^-1 1 = 1 - O(1e-16) and the energy would drift linearly in time.
 // Each instance keeps its own Newton status; an instance that has converged
 // (or failed) is masked while the others iterate.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
 #include <cstdint>
 
 #include "mb4_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace mb4 {
 
@@ -31,6 +34,33 @@ template <> struct Vec2<double> { typedef double2 type; };
 template <typename T> struct alignas(4 * sizeof(T)) JCoef { T e1, e2, a, pad; };
 
 struct Nbr { int xm, xp, ym, yp; };
+
+// Programmatic dependent launch (griddepcontrol).  A kernel launched with
+// programmatic stream serialisation can be scheduled once every block of its
+// predecessor has called pdl_launch_dependents(); pdl_wait() then blocks until
+// the predecessor grid has completed and its writes are visible.  Every kernel
+// that may be launched this way calls pdl_wait() before it reads anything;
+// without such a launch both calls do nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch kern with programmatic stream serialisation when dep is set (the
+// previous launch on the stream is a kernel whose results it waits for).
+template <typename... KArgs, typename... Args>
+void launch_k(bool dep, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dep ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 __device__ __forceinline__ Nbr neighbours(int k, int nx, int ny, int S) {
   int y = k / nx;
@@ -106,6 +136,10 @@ template <typename T> __device__ __forceinline__ float to_float(T x);
 template <> __device__ __forceinline__ float to_float<float>(float x) { return x; }
 template <> __device__ __forceinline__ float to_float<double>(double x) { return d2f_trunc(x); }
 
+// Threads per block of the one-site-per-thread kernels: small blocks give many
+// blocks per SM and short tails when a launch is only a few waves deep.
+constexpr int kSiteThreads = 128;
+
 // Offsets of instance b's data.
 __device__ __forceinline__ size_t plane(int b, int S) { return (size_t)b * S; }
 __device__ __forceinline__ size_t stage(int b, int m, int S) { return ((size_t)b * 3 + m) * S; }
@@ -123,7 +157,7 @@ __device__ __forceinline__ size_t level(int b, int a, int i, int s, int S) {
 // dU^0 = 0 (the first update writes them).  Grid: (sites / 256, B).
 // ---------------------------------------------------------------------------
 template <typename TK>
-__global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __restrict__ u,
+__global__ void __launch_bounds__(kSiteThreads) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
                                                JCoef<TK>* __restrict__ jc, typename Vec2<TK>::type* __restrict__ v,
                                                const InstConst* __restrict__ ic, InstStatus* is) {
@@ -172,8 +206,8 @@ __global__ void __launch_bounds__(256) k_setup(StepParams p, const double2* __re
 
 template <typename TK>
 void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  dim3 grid((p.S + 255) / 256, p.B);
-  k_setup<TK><<<grid, 256, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v, b.ic,
+  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
+  k_setup<TK><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v, b.ic,
                                    b.is);
 }
 
@@ -187,12 +221,14 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 // T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
 // ---------------------------------------------------------------------------
 template <typename TO>
-__global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* __restrict__ u,
+__global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
                                                   const double2* __restrict__ dUb,
                                                   typename Vec2<TO>::type* __restrict__ out, long long out_stride,
                                                   int skip_first, const InstConst* __restrict__ ic,
                                                   const InstStatus* is) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int b = blockIdx.y;
   if (!is[b].active) return;
   if (skip_first && is[b].newton_iter == 0) return;   // b^0 was written by k_setup
@@ -243,16 +279,16 @@ __global__ void __launch_bounds__(256) k_residual(StepParams p, const double2* _
 
 template <typename TK>
 void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, cudaStream_t s) {
-  dim3 grid((p.S + 255) / 256, p.B);
+  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
   // b_i of instance b goes to its level 0: level(b, 0, i) = b*(s+1)*3*S + i*S
-  k_residual<TK><<<grid, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
+  k_residual<TK><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
                                       (long long)(p.s + 1) * 3 * p.S, skip_first ? 1 : 0, b.ic, b.is);
 }
 
 template <typename TK>
 void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3, cudaStream_t s) {
-  dim3 grid((p.S + 255) / 256, p.B);
-  k_residual<double><<<grid, 256, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.ic, b.is);
+  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
+  k_residual<double><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.ic, b.is);
 }
 
 // ---------------------------------------------------------------------------
@@ -263,9 +299,11 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 // (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
 // ---------------------------------------------------------------------------
 template <typename TK>
-__global__ void __launch_bounds__(256) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
+__global__ void __launch_bounds__(kSiteThreads) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
                                                 const InstConst* __restrict__ ic, const InstStatus* is) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int b = blockIdx.y;
   if (!is[b].active) return;
   typedef typename Vec2<TK>::type TK2;
@@ -313,6 +351,8 @@ template <int SK>
 __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const float4* __restrict__ jc,
                                                         float2* __restrict__ v, const InstConst* __restrict__ ic,
                                                         const InstStatus* is) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int b = blockIdx.y;
   if (!is[b].active) return;
   constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
@@ -375,49 +415,94 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
 }
 
 // Gram accumulators.  FP32 mode: products and per-thread sums in FP32, a
-// pairwise (shuffle-tree) warp sum, then FP64 across warps and blocks.  For
-// the monomial bases met here (s <= 10, ||J/theta|| <= 1) the normal equations
-// are well enough conditioned that this gives the same least-squares residual
-// as exact sums of the FP32 products; the FP32 basis vectors themselves set the
-// accuracy of the inner solve.
+// pairwise (shuffle-tree) warp sum per entry, then FP64 across warps and blocks.
+// For the monomial bases met here (s <= 10, ||J/theta|| <= 1) the normal
+// equations are well enough conditioned that this gives the same least-squares
+// residual as exact sums of the FP32 products; the FP32 basis vectors themselves
+// set the accuracy of the inner solve.  FP64 mode: see warp_sum_f64.
 template <typename TK> struct GramAcc;
 template <> struct GramAcc<float> {
   float v;
   __device__ void zero() { v = 0.f; }
   __device__ void add(float2 a, float2 b) { v = fmaf(a.x, b.x, v); v = fmaf(a.y, b.y, v); }
-  __device__ double warp_sum() {
-    float r = v;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    return f2d_bits(r);
-  }
 };
 template <> struct GramAcc<double> {
   double v;
   __device__ void zero() { v = 0.0; }
   __device__ void add(double2 a, double2 b) { v = fma(a.x, b.x, v); v = fma(a.y, b.y, v); }
-  __device__ double warp_sum() {
-    double r = v;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    return r;
-  }
 };
 
+// Warp sums of NE per-lane FP64 values, written to out[0..NE).  A butterfly per
+// entry would cost 5 NE adds per lane on the FP64 pipe -- the pipe that bounds
+// the Gram kernel.  Recursive halving instead: at offset o = 16, 8, 4, 2 each lane
+// keeps the half of its live values picked by lane bit o and adds the partner's
+// copy of that half; after four steps a lane holds P/16 entries (P = NE padded
+// to a multiple of 16), which the o = 1 partner holds too.  About P adds per lane.
+template <int NE>
+__device__ __forceinline__ void warp_sum_f64(const GramAcc<double> (&acc)[NE], double* out, int lane) {
+  constexpr int P = ((NE + 15) / 16) * 16;
+  double x[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) x[j] = (j < NE) ? acc[j].v : 0.0;
+  int base = 0;
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int o = 16 >> st;
+    const int h = P >> (st + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < (P >> (st + 1)); ++j) {
+      const double send = up ? x[j] : x[j + h];
+      const double keep = up ? x[j + h] : x[j];
+      x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (up) base += h;
+  }
+#pragma unroll
+  for (int j = 0; j < P / 16; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], 1);
+  if ((lane & 1) == 0) {
+#pragma unroll
+    for (int j = 0; j < P / 16; ++j)
+      if (base + j < NE) out[base + j] = x[j];
+  }
+}
+
+template <int NE>
+__device__ __forceinline__ void warp_sums(const GramAcc<float> (&acc)[NE], double* out, int lane) {
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    float r = acc[e].v;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) out[e] = f2d_bits(r);
+  }
+}
+template <int NE>
+__device__ __forceinline__ void warp_sums(const GramAcc<double> (&acc)[NE], double* out, int lane) {
+  warp_sum_f64<NE>(acc, out, lane);
+}
+
 // Gram matrices G_ab = <v_a, v_b> (real inner product of the [p; q] form),
-// a <= b <= s, of system i = blockIdx.y of instance blockIdx.z; block partials go
-// to part[((inst * 3 + i) * gridDim.x + block) * NE + e].  The last block of the
-// instance to finish then
-//  1. reduces the partials in a fixed order (so results do not depend on
-//     which block finishes last),
-//  2. forms, per system, the normal equations of the least-squares problem
-//     min_c || b - (I - h lam J) sum_a c_a v_a ||:
-//       (B^T G B) c = B^T G e_0,  B = [I; 0] - sig [0; I]  (s x s),
-//  3. factors them with one warp per system (right-looking Cholesky; the basis
-//     is truncated at the first pivot below trunc_rel times the leading one, a
-//     numerically exhausted Krylov space; b = 0 gives c = 0) and solves.
-template <typename TK, int SK>
+// a <= b <= s, of system i = blockIdx.y of instance blockIdx.z.  With CL > 1 the
+// blocks form clusters of CL along x: each cluster's rank-0 block adds its
+// members' block sums from their shared memory (distributed shared memory, in
+// rank order) and writes one partial per cluster to
+// part[((inst * 3 + i) * (gridDim.x / CL) + cluster) * NE + e].  The last
+// cluster of system i to finish then
+//  1. reduces that system's partials in a fixed order (so results do not depend
+//     on which block finishes last),
+//  2. forms the normal equations of the least-squares problem
+//     min_c || b - (I - h lam_i J) sum_a c_a v_a ||:
+//       (B^T G B) c = B^T G e_0,  B = [I; 0] - sig_i [0; I]  (s x s),
+//  3. factors them with one warp (right-looking Cholesky; the basis is truncated
+//     at the first pivot below trunc_rel times the leading one, a numerically
+//     exhausted Krylov space; b = 0 gives c = 0) and solves.
+// The three systems finish on three different blocks, in parallel.
+template <typename TK, int SK, int CL>
 __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                   double* __restrict__ part, double* __restrict__ coef,
                                                   const InstConst* __restrict__ ic, InstStatus* is) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int inst = blockIdx.z;
   if (!is[inst].active) return;
   typedef typename Vec2<TK>::type TK2;
@@ -459,113 +544,129 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
       for (int c = a; c < NV; ++c) acc[e++].add(x[a], x[c]);
   }
   __shared__ double red[8][NE];
+  __shared__ double blk[NE];
   __shared__ bool is_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    double w = acc[e].warp_sum();
-    if (lane == 0) red[warp][e] = w;
-  }
+  warp_sums<NE>(acc, red[warp], lane);
   __syncthreads();
-  const int nb = gridDim.x;
-  double* pi = part + (size_t)inst * 3 * nb * NE;
   for (int e = threadIdx.x; e < NE; e += blockDim.x) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][e];
-    pi[((size_t)i * nb + blockIdx.x) * NE + e] = t;
+    blk[e] = t;
   }
+  const int nb = gridDim.x / CL;                 // partials of system i
+  double* pi = part + ((size_t)inst * 3 + i) * nb * NE;
+  bool leader = true;
+  if (CL > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();                              // members' blk[] complete and visible
+    leader = (cluster.block_rank() == 0);
+    if (leader) {
+      for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < CL; ++r) t += cluster.map_shared_rank(blk, r)[e];
+        pi[(size_t)(blockIdx.x / CL) * NE + e] = t;
+      }
+    }
+    cluster.sync();                              // members stay resident until read
+  } else {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NE; e += blockDim.x) pi[(size_t)blockIdx.x * NE + e] = blk[e];
+  }
+  if (!leader) return;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int t = atomicAdd(&is[inst].ticket_gram, 1u);
-    is_last = (t == gridDim.x * gridDim.y - 1);
+    unsigned int t = atomicAdd(&is[inst].ticket_gram[i], 1u);
+    is_last = (t == (unsigned int)(nb - 1));
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  // 1. fixed-order reduction: thread t takes entry t % NT and block slice t / NT.
-  constexpr int NT = 3 * NE;
-  constexpr int SLICES = (256 / NT) > 0 ? (256 / NT) : 1;
-  __shared__ double slice[SLICES][NT];
-  __shared__ double G[3][NE];
-  __shared__ double Nm[3][SK][SK + 1];          // [.., SK] holds the right-hand side
-  for (int t = threadIdx.x; t < SLICES * NT; t += blockDim.x) {
-    const int sl = t / NT, r = t - sl * NT, si = r / NE, e = r - si * NE;
+  // 1. fixed-order reduction: thread t takes entry t % NE and partial slice t / NE.
+  constexpr int SLICES = (256 / NE) > 0 ? (256 / NE) : 1;
+  __shared__ double slice[SLICES][NE];
+  __shared__ double G[NE];
+  __shared__ double Nm[SK][SK + 1];             // [.., SK] holds the right-hand side
+  __shared__ double rinv[SK];
+  for (int t = threadIdx.x; t < SLICES * NE; t += blockDim.x) {
+    const int sl = t / NE, e = t - sl * NE;
     const int b0 = sl * nb / SLICES, b1 = (sl + 1) * nb / SLICES;
-    const double* pp = pi + (size_t)si * nb * NE + e;
-    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const double* pp = pi + e;
+    double q[4] = {0, 0, 0, 0};
     int bb = b0;
-    for (; bb + 8 <= b1; bb += 8) {
-      double w[8];
+    for (; bb + 4 <= b1; bb += 4) {
+      double w[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) w[j] = __ldcg(pp + (size_t)(bb + j) * NE);
+      for (int j = 0; j < 4; ++j) w[j] = __ldcg(pp + (size_t)(bb + j) * NE);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) q[j] += w[j];
+      for (int j = 0; j < 4; ++j) q[j] += w[j];
     }
     for (int j = 0; bb < b1; ++bb, ++j) q[j] += __ldcg(pp + (size_t)bb * NE);
-    slice[sl][r] = ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+    slice[sl][e] = (q[0] + q[1]) + (q[2] + q[3]);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+  for (int e = threadIdx.x; e < NE; e += blockDim.x) {
     double sum = 0.0;
-    for (int sl = 0; sl < SLICES; ++sl) sum += slice[sl][t];
-    G[t / NE][t % NE] = sum;
+    for (int sl = 0; sl < SLICES; ++sl) sum += slice[sl][e];
+    G[e] = sum;
   }
   __syncthreads();
   // 2. normal equations, all entries in parallel
-  auto g = [&](int si, int a, int c) -> double {
+  auto g = [&](int a, int c) -> double {
     if (a > c) { int t = a; a = c; c = t; }
-    return G[si][a * NV - a * (a - 1) / 2 + (c - a)];
+    return G[a * NV - a * (a - 1) / 2 + (c - a)];
   };
-  for (int t = threadIdx.x; t < 3 * SK * (SK + 1); t += blockDim.x) {
-    const int si = t / (SK * (SK + 1)), r = t - si * SK * (SK + 1), a = r / (SK + 1), c = r - a * (SK + 1);
-    const double sg = ic[inst].sig[si];
-    Nm[si][a][c] = (c < SK) ? g(si, a, c) - sg * (g(si, a + 1, c) + g(si, a, c + 1)) + sg * sg * g(si, a + 1, c + 1)
-                            : g(si, a, 0) - sg * g(si, a + 1, 0);
+  const double sg = ic[inst].sig[i];
+  for (int t = threadIdx.x; t < SK * (SK + 1); t += blockDim.x) {
+    const int a = t / (SK + 1), c = t - a * (SK + 1);
+    Nm[a][c] = (c < SK) ? g(a, c) - sg * (g(a + 1, c) + g(a, c + 1)) + sg * sg * g(a + 1, c + 1)
+                        : g(a, 0) - sg * g(a + 1, 0);
   }
   __syncthreads();
-  // 3. one warp per system: Cholesky in place (lower triangle), then the two triangular solves
-  if (warp < 3) {
-    double (*N)[SK + 1] = Nm[warp];
-    int dim = (g(warp, 0, 0) > 0.0) ? SK : 0;
-    const double lead = N[0][0];
+  // 3. one warp: Cholesky in place (lower triangle), then the two triangular solves,
+  // with one reciprocal square root per pivot (kept in rinv) and no divisions.
+  if (warp == 0) {
+    int dim = (G[0] > 0.0) ? SK : 0;
+    const double lead = Nm[0][0];
     for (int a = 0; a < dim; ++a) {
-      const double dg = N[a][a];
+      const double dg = Nm[a][a];
       if (!(dg > (double)p.trunc_rel * lead)) { dim = a; break; }
-      const double la = sqrt(dg);
+      const double il = rsqrt(dg);
       __syncwarp();
-      for (int b2 = a + 1 + lane; b2 < SK; b2 += 32) N[b2][a] /= la;
-      if (lane == 0) N[a][a] = la;
+      for (int b2 = a + 1 + lane; b2 < SK; b2 += 32) Nm[b2][a] *= il;
+      if (lane == 0) { Nm[a][a] = dg * il; rinv[a] = il; }
       __syncwarp();
       const int m = SK - a - 1;
       for (int idx = lane; idx < m * m; idx += 32) {
         const int b2 = a + 1 + idx / m, c = a + 1 + idx % m;
-        if (c <= b2) N[b2][c] -= N[b2][a] * N[c][a];
+        if (c <= b2) Nm[b2][c] -= Nm[b2][a] * Nm[c][a];
       }
       __syncwarp();
     }
     if (lane == 0) {
       double y[SK], cc[SK];
       for (int a = 0; a < dim; ++a) {
-        double t = N[a][SK];
-        for (int b2 = 0; b2 < a; ++b2) t -= N[a][b2] * y[b2];
-        y[a] = t / N[a][a];
+        double t = Nm[a][SK];
+        for (int b2 = 0; b2 < a; ++b2) t -= Nm[a][b2] * y[b2];
+        y[a] = t * rinv[a];
       }
       for (int a = dim - 1; a >= 0; --a) {
         double t = y[a];
-        for (int b2 = a + 1; b2 < dim; ++b2) t -= N[b2][a] * cc[b2];
-        cc[a] = t / N[a][a];
+        for (int b2 = a + 1; b2 < dim; ++b2) t -= Nm[b2][a] * cc[b2];
+        cc[a] = t * rinv[a];
       }
-      for (int a = 0; a < SK; ++a) coef[((size_t)inst * 3 + warp) * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
+      for (int a = 0; a < SK; ++a) coef[((size_t)inst * 3 + i) * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
+      is[inst].ticket_gram[i] = 0u;
     }
   }
-  if (threadIdx.x == 0) is[inst].ticket_gram = 0u;
 }
 
 template <int SK>
 void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   dim3 grid(((p.nx + kPowTX - 1) / kPowTX) * ((p.ny + kPowTY - 1) / kPowTY), p.B);
-  k_powers<SK><<<grid, kPowThreads, pow_smem_bytes<SK>(), s>>>(p, (const float4*)b.jc, (float2*)b.v, b.ic, b.is);
+  launch_k(p.pdl != 0, k_powers<SK>, grid, dim3(kPowThreads), pow_smem_bytes<SK>(), s, p, (const float4*)b.jc,
+           (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is);
 }
 
 // Opt the matrix-powers kernels into more than 48 KB of dynamic shared memory.
@@ -603,16 +704,44 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 #undef MB4_CALL
     return;
   }
-  dim3 grid((p.S + 255) / 256, p.B);
+  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
   for (int a = 0; a < p.s; ++a)
-    k_matvec<TK><<<grid, 256, 0, s>>>(p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a, b.ic, b.is);
+    launch_k(p.pdl != 0, k_matvec<TK>, grid, dim3(kSiteThreads), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a,
+             (const InstConst*)b.ic, (const InstStatus*)b.is);
+}
+
+template <typename TK, int SK>
+void launch_gram_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
+  typedef typename Vec2<TK>::type TK2;
+  const TK2* v = (const TK2*)b.v;
+  // Clusters pay off for the FP32 basis, whose Gram kernel is short and tail-bound;
+  // the FP64 kernel is FP64-issue-bound, and whole 8-block clusters spread less
+  // evenly over the SMs than single blocks.
+  if (sizeof(TK) == sizeof(float) && p.gram_blocks % kGramCluster == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.gram_blocks, 3, p.B);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kGramCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = p.pdl ? 2 : 1;
+    cudaLaunchKernelEx(&cfg, k_gram_lsq<TK, SK, kGramCluster>, p, v, b.gram_part, b.coef,
+                       (const InstConst*)b.ic, b.is);
+  } else {
+    launch_k(p.pdl != 0, k_gram_lsq<TK, SK, 1>, dim3(p.gram_blocks, 3, p.B), dim3(256), 0, s, p, v, b.gram_part,
+             b.coef, (const InstConst*)b.ic, b.is);
+  }
 }
 
 template <typename TK>
 void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-#define MB4_CALL(N)                                                                                      \
-  k_gram_lsq<TK, N><<<dim3(p.gram_blocks, 3, p.B), 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, \
-                                                               b.gram_part, b.coef, b.ic, b.is)
+#define MB4_CALL(N) launch_gram_s<TK, N>(p, b, s)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
 }
@@ -625,14 +754,18 @@ int gram_blocks_per_system(int s_dim, int B) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaSuccess;
   switch (s_dim) {
-#define MB4_OCC(N) case N: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_lsq<TK, N>, 256, 0); break;
+#define MB4_OCC(N) case N: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_lsq<TK, N, 1>, 256, 0); break;
     MB4_OCC(1) MB4_OCC(2) MB4_OCC(3) MB4_OCC(4) MB4_OCC(5) MB4_OCC(6) MB4_OCC(7) MB4_OCC(8) MB4_OCC(9)
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_lsq<TK, 10>, 256, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_lsq<TK, 10, 1>, 256, 0); break;
 #undef MB4_OCC
   }
   if (e != cudaSuccess || occ < 1 || sms < 1) return 0;
+  // The FP64 kernel is bound by the FP64 pipe: two blocks per SM already overlap
+  // the loads with the arithmetic, and fewer blocks mean fewer partial sums.
+  if (sizeof(TK) == sizeof(double) && occ > 2) occ = 2;
   long long nb = (long long)sms * occ / (3LL * (B > 0 ? B : 1));
   if (nb > kGramCap) nb = kGramCap;   // more blocks only lengthen the last block's reduction
+  if (sizeof(TK) == sizeof(float) && nb >= kGramCluster) nb -= nb % kGramCluster;   // whole clusters
   return nb < 1 ? 1 : (int)nb;
 }
 template int gram_blocks_per_system<float>(int, int);
@@ -667,10 +800,12 @@ __device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaG
 // (and, when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
 // for at most newton_max iterations.  Grid: (sites / 256, B).
 template <typename TK, int SK>
-__global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
+__global__ void __launch_bounds__(kSiteThreads) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                 const double* __restrict__ coef, const double2* __restrict__ u,
                                                 double2* __restrict__ Ubar, InstStatus* is, BatchCtl* bc,
                                                 cudaGraphConditionalHandle h, int use_cond) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int inst = blockIdx.y;
   InstStatus& I = is[inst];
   if (!I.active) {
@@ -781,10 +916,10 @@ __global__ void __launch_bounds__(256) k_update(StepParams p, const typename Vec
 
 template <typename TK>
 void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long h, int use_cond, cudaStream_t s) {
-  dim3 grid((p.S + 255) / 256, p.B);
+  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
 #define MB4_CALL(N)                                                                                      \
-  k_update<TK, N><<<grid, 256, 0, s>>>(p, (const typename Vec2<TK>::type*)b.v, b.coef, b.u, b.Ubar, b.is, \
-                                       b.bc, (cudaGraphConditionalHandle)h, use_cond)
+  launch_k(p.pdl != 0, k_update<TK, N>, grid, dim3(kSiteThreads), 0, s, p, (const typename Vec2<TK>::type*)b.v, \
+           (const double*)b.coef, (const double2*)b.u, b.Ubar, b.is, b.bc, (cudaGraphConditionalHandle)h, use_cond)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
 }
@@ -792,7 +927,7 @@ void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long 
 // Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = u0 + sum_n T[2][n] dU_n, for the
 // instances that took part in the step and did not fail.  Block 0 of each instance
 // books the step and re-arms the instance for the next one.
-__global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restrict__ u,
+__global__ void __launch_bounds__(kSiteThreads) k_accept(StepParams p, double2* __restrict__ u,
                                                 const double2* __restrict__ Ubar, InstStatus* is) {
   const int inst = blockIdx.y;
   InstStatus& I = is[inst];
@@ -824,8 +959,8 @@ __global__ void __launch_bounds__(256) k_accept(StepParams p, double2* __restric
 }
 
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  dim3 grid((p.S + 255) / 256, p.B);
-  k_accept<<<grid, 256, 0, s>>>(p, b.u, b.Ubar, b.is);
+  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
+  k_accept<<<grid, kSiteThreads, 0, s>>>(p, b.u, b.Ubar, b.is);
 }
 
 // Arms every enabled instance without an error for the next step (start of a call).
@@ -843,10 +978,8 @@ __global__ void k_arm(int B, InstStatus* is, BatchCtl* bc) {
   I.rmax_bits = 0ull;
   I.u0max_bits = 0u;
   I.prev_rmax = 0.0;
-  I.ticket_gram = 0u;
+  I.ticket_gram[0] = I.ticket_gram[1] = I.ticket_gram[2] = 0u;
   I.ticket_update = 0u;
-  I.steps_done = 0;
-  I.newton_total = 0;
   const int go = I.enabled && !I.error;
   I.in_step = go;
   I.active = go;
@@ -877,73 +1010,109 @@ __device__ __forceinline__ DD dd_add(DD a, DD b) {
 }
 
 constexpr int kObs = 6;            // H, U_K, U_E, U_nl, sum|u|^2, sum|u|^4
+constexpr int kParts = 5;          // summed per site: U_K, U_E, U_nl, sum|u|^2, sum|u|^4 (H = the first three)
+
+// Warp sums of kParts double-double values (fixed order).  Recursive halving as in
+// warp_sum_f64: at o = 16, 8, 4 a lane keeps half of its live values (padded to 8)
+// and adds the partner's copy; o = 2, 1 then add the one value left.  9 dd_adds
+// per lane instead of 25 for a butterfly per value.  Entry e ends in the lanes
+// whose bits 4, 3, 2 spell e.
+__device__ __forceinline__ void warp_sum_dd(DD (&x)[8], int lane) {
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const int o = 16 >> st;
+    const int h = 4 >> st;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < (4 >> st); ++j) {
+      DD send = up ? x[j] : x[j + h];
+      DD keep = up ? x[j + h] : x[j];
+      DD t;
+      t.s = __shfl_xor_sync(0xffffffffu, send.s, o);
+      t.c = __shfl_xor_sync(0xffffffffu, send.c, o);
+      x[j] = up ? dd_add(t, keep) : dd_add(keep, t);   // lower lane's half first, in both lanes
+    }
+  }
+#pragma unroll
+  for (int o = 2; o > 0; o >>= 1) {
+    DD t;
+    t.s = __shfl_xor_sync(0xffffffffu, x[0].s, o);
+    t.c = __shfl_xor_sync(0xffffffffu, x[0].c, o);
+    x[0] = (lane & o) ? dd_add(t, x[0]) : dd_add(x[0], t);
+  }
+}
 
 __global__ void __launch_bounds__(256) k_observables(StepParams p, const double2* __restrict__ u,
                                                      const double* __restrict__ Vp,
                                                      const InstConst* __restrict__ ic, double* __restrict__ part) {
   const int inst = blockIdx.y;
   const int S = p.S;
-  const double chi = ic[inst].chi;
+  const double half_chi = 0.5 * ic[inst].chi;
   const double2* ub = u + plane(inst, S);
   const double* vb = Vp + plane(inst, S);
-  DD acc[kObs];
+  DD acc[8];
 #pragma unroll
-  for (int o = 0; o < kObs; ++o) acc[o].s = acc[o].c = 0.0;
+  for (int o = 0; o < 8; ++o) acc[o].s = acc[o].c = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
     Nbr n = neighbours(k, p.nx, p.ny, S);
     double2 c = ub[k], a = ub[n.xm], b = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
     double Kx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + b.x, p.eps0 * c.x));
     double Ky = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + b.y, p.eps0 * c.y));
-    double tK = fma(c.x, Kx, c.y * Ky);
     double nn = fma(c.x, c.x, c.y * c.y);
-    double tE = vb[k] * nn;
-    double tI = 0.5 * chi * nn * nn;
-    two_sum_add(acc[0], tK);
-    two_sum_add(acc[0], tE);
-    two_sum_add(acc[0], tI);
-    two_sum_add(acc[1], tK);
-    two_sum_add(acc[2], tE);
-    two_sum_add(acc[3], tI);
-    two_sum_add(acc[4], nn);
-    two_sum_add(acc[5], nn * nn);
+    double n4 = nn * nn;
+    two_sum_add(acc[0], fma(c.x, Kx, c.y * Ky));
+    two_sum_add(acc[1], vb[k] * nn);
+    two_sum_add(acc[2], half_chi * n4);
+    two_sum_add(acc[3], nn);
+    two_sum_add(acc[4], n4);
   }
-  __shared__ DD red[8][kObs];
+  __shared__ DD red[8][kParts];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 0; o < kObs; ++o) {
-    DD r = acc[o];
-    for (int off = 16; off > 0; off >>= 1) {
-      DD t;
-      t.s = __shfl_xor_sync(0xffffffffu, r.s, off);
-      t.c = __shfl_xor_sync(0xffffffffu, r.c, off);
-      r = dd_add(r, t);
-    }
-    if (lane == 0) red[warp][o] = r;
+  warp_sum_dd(acc, lane);
+  if ((lane & 3) == 0) {
+    const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if (e < kParts) red[warp][e] = acc[0];
   }
   __syncthreads();
-  if (threadIdx.x < kObs) {
+  if (threadIdx.x < kParts) {
     DD r = red[0][threadIdx.x];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = dd_add(r, red[w][threadIdx.x]);
-    double* pb = part + ((size_t)inst * gridDim.x + blockIdx.x) * kObs * 2;
+    double* pb = part + ((size_t)inst * gridDim.x + blockIdx.x) * kParts * 2;
     pb[threadIdx.x * 2 + 0] = r.s;
     pb[threadIdx.x * 2 + 1] = r.c;
   }
 }
 
+// One block of kParts warps per instance: warp o sums part o over the block
+// partials (lane l takes blocks l, l + 32, ...; then a butterfly in a fixed
+// order); H = U_K + U_E + U_nl in double-double.
 __global__ void k_observables_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
   const int inst = blockIdx.x;
-  const int o = threadIdx.x;
-  if (o >= kObs) return;
+  const int o = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ DD tot[kParts];
+  const double* pb = part + (size_t)inst * nblocks * kParts * 2;
   DD r;
   r.s = r.c = 0.0;
-  const double* pb = part + (size_t)inst * nblocks * kObs * 2;
-  for (int b = 0; b < nblocks; ++b) {
+  for (int b = lane; b < nblocks; b += 32) {
     DD t;
-    t.s = pb[((size_t)b * kObs + o) * 2 + 0];
-    t.c = pb[((size_t)b * kObs + o) * 2 + 1];
+    t.s = pb[((size_t)b * kParts + o) * 2 + 0];
+    t.c = pb[((size_t)b * kParts + o) * 2 + 1];
     r = dd_add(r, t);
   }
-  out[(size_t)inst * kObs + o] = r.s + r.c;
+  for (int off = 1; off < 32; off <<= 1) {
+    DD t;
+    t.s = __shfl_xor_sync(0xffffffffu, r.s, off);
+    t.c = __shfl_xor_sync(0xffffffffu, r.c, off);
+    r = (lane & off) ? dd_add(t, r) : dd_add(r, t);
+  }
+  if (lane == 0) tot[o] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const DD H = dd_add(dd_add(tot[0], tot[1]), tot[2]);
+    double* ob = out + (size_t)inst * kObs;
+    ob[0] = H.s + H.c;
+    for (int q = 0; q < kParts; ++q) ob[1 + q] = tot[q].s + tot[q].c;
+  }
 }
 
 int obs_blocks_per_instance(int B) {
@@ -955,7 +1124,7 @@ int obs_blocks_per_instance(int B) {
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   const int nb = obs_blocks_per_instance(p.B);
   k_observables<<<dim3(nb, p.B), 256, 0, s>>>(p, b.u, b.V, b.ic, b.obs_part);
-  k_observables_final<<<p.B, 32, 0, s>>>(b.obs_part, nb, b.obs_out);
+  k_observables_final<<<p.B, 32 * kParts, 0, s>>>(b.obs_part, nb, b.obs_out);
 }
 
 // ---------------------------------------------------------------------------

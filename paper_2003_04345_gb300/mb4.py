@@ -35,8 +35,8 @@ KERNEL_CLASSES = ("setup", "residual", "matvec", "gram", "update", "accept")
 
 # Every entry point include/mb4.h declares.
 EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", "mb4_get_state",
-           "mb4_get_stages", "mb4_step", "mb4_step_profiled", "mb4_energy", "mb4_norm", "mb4_observables", "mb4_residual",
-           "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
+           "mb4_get_stages", "mb4_step", "mb4_step_async", "mb4_wait", "mb4_step_profiled", "mb4_energy",
+           "mb4_norm", "mb4_observables", "mb4_residual", "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
            "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
            "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
            "mb4_batch_clear_errors", "mb4_batch_bytes", "mb4_server_create", "mb4_server_destroy",
@@ -59,7 +59,8 @@ class Nonlinearity(C.Structure):
 class Options(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("krylov_s", C.c_int),
                 ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
-                ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double)]
+                ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
+                ("overlap_launches", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -114,6 +115,8 @@ def lib():
         L.mb4_get_state.argtypes = [_P, _P, _P, C.c_int]
         L.mb4_get_stages.argtypes = [_P, _P, _P, C.c_int]
         L.mb4_step.argtypes = [_P, C.c_int, C.POINTER(Stats)]
+        L.mb4_step_async.argtypes = [_P, C.c_int]
+        L.mb4_wait.argtypes = [_P, C.POINTER(Stats)]
         L.mb4_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), _D, C.POINTER(C.c_longlong)]
         L.mb4_energy.argtypes = [_P, _D, _D]
         L.mb4_norm.argtypes = [_P, _D]
@@ -217,9 +220,9 @@ class _Planar:
 class Integrator:
     """One MB4 context (mb4_create ... mb4_destroy)."""
 
-    def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", krylov_s=0,
-                 newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0, c2=2.0 / 3.0,
-                 stream=None, use_graph=True, newton_predict=0.0):
+    def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
+        """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
+        stream, use_graph, newton_predict, overlap_launches)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -238,19 +241,7 @@ class Integrator:
                 raise ValueError("V must hold nx*ny values")
             pot = Potential(Vh.ctypes.data, 0)
             keep = Vh
-        opt = Options()
-        L.mb4_default_options(C.byref(opt))
-        opt.newton_rtol = float(newton_rtol)
-        opt.newton_max = int(newton_max)
-        opt.krylov_s = int(krylov_s)
-        opt.precision = {"fp64": MB4_FP64, "mixed": MB4_MIXED}[precision] if isinstance(precision, str) \
-            else int(precision)
-        opt.alpha1 = float(alpha1)
-        opt.c1, opt.c2 = float(c1), float(c2)
-        opt.use_graph = 1 if use_graph else 0
-        opt.newton_predict = float(newton_predict)
-        if stream is not None:
-            opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        opt = _options(precision=precision, **opts)
         self.precision = precision
         _check(L.mb4_create(C.byref(grid), C.byref(pot), C.byref(Nonlinearity(float(chi))), self.h,
                             C.byref(opt), C.byref(self._ctx)), "mb4_create")
@@ -301,6 +292,19 @@ class Integrator:
         if check:
             _check(rc, "mb4_step")
         return (st.as_dict(), rc) if not check else st.as_dict()
+
+    def step_async(self, nsteps=1):
+        """Queue nsteps steps on the stream without waiting (see wait)."""
+        _check(lib().mb4_step_async(self._ctx, int(nsteps)), "mb4_step_async")
+
+    def wait(self, check=True):
+        """Wait for queued steps; stats cover every step since the last wait/step."""
+        st = Stats()
+        rc = lib().mb4_wait(self._ctx, C.byref(st))
+        if check:
+            _check(rc, "mb4_wait")
+            return st.as_dict()
+        return st.as_dict(), rc
 
     def step_profiled(self, nsteps=1):
         """Host-driven steps with CUDA events around every kernel: returns
@@ -367,7 +371,7 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 
 
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
-             c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0):
+             c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -379,6 +383,7 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
     opt.c1, opt.c2 = float(c1), float(c2)
     opt.use_graph = 1 if use_graph else 0
     opt.newton_predict = float(newton_predict)
+    opt.overlap_launches = 1 if overlap_launches else 0
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
@@ -457,7 +462,9 @@ class Batch:
         """(per-instance stats list, per-instance status codes)."""
         st = (Stats * self.B)()
         codes = (C.c_int * self.B)()
-        lib().mb4_batch_wait(self._ctx, st, codes)
+        rc = lib().mb4_batch_wait(self._ctx, st, codes)
+        if rc not in (MB4_OK, MB4_ERR_NEWTON_NOT_CONVERGED, MB4_ERR_KRYLOV_BREAKDOWN, MB4_ERR_NONFINITE):
+            _check(rc, "mb4_batch_wait")     # not a per-instance code: the call itself failed
         return [s.as_dict() for s in st], list(codes)
 
     def step(self, nsteps=1):

@@ -188,6 +188,21 @@ def test_graph_and_host_loop_agree_bitwise(mb4):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_overlapped_launches_change_nothing(mb4, precision, use_graph):
+    """Programmatic dependent launch only moves when blocks are scheduled: the
+    results are bit for bit those of plain launches."""
+    w = inputs.grid16_fp64()
+    out = []
+    for ov in (True, False):
+        with mb4.from_workload(w, precision=precision, use_graph=use_graph, overlap_launches=ov) as it:
+            st = it.step(12)
+            out.append((it.get_state(), st["newton_iters_total"]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_deterministic_and_resumable(mb4, precision):
     w = inputs.grid16_fp64()
     with mb4.from_workload(w, precision=precision) as a:
@@ -204,6 +219,34 @@ def test_deterministic_and_resumable(mb4, precision):
         d.set_state(mid)
         d.step(10)
         assert np.array_equal(d.get_state(), ua)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_async_steps_equal_synchronous_steps(mb4, precision):
+    """mb4_step_async queues steps back to back; mb4_wait reports all of them."""
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w, precision=precision) as a:
+        st_a = a.step(7)
+        ua = a.get_state()
+    with mb4.from_workload(w, precision=precision) as b:
+        for n in (2, 3, 2):
+            b.step_async(n)
+        st_b = b.wait()
+        assert np.array_equal(b.get_state(), ua)
+        assert st_b["steps_done"] == 7 and st_b["newton_iters_total"] == st_a["newton_iters_total"]
+        b.step_async(1)
+        assert b.wait()["steps_done"] == 1          # counts restart at every wait
+
+
+def test_async_failure_is_reported_by_wait(mb4):
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w, newton_max=1) as it:
+        u0 = it.get_state()
+        it.step_async(2)
+        it.step_async(2)
+        st, rc = it.wait(check=False)
+        assert rc == mb4.MB4_ERR_NEWTON_NOT_CONVERGED and st["steps_done"] == 0
+        assert np.array_equal(it.get_state(), u0)
 
 
 def test_time_reversal_on_gpu(mb4):

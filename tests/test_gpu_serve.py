@@ -49,8 +49,10 @@ def _solo(mb4, q, **opts):
 
 
 def test_served_results_equal_solo_runs(mb4):
-    reqs = _trace(14)
-    with mb4.Server(2 << 30, max_slots=4, keep_states=True, precision="mixed") as srv:
+    """A burst of 14 requests over 6 shape classes with 2 slots per batch: the
+    classes run concurrently and every result equals its solo run."""
+    reqs = _trace(14, span=0.0)
+    with mb4.Server(2 << 30, max_slots=2, keep_states=True, precision="mixed") as srv:
         ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], q["arrival"])
                for q in reqs]
         done = srv.run()
@@ -63,11 +65,34 @@ def test_served_results_equal_solo_runs(mb4):
         assert res["admitted"] >= res["arrival"] - 1e-9 and res["completed"] >= res["admitted"]
         assert abs(res["energy_end"] - res["energy_start"]) <= 1e-13 * abs(res["energy_start"])
         assert _rel(u, _solo(mb4, q, precision="mixed")) <= 1e-12
-        spans.append((res["admitted"], res["completed"]))
-    # continuous batching: some requests were on the GPU at the same time
+        spans.append((res["admitted"], res["completed"], (q["nx"], q["ny"], q["h"])))
+    # different requests were on the GPU at the same time
     overlaps = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
                    if spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1])
     assert overlaps > 0
+
+
+def test_waiting_requests_take_freed_slots(mb4):
+    """One shape class, five requests, a budget that holds a single two-slot batch:
+    two requests run together, and the others are admitted into the slots the
+    finished ones free (continuous batching within the memory budget)."""
+    reqs = _trace(5, seed=2, span=0.0)
+    for r, q in enumerate(reqs):
+        q.update(nx=32, ny=20, h=0.01, nsteps=10 + 7 * r)
+        q["V"] = inputs.potential(32, 20, 1.0, 2, 20.0, 50 + r)
+        q["psi"] = inputs.wavepacket(32, 20, 2.5, math.pi / 4, 0.1 * r)
+    two = mb4.batch_bytes(32, 20, 2, precision="mixed")
+    with mb4.Server(two + two // 4, max_slots=2, keep_states=True, precision="mixed") as srv:
+        ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], 0.0) for q in reqs]
+        assert srv.run() == len(reqs)
+        results = [srv.result(i, state=True) for i in ids]
+    spans = []
+    for q, (res, u) in zip(reqs, results):
+        assert res["status"] == 0 and res["steps_done"] == q["nsteps"]
+        assert _rel(u, _solo(mb4, q, precision="mixed")) <= 1e-12
+        spans.append((res["admitted"], res["completed"]))
+    assert any(a[0] < b[1] and b[0] < a[1] for a in spans for b in spans if a is not b)   # ran together
+    assert sum(1 for b in spans if any(b[0] >= a[1] for a in spans if a is not b)) >= 3  # waited for a slot
 
 
 def test_budget_limits_concurrency(mb4):
