@@ -55,13 +55,13 @@ def kernel_model(kclass, precision, s):
     ne = (s + 1) * (s + 2) // 2
     f64 = precision == "fp64"
     if kclass == "residual":
-        return {"flops": 264, "fp64_ops": 144, "bytes": 16 + 16 + 8 + 48 + 6 * tk, "fp64": True}
+        return {"flops": 240, "fp64_ops": 138, "bytes": 16 + 16 + 8 + 48 + 6 * tk, "fp64": True}
     if kclass == "matvec":
         return {"flops": 54, "fp64_ops": 36 if f64 else 0, "bytes": 6 * tk + 4 * tk + 6 * tk, "fp64": f64}
     if kclass == "gram":   # Gram partial sums (+ the last block's reduction and least squares)
         return {"flops": 3 * ne * 4, "fp64_ops": 3 * ne * 2 if f64 else 0, "bytes": (s + 1) * 6 * tk, "fp64": f64}
     if kclass == "update":
-        return {"flops": 3 * s * 4 + 6 + 36, "fp64_ops": 6 * (s + 1) if f64 else 6,
+        return {"flops": 3 * s * 4 + 6, "fp64_ops": 6 * (s + 1) if f64 else 6,
                 "bytes": s * 6 * tk + 48 + 48, "fp64": f64}
     if kclass == "setup":
         return {"flops": 40, "fp64_ops": 0, "bytes": 16 + 8 + 16 + 48 + 4 * tk + 6 * tk, "fp64": True}
@@ -214,8 +214,11 @@ def run_ours(args):
     flush = lambda: flush_buf.zero_()
 
     results = {}
-    for precision in ("fp64", "mixed"):
-        it = mb4.from_workload(w, precision=precision, stream=stream)
+    for precision in ("fp64", "mixed", "fp64_alg1"):
+        # fp64_alg1: the FP64 path with Algorithm 1's Newton start U^0 = e3 (x) u0 instead
+        # of the default extrapolated start (same equations, same tolerance)
+        start = 0 if precision == "fp64_alg1" else None
+        it = mb4.from_workload(w, precision=precision.split("_")[0], stream=stream, newton_start=start)
         o0 = it.observables()
         it.step(W)
         torch.cuda.synchronize()
@@ -229,7 +232,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier(world)
         wall = time.perf_counter() - t0
-        if precision == "mixed":
+        if precision == "fp64_alg1":
             clocks = sampler.stop()
         o1 = it.observables()
         drift = max([abs(h - o0["H"]) / abs(o0["H"]) for h in Hs + [o1["H"]]])
@@ -241,9 +244,12 @@ def run_ours(args):
             "norm_drift": abs(o1["norm2"] - o0["norm2"]), "krylov_s": s_dim,
             # per step: arm, setup, accept; per Newton iteration: residual, s basis
             # launches (one matrix-powers launch in mixed mode), Gram, update; 2 per log
-            "launches": K * 3 + newton * ((s_dim if precision == "fp64" else 1) + 3) + 2 * obs_calls,
+            "launches": K * 3 + newton * ((s_dim if precision.startswith("fp64") else 1) + 3) + 2 * obs_calls,
             "obs_calls": obs_calls,
         }
+        if precision == "fp64_alg1":
+            it.close()
+            continue
         # per-kernel device times from the event-instrumented run of the same steps
         kp = min(K, 100)
         _, prof = it.step_profiled(kp)
@@ -311,10 +317,15 @@ def run_ours(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "grid512_fp64", "nx": w.nx, "ny": w.ny, "h": w.h, "chi": w.chi, "W": w.W,
                    "defect_fraction": w.defect_fraction, "V_defect": w.V_defect, "sigma": w.sigma,
-                   "precision": "fp64", "krylov_s": fp["krylov_s"], "log_every": LOG_EVERY,
+                   "precision": "fp64", "krylov_s": fp["krylov_s"], "newton_start": 2, "log_every": LOG_EVERY,
                    "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "energy_drift": fp["energy_drift"], "newton_per_step": fp["newton_per_step"],
+        "algorithm1_start": {"value": results["fp64_alg1"]["value"],
+                             "ms_per_step": results["fp64_alg1"]["ms_per_step"],
+                             "newton_per_step": results["fp64_alg1"]["newton_per_step"],
+                             "energy_drift": results["fp64_alg1"]["energy_drift"],
+                             "note": "FP64 path with U^0 = e3 (x) u0 (newton_start = 0)"},
         "mixed": {"value": results["mixed"]["value"], "ms_per_step": results["mixed"]["ms_per_step"],
                   "energy_drift": results["mixed"]["energy_drift"],
                   "newton_per_step": results["mixed"]["newton_per_step"],

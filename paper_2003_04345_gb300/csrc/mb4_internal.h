@@ -40,6 +40,10 @@ struct StepParams {
   int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   int pdl;                 // programmatic dependent launch inside the Newton loop
+  int pred_order;          // Newton start: 0 = e3 (x) u0; m = extrapolate the last m increments
+  int pred_adaptive;       // choose per instance between the two starts by measured cost
+  int pred_cost_milli;     // the extrapolated start's extra residual, in 1/1000 Newton iterations
+  int explore_every;       // steps between tries of the start not currently preferred
   double tx, ty, eps0, h;
   // residual in the eigenbasis of E on the increments dU = Tinv (U - e3 (x) u0)
   double hlam[3];          // h * lambda_i
@@ -80,6 +84,12 @@ struct InstStatus {
   unsigned int u0max_bits;           // ||u0||_inf of the current step (float bits, >= 0)
   unsigned int ticket_gram[3];       // last-block tickets, one per shifted system (reset by the last block)
   unsigned int ticket_update;
+  int pred_count;                    // converged increments kept for the Newton start (<= pred_order)
+  int predicted;                     // the current step started from an extrapolation
+  int next_predicted;                // start chosen for the next step (adaptive mode)
+  int start_known;                   // bit m: start_iters[m] holds a measurement
+  int start_iters[2];                // Newton iterations of the last step with start m (0: e3 (x) u0)
+  int explore_in;                    // steps until the other start is tried again
   unsigned long long rmax_bits;      // max |r| of the current iteration (double bits, >= 0)
   long long steps_done;              // accepted steps since the last reset
   long long newton_total;
@@ -104,12 +114,14 @@ struct DevBuffers {
   double* d;         // onsite + V, B*S
   double2* S0;       // (K+V) u0, B*S
   double2* Ubar;     // transformed stage increments dU, B*3*S
+  double2* dU_hist;  // converged dU of the last pred_order steps, newest first: B*pred_order*3*S (or null)
   void* jc;          // J coefficients {e1, e2, a, 0} (TK4), B*S
   void* v;           // Krylov basis, B*(s+1)*3*S of TK2; level 0 = right-hand side b
   double* gram_part; // B*3*gram_blocks*nent (per-cluster partials use the first part)
   double* coef;      // B*3*kMaxS least-squares coefficients
   double* obs_part;  // observables partial sums
   double* obs_out;   // B*6
+  int* changed;      // B flags: set_state changed the instance's state
   InstConst* ic;     // B
   InstStatus* is;    // B
   BatchCtl* bc;
@@ -132,6 +144,10 @@ template <typename TK> void launch_update(const StepParams& p, const DevBuffers&
                                           int use_cond, cudaStream_t st);
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// Write n = ninst * S sites of state from re/im into u starting at instance first; an
+// instance whose state changes (any bit) forgets its Newton-start history.
+void launch_set_state(const StepParams& p, const DevBuffers& b, const double* re, const double* im, int first,
+                      int ninst, cudaStream_t st);
 int obs_blocks_per_instance(int B);
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 // Y_j += sign * x on three complex planes of S sites.

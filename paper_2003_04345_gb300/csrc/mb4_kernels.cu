@@ -154,12 +154,17 @@ __device__ __forceinline__ size_t level(int b, int a, int i, int s, int S) {
 // right-hand side is b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].
 // J and b^0 only feed the Krylov solve, so they are formed in its precision TK;
 // (K+V) u0 is reused by every residual and stays FP64.  The increments start at
-// dU^0 = 0 (the first update writes them).  Grid: (sites / 256, B).
+// dU^0 = 0 (the first update writes them), or, for an instance whose step starts
+// from an extrapolation (option newton_start), at the polynomial extrapolation of
+// the last m converged increments (m = 1: the last; 2: 2 H0 - H1; 3: 3 H0 - 3 H1 + H2,
+// H0 the newest), whose residual the first k_residual then evaluates.
+// Grid: (sites / 128, B).
 // ---------------------------------------------------------------------------
 template <typename TK>
 __global__ void __launch_bounds__(kSiteThreads) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
                                                JCoef<TK>* __restrict__ jc, typename Vec2<TK>::type* __restrict__ v,
+                                               const double2* __restrict__ dUh, double2* __restrict__ dUb,
                                                const InstConst* __restrict__ ic, InstStatus* is) {
   const int b = blockIdx.y;
   if (!is[b].active) return;
@@ -188,15 +193,34 @@ __global__ void __launch_bounds__(kSiteThreads) k_setup(StepParams p, const doub
     j.a = (TK)2 * ct * pk * qk;
     j.pad = (TK)0;
     jc[plane(b, S) + k] = j;
-    const TK cn = kval<TK>(C.chi, C.f_chi) * nn;
-    const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
+    if (is[b].predicted) {
+      const int mo = min(is[b].pred_count, p.pred_order);
+      const double w0 = (mo == 1) ? 1.0 : (mo == 2) ? 2.0 : 3.0;
+      const double w1 = (mo == 2) ? -1.0 : -3.0;
+      const double2* H = dUh + (size_t)b * p.pred_order * 3 * S;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      TK2 bi;
-      const TK hc = kval<TK>(p.hTc[i], p.f_hTc[i]);
-      bi.x = hc * Fy;
-      bi.y = -hc * Fx;
-      v[level(b, 0, i, p.s, S) + k] = bi;
+      for (int i = 0; i < 3; ++i) {
+        double2 x = H[(size_t)i * S + k];
+        if (mo >= 2) {
+          const double2 y = H[(size_t)(3 + i) * S + k];
+          double2 z = make_double2(0.0, 0.0);
+          if (mo >= 3) z = H[(size_t)(6 + i) * S + k];
+          x.x = fma(w0, x.x, fma(w1, y.x, z.x));
+          x.y = fma(w0, x.y, fma(w1, y.y, z.y));
+        }
+        dUb[stage(b, i, S) + k] = x;
+      }
+    } else {
+      const TK cn = kval<TK>(C.chi, C.f_chi) * nn;
+      const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        TK2 bi;
+        const TK hc = kval<TK>(p.hTc[i], p.f_hTc[i]);
+        bi.x = hc * Fy;
+        bi.y = -hc * Fx;
+        v[level(b, 0, i, p.s, S) + k] = bi;
+      }
     }
     m = fmaxf(absf_of(c.x), absf_of(c.y));
   }
@@ -207,8 +231,8 @@ __global__ void __launch_bounds__(kSiteThreads) k_setup(StepParams p, const doub
 template <typename TK>
 void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
-  k_setup<TK><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v, b.ic,
-                                   b.is);
+  k_setup<TK><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
+                                             b.dU_hist, b.Ubar, b.ic, b.is);
 }
 
 // ---------------------------------------------------------------------------
@@ -231,7 +255,7 @@ __global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const d
   pdl_launch_dependents();
   const int b = blockIdx.y;
   if (!is[b].active) return;
-  if (skip_first && is[b].newton_iter == 0) return;   // b^0 was written by k_setup
+  if (skip_first && is[b].newton_iter == 0 && !is[b].predicted) return;   // b^0 was written by k_setup
   typedef typename Vec2<TO>::type TO2;
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -241,6 +265,9 @@ __global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const d
   const double2 u0 = u[plane(b, S) + k];
   const double2 s0 = S0[plane(b, S) + k];
   const double d = D[plane(b, S) + k];
+  // acc holds (Phibar.y + ... , -(Phibar.x)) in the form b = -Phibar = (acc.y, -acc.x):
+  // acc.x = dU.y + hTc S0.x + h lam (K+V)dU.x + ..., acc.y = -dU.x + hTc S0.y + ...,
+  // so that the dU term rides on the first FMA instead of a final subtraction.
   double2 dU[3], acc[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
@@ -249,8 +276,8 @@ __global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const d
     dU[m] = c;
     double sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
     double sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
-    acc[m].x = fma(p.hlam[m], sx, p.hTc[m] * s0.x);
-    acc[m].y = fma(p.hlam[m], sy, p.hTc[m] * s0.y);
+    acc[m].x = fma(p.hlam[m], sx, fma(p.hTc[m], s0.x, c.y));
+    acc[m].y = fma(p.hlam[m], sy, fma(p.hTc[m], s0.y, -c.x));
   }
 #pragma unroll
   for (int q = 0; q < kGauss; ++q) {
@@ -271,8 +298,8 @@ __global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const d
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     TO2 o;
-    o.x = from_double<TO>(acc[i].y - dU[i].x);
-    o.y = from_double<TO>(-acc[i].x - dU[i].y);
+    o.x = from_double<TO>(acc[i].y);
+    o.y = from_double<TO>(-acc[i].x);
     ob[(size_t)i * S + k] = o;
   }
 }
@@ -794,7 +821,7 @@ __device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaG
 }
 
 // Newton update (Algorithm 1 lines 18-20) and loop test (line 12; failure rule of
-// Sec. 2.2): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (dU^0 = 0, so the
+// Sec. 2.2): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (from dU^0 = 0 the
 // first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
 // block of each instance runs its test: continue while ||r^l||_inf > rtol ||u0||_inf
 // (and, when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
@@ -820,7 +847,7 @@ __global__ void __launch_bounds__(kSiteThreads) k_update(StepParams p, const typ
   if (threadIdx.x < 3 * SK)
     cs[threadIdx.x / SK][threadIdx.x % SK] =
         (TK)coef[((size_t)inst * 3 + threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
-  const bool first = (*(volatile int*)&I.newton_iter) == 0;
+  const bool first = (*(volatile int*)&I.newton_iter) == 0 && !I.predicted;
   __syncthreads();
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -924,11 +951,45 @@ void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long 
 #undef MB4_CALL
 }
 
+// Newton start of the next step (option newton_start).  Fixed mode: extrapolate.
+// Adaptive mode: record the Newton iterations this step's start took; take the start
+// whose last measured cost is lower -- iterations, plus pred_cost for the extra residual
+// of an extrapolated start -- and every explore_every steps the other one, so that a
+// change of regime is seen.  Integer data only: the choice is reproducible.
+__device__ void choose_next_start(const StepParams& p, InstStatus& I) {
+  const int full_before = I.pred_count >= p.pred_order;   // this step's extrapolation used all m
+  if (I.pred_count < p.pred_order) I.pred_count += 1;
+  if (!p.pred_adaptive) {
+    I.next_predicted = 1;
+    return;
+  }
+  const int m = I.predicted ? 1 : 0;
+  if (m == 0 || full_before) {                   // a start with less history is not representative
+    I.start_iters[m] = I.newton_iter;
+    if (!(I.start_known & (1 << m)) && (I.start_known | (1 << m)) == 3) I.explore_in = p.explore_every;
+    I.start_known |= 1 << m;
+  }
+  int next;
+  if (!(I.start_known & 2)) {
+    next = (I.pred_count >= p.pred_order) ? 1 : 0;   // try the extrapolation once it has full history
+  } else if (!(I.start_known & 1)) {
+    next = 0;
+  } else {
+    next = (1000 * I.start_iters[1] + p.pred_cost_milli < 1000 * I.start_iters[0]) ? 1 : 0;
+    if (--I.explore_in <= 0) {
+      next = 1 - next;
+      I.explore_in = p.explore_every;
+    }
+  }
+  I.next_predicted = next;
+}
+
 // Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = u0 + sum_n T[2][n] dU_n, for the
 // instances that took part in the step and did not fail.  Block 0 of each instance
 // books the step and re-arms the instance for the next one.
 __global__ void __launch_bounds__(kSiteThreads) k_accept(StepParams p, double2* __restrict__ u,
-                                                const double2* __restrict__ Ubar, InstStatus* is) {
+                                                const double2* __restrict__ Ubar, double2* __restrict__ dUh,
+                                                InstStatus* is) {
   const int inst = blockIdx.y;
   InstStatus& I = is[inst];
   const int took_part = I.in_step;
@@ -941,11 +1002,21 @@ __global__ void __launch_bounds__(kSiteThreads) k_accept(StepParams p, double2* 
     r.x = fma(p.T[2][2], c.x, fma(p.T[2][1], b.x, fma(p.T[2][0], a.x, r.x)));
     r.y = fma(p.T[2][2], c.y, fma(p.T[2][1], b.y, fma(p.T[2][0], a.y, r.y)));
     u[plane(inst, S) + k] = r;
+    if (p.pred_order > 0) {   // keep the converged increments, newest first (entries past
+                              // pred_count are moved too, unread, so no block reads pred_count)
+      double2* H = dUh + (size_t)inst * p.pred_order * 3 * S;
+      for (int q = p.pred_order - 1; q >= 1; --q)
+        for (int i = 0; i < 3; ++i) H[(size_t)(3 * q + i) * S + k] = H[(size_t)(3 * (q - 1) + i) * S + k];
+      H[k] = a;
+      H[(size_t)S + k] = b;
+      H[(size_t)2 * S + k] = c;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (took_part && !failed) {
       I.steps_done += 1;
       I.newton_total += I.newton_iter;
+      if (p.pred_order > 0) choose_next_start(p, I);
     }
     I.newton_iter = 0;
     I.nonfinite = 0;
@@ -955,16 +1026,17 @@ __global__ void __launch_bounds__(kSiteThreads) k_accept(StepParams p, double2* 
     const int go = I.enabled && !I.error;
     I.in_step = go;
     I.active = go;
+    I.predicted = go && p.pred_order > 0 && I.pred_count > 0 && I.next_predicted;
   }
 }
 
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
-  k_accept<<<grid, kSiteThreads, 0, s>>>(p, b.u, b.Ubar, b.is);
+  k_accept<<<grid, kSiteThreads, 0, s>>>(p, b.u, b.Ubar, b.dU_hist, b.is);
 }
 
 // Arms every enabled instance without an error for the next step (start of a call).
-__global__ void k_arm(int B, InstStatus* is, BatchCtl* bc) {
+__global__ void k_arm(int B, int pred_order, InstStatus* is, BatchCtl* bc) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b == 0) {
     bc->ticket_inst = 0u;
@@ -983,10 +1055,44 @@ __global__ void k_arm(int B, InstStatus* is, BatchCtl* bc) {
   const int go = I.enabled && !I.error;
   I.in_step = go;
   I.active = go;
+  I.predicted = go && pred_order > 0 && I.pred_count > 0 && I.next_predicted;
+}
+
+// set_state: pack (re, im) into the state and flag the instances whose state changes
+// (bitwise); those forget their Newton-start history, which no longer fits.
+__global__ void k_set_state(const double* __restrict__ re, const double* __restrict__ im, double2* __restrict__ z,
+                            size_t n, int S, int* changed) {
+  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double2 old = z[k];
+  const double2 v = make_double2(re[k], im[k]);
+  z[k] = v;
+  if (dbits(old.x) != dbits(v.x) || dbits(old.y) != dbits(v.y)) {
+    int* f = changed + k / (size_t)S;
+    if (!*(volatile int*)f) atomicOr(f, 1);
+  }
+}
+
+__global__ void k_forget_changed(const int* __restrict__ changed, InstStatus* is, int ninst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < ninst && changed[b]) {
+    is[b].pred_count = 0;
+    is[b].start_known = 0;
+    is[b].explore_in = 0;
+  }
+}
+
+void launch_set_state(const StepParams& p, const DevBuffers& b, const double* re, const double* im, int first,
+                      int ninst, cudaStream_t s) {
+  const size_t n = (size_t)ninst * p.S;
+  cudaMemsetAsync(b.changed + first, 0, (size_t)ninst * sizeof(int), s);
+  if (n) k_set_state<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(re, im, b.u + (size_t)first * p.S, n, p.S,
+                                                                  b.changed + first);
+  k_forget_changed<<<(ninst + 255) / 256, 256, 0, s>>>(b.changed + first, b.is + first, ninst);
 }
 
 void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  k_arm<<<(p.B + 255) / 256, 256, 0, s>>>(p.B, b.is, b.bc);
+  k_arm<<<(p.B + 255) / 256, 256, 0, s>>>(p.B, p.pred_order, b.is, b.bc);
 }
 
 // ---------------------------------------------------------------------------

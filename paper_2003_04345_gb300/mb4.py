@@ -60,7 +60,7 @@ class Options(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("krylov_s", C.c_int),
                 ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
-                ("overlap_launches", C.c_int)]
+                ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -222,7 +222,7 @@ class Integrator:
 
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
         """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
-        stream, use_graph, newton_predict, overlap_launches)."""
+        stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -371,7 +371,8 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 
 
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
-             c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True):
+             c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True,
+             newton_start=None, newton_start_adaptive=None):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -384,6 +385,10 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
     opt.use_graph = 1 if use_graph else 0
     opt.newton_predict = float(newton_predict)
     opt.overlap_launches = 1 if overlap_launches else 0
+    if newton_start is not None:                # None keeps the library default
+        opt.newton_start = int(newton_start)
+    if newton_start_adaptive is not None:
+        opt.newton_start_adaptive = 1 if newton_start_adaptive else 0
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
