@@ -239,6 +239,7 @@ def run_ours(args):
         ms_max = max_over_ranks(ms, world, dev)
         s_dim = 4
         results[precision] = {
+            "launch_shape": list(it.launch_shape()),
             "value": world * S * K / (ms_max / 1e3), "ms_per_step": ms_max / K, "wall_s": wall,
             "newton_per_step": newton / K, "energy_drift": drift,
             "norm_drift": abs(o1["norm2"] - o0["norm2"]), "krylov_s": s_dim,
@@ -318,6 +319,8 @@ def run_ours(args):
         "config": {"workload": "grid512_fp64", "nx": w.nx, "ny": w.ny, "h": w.h, "chi": w.chi, "W": w.W,
                    "defect_fraction": w.defect_fraction, "V_defect": w.V_defect, "sigma": w.sigma,
                    "precision": "fp64", "krylov_s": fp["krylov_s"], "newton_start": 2, "log_every": LOG_EVERY,
+                   "threads_per_block": {"fp64": fp["launch_shape"], "mixed": results["mixed"]["launch_shape"],
+                                         "order": "setup/accept, residual, basis, update (autotuned)"},
                    "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "energy_drift": fp["energy_drift"], "newton_per_step": fp["newton_per_step"],
@@ -339,10 +342,11 @@ def run_ours(args):
         "gpu_launches": fp["launches"],
         "clocks": clocks,
     }
-    if not args.no_extra:
+    if not args.no_extra and world == 1:        # single-GPU lines: one process owns the device
         line["ensemble"] = bench_ensemble(args, flush)
         line["grid2048"] = bench_grid2048(args, flush)
         line["served"] = bench_served(args)
+        line["served"]["rate_sweep"] = [bench_served(args, n_requests=8, rate=r) for r in (1.0, 4.0)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0:
@@ -388,7 +392,9 @@ def bench_ensemble(args, flush, K=20):
             bt.step(3)
             ms, newton = _timed_batch_steps(bt, K, flush)
             H1 = bt.observables()[:, 0]
+            shape = list(bt.launch_shape())
         out[precision] = {"value": B * n * n * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
+                          "threads_per_block": shape,
                           "newton_per_member_step": newton / (B * K),
                           "energy_drift_max": float(np.max(np.abs(H1 - H0) / np.abs(H0)))}
     return out
@@ -432,7 +438,10 @@ def bench_served(args, n_requests=24, rate=200.0):
     sizes in {64^2 .. 1024^2}, step counts in [100, 5000], h in {0.002, 0.005,
     0.01}, per-request seed and defect density 0-2%, replayed for the first
     n_requests arrivals through the continuous-batching server (mixed precision,
-    64 GiB HBM budget).  Latency = completion - arrival."""
+    64 GiB HBM budget).  Latency = completion - arrival.  200 req/s offers ~100x
+    what one GPU can serve, so this measures a saturated queue; the rate sweep
+    replays the first requests of the same trace at lower rates (the arrival gaps
+    scale with 1/rate) to show the unsaturated latency."""
     import numpy as np
     from paper_2003_04345_gb300 import inputs, mb4
     trace = inputs.served_trace(n_requests, rate, seed=0)

@@ -123,6 +123,15 @@ typedef struct {
                             extrapolated start needs -- and tries the other start every 32
                             steps; the choice depends only on iteration counts, so runs repeat
                             bit for bit.  0 = always extrapolate once history exists.        */
+    int    autotune;     /* 1 (default): at create, time the one-site-per-thread kernels
+                            (residual, Krylov basis, update; set-up and accept follow the
+                            residual) with 64, 128 and 256 threads per block on the context's
+                            own buffers and keep the fastest (128 unless another is faster by
+                            more than 5%); the choice is cached per device,
+                            precision, grid, batch size and s.  Every choice gives the same
+                            results bit for bit.  0: 128 threads everywhere.                 */
+    int    site_threads; /* 0 (default): as autotune says.  64, 128 or 256: that many threads per
+                            block for every per-site kernel, no tuning.                       */
 } mb4_options;
 
 #define MB4_MAX_NEWTON_START 3
@@ -195,6 +204,10 @@ int mb4_wait(mb4_ctx* ctx, mb4_stats* stats);
  * for bit).  Adds to ms[MB4_K_COUNT] the summed device time of each kernel
  * class and to launches[MB4_K_COUNT] its launch count (both nullable). */
 int mb4_step_profiled(mb4_ctx* ctx, int nsteps, mb4_stats* stats, double* ms, long long* launches);
+
+/* Threads per block the context launches its per-site kernels with:
+ * shape4 = {set-up and accept, residual, Krylov basis (FP64 stencil), update}. */
+int mb4_get_launch_shape(const mb4_ctx* ctx, int* shape4);
 
 /* Energy H = U_K + U_E + U_nl of the current state (Sec. 2.1: U_K = u^H K u,
  * U_E = u^H V u, U_nl = -(gamma/2)||n||^2 = (chi/2) sum |u|^4), with compensated
@@ -273,6 +286,9 @@ int mb4_batch_observables(const mb4_batch* b, double* out);
 
 /* Clear the error of every instance (the state is the last accepted one). */
 int mb4_batch_clear_errors(mb4_batch* b);
+
+/* As mb4_get_launch_shape, for a batch. */
+int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape4);
 
 /* Device bytes a batch of this shape and options would allocate (for admission). */
 long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt);

@@ -3,7 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -86,6 +90,9 @@ int validate_options(const mb4_options* in, mb4_options* o) {
   if (o->overlap_launches != 0 && o->overlap_launches != 1) return MB4_ERR_INVALID_ARG;
   if (o->newton_start < 0 || o->newton_start > MB4_MAX_NEWTON_START) return MB4_ERR_INVALID_ARG;
   if (o->newton_start_adaptive != 0 && o->newton_start_adaptive != 1) return MB4_ERR_INVALID_ARG;
+  if (o->autotune != 0 && o->autotune != 1) return MB4_ERR_INVALID_ARG;
+  if (o->site_threads != 0 && o->site_threads != 64 && o->site_threads != 128 && o->site_threads != 256)
+    return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -142,6 +149,7 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.B = c->B;
   p.s = o.krylov_s;
   p.pdl = o.overlap_launches;
+  p.bs_site = p.bs_residual = p.bs_matvec = p.bs_update = o.site_threads > 0 ? o.site_threads : 128;
   p.pred_order = o.newton_start;
   p.pred_adaptive = o.newton_start_adaptive;
   // Cost of the extra residual of an extrapolated start, in Newton iterations (1/1000):
@@ -333,6 +341,93 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
   return (long long)t;
 }
 
+// ---- launch-shape autotuner ------------------------------------------------
+// The per-site kernels (residual, FP64 Krylov basis, update) are timed with 64, 128
+// and 256 threads per block on the batch's own buffers (10 launches each after a
+// warm-up), and the fastest kept: 128 unless another is faster by more than 5%, a
+// margin above the launch-to-launch noise of these 10-80 us kernels.  Set-up and accept take the residual's
+// shape.  None of this changes results: those kernels compute each site alone.
+typedef std::tuple<int, int, int, int, int, int> TuneKey;   // device, precision, nx, ny, B, s
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 4>> g_tune;
+
+int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  StepParams p = c->p;
+  if (which == 0) p.bs_residual = bs;
+  else if (which == 1) p.bs_matvec = bs;
+  else p.bs_update = bs;
+  const bool mixed = (c->precision == MB4_MIXED);
+  float total = 0.f;
+  for (int r = 0; r < 11; ++r) {
+    launch_arm(p, c->b, c->stream);                // active, Newton iteration 0
+    MB4_TRY(cudaEventRecord(e0, c->stream));
+    if (which == 0) {
+      if (mixed) launch_residual<float>(p, c->b, false, c->stream);
+      else launch_residual<double>(p, c->b, false, c->stream);
+    } else if (which == 1) {
+      launch_matvecs<double>(p, c->b, c->stream);
+    } else {
+      if (mixed) launch_update<float>(p, c->b, 0ull, 0, c->stream);
+      else launch_update<double>(p, c->b, 0ull, 0, c->stream);
+    }
+    MB4_TRY(cudaEventRecord(e1, c->stream));
+    MB4_TRY(cudaEventSynchronize(e1));
+    float t = 0.f;
+    MB4_TRY(cudaEventElapsedTime(&t, e0, e1));
+    if (r > 0) total += t;                         // the first launch warms up
+  }
+  *ms = total / 10.f;
+  return MB4_OK;
+}
+
+int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
+  const TuneKey key(c->device, c->precision, grid->nx, grid->ny, c->B, c->p.s);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      c->p.bs_site = it->second[0];
+      c->p.bs_residual = it->second[1];
+      c->p.bs_matvec = it->second[2];
+      c->p.bs_update = it->second[3];
+      return MB4_OK;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MB4_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return MB4_ERR_CUDA;
+  }
+  const int cand[3] = {64, 128, 256};
+  int chosen[3] = {128, 128, 128};
+  int rc = MB4_OK;
+  for (int which = 0; which < 3 && rc == MB4_OK; ++which) {
+    if (which == 1 && c->precision == MB4_MIXED) continue;   // the FP32 basis uses matrix powers
+    float t[3];
+    for (int k = 0; k < 3 && rc == MB4_OK; ++k) rc = time_site_kernel(c, which, cand[k], e0, e1, &t[k]);
+    if (rc != MB4_OK) break;
+    int best = 1;                                  // 128 unless another is clearly faster
+    for (int k = 0; k < 3; ++k)
+      if (t[k] < 0.95f * t[best]) best = k;
+    chosen[which] = cand[best];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != MB4_OK) return rc;
+  c->p.bs_residual = chosen[0];
+  c->p.bs_matvec = chosen[1];
+  c->p.bs_update = chosen[2];
+  c->p.bs_site = chosen[0];
+  // the timing launches wrote scratch, the increments and the status: start clean
+  MB4_TRY(cudaMemsetAsync(c->b.Ubar, 0, (size_t)3 * c->B * c->p.S * sizeof(double2), c->stream));
+  MB4_TRY(cudaMemsetAsync(c->b.bc, 0, sizeof(BatchCtl), c->stream));
+  MB4_CHECK(write_status(c));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {c->p.bs_site, c->p.bs_residual, c->p.bs_matvec, c->p.bs_update};
+  return MB4_OK;
+}
+
 // Create a batch of B instances; V is host B*S doubles, chi host B doubles.
 int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const double* chi, double h,
                const mb4_options& o) {
@@ -392,6 +487,7 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_TRY(cudaMemsetAsync(d.coef, 0, (size_t)B * 3 * kMaxS * sizeof(double), c->stream));
   MB4_TRY(cudaMemsetAsync(d.bc, 0, sizeof(BatchCtl), c->stream));
   MB4_CHECK(write_status(c));
+  if (o.autotune && o.site_threads == 0) MB4_CHECK(autotune_launch_shapes(c, grid));
   if (c->use_graph) MB4_CHECK(build_graph(c));
   return MB4_OK;
 }
@@ -484,6 +580,7 @@ int mb4_default_options(mb4_options* o) {
   o->overlap_launches = 1;
   o->newton_start = 2;
   o->newton_start_adaptive = 1;
+  o->autotune = 1;
   return MB4_OK;
 }
 
@@ -638,6 +735,17 @@ int mb4_batch_clear_errors(mb4_batch* c) {
   if (!c) return MB4_ERR_INVALID_ARG;
   return clear_errors(c);
 }
+
+int mb4_batch_get_launch_shape(const mb4_batch* c, int* shape4) {
+  if (!c || !shape4) return MB4_ERR_INVALID_ARG;
+  shape4[0] = c->p.bs_site;
+  shape4[1] = c->p.bs_residual;
+  shape4[2] = c->p.bs_matvec;
+  shape4[3] = c->p.bs_update;
+  return MB4_OK;
+}
+
+int mb4_get_launch_shape(const mb4_ctx* c, int* shape4) { return mb4_batch_get_launch_shape(c, shape4); }
 
 // ---- single contexts: a batch of one -------------------------------------
 

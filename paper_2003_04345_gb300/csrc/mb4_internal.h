@@ -40,6 +40,8 @@ struct StepParams {
   int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   int pdl;                 // programmatic dependent launch inside the Newton loop
+  int bs_site, bs_residual, bs_matvec, bs_update;   // threads per block of the per-site kernels
+                                                    // (bs_site: k_setup, k_accept)
   int pred_order;          // Newton start: 0 = e3 (x) u0; m = extrapolate the last m increments
   int pred_adaptive;       // choose per instance between the two starts by measured cost
   int pred_cost_milli;     // the extrapolated start's extra residual, in 1/1000 Newton iterations

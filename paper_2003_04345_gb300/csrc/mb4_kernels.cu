@@ -136,9 +136,10 @@ template <typename T> __device__ __forceinline__ float to_float(T x);
 template <> __device__ __forceinline__ float to_float<float>(float x) { return x; }
 template <> __device__ __forceinline__ float to_float<double>(double x) { return d2f_trunc(x); }
 
-// Threads per block of the one-site-per-thread kernels: small blocks give many
-// blocks per SM and short tails when a launch is only a few waves deep.
-constexpr int kSiteThreads = 128;
+// Threads per block of the one-site-per-thread kernels: chosen per context (StepParams
+// bs_*; the autotuner of the C ABI or 128), at most kSiteThreadsMax.  Their results do
+// not depend on it: each site is computed alone and the only reductions are maxima.
+constexpr int kSiteThreadsMax = 256;
 
 // Offsets of instance b's data.
 __device__ __forceinline__ size_t plane(int b, int S) { return (size_t)b * S; }
@@ -158,10 +159,10 @@ __device__ __forceinline__ size_t level(int b, int a, int i, int s, int S) {
 // from an extrapolation (option newton_start), at the polynomial extrapolation of
 // the last m converged increments (m = 1: the last; 2: 2 H0 - H1; 3: 3 H0 - 3 H1 + H2,
 // H0 the newest), whose residual the first k_residual then evaluates.
-// Grid: (sites / 128, B).
+// Grid: (sites / bs_site, B).
 // ---------------------------------------------------------------------------
 template <typename TK>
-__global__ void __launch_bounds__(kSiteThreads) k_setup(StepParams p, const double2* __restrict__ u,
+__global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
                                                JCoef<TK>* __restrict__ jc, typename Vec2<TK>::type* __restrict__ v,
                                                const double2* __restrict__ dUh, double2* __restrict__ dUb,
@@ -230,8 +231,8 @@ __global__ void __launch_bounds__(kSiteThreads) k_setup(StepParams p, const doub
 
 template <typename TK>
 void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
-  k_setup<TK><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
+  dim3 grid((p.S + p.bs_site - 1) / p.bs_site, p.B);
+  k_setup<TK><<<grid, p.bs_site, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
                                              b.dU_hist, b.Ubar, b.ic, b.is);
 }
 
@@ -245,7 +246,7 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 // T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
 // ---------------------------------------------------------------------------
 template <typename TO>
-__global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const double2* __restrict__ u,
+__global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
                                                   const double2* __restrict__ dUb,
                                                   typename Vec2<TO>::type* __restrict__ out, long long out_stride,
@@ -306,16 +307,16 @@ __global__ void __launch_bounds__(kSiteThreads) k_residual(StepParams p, const d
 
 template <typename TK>
 void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, cudaStream_t s) {
-  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
+  dim3 grid((p.S + p.bs_residual - 1) / p.bs_residual, p.B);
   // b_i of instance b goes to its level 0: level(b, 0, i) = b*(s+1)*3*S + i*S
-  k_residual<TK><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
+  k_residual<TK><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
                                       (long long)(p.s + 1) * 3 * p.S, skip_first ? 1 : 0, b.ic, b.is);
 }
 
 template <typename TK>
 void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3, cudaStream_t s) {
-  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
-  k_residual<double><<<grid, kSiteThreads, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.ic, b.is);
+  dim3 grid((p.S + p.bs_residual - 1) / p.bs_residual, p.B);
+  k_residual<double><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.ic, b.is);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +327,7 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 // (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
 // ---------------------------------------------------------------------------
 template <typename TK>
-__global__ void __launch_bounds__(kSiteThreads) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
+__global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
                                                 const InstConst* __restrict__ ic, const InstStatus* is) {
   pdl_wait();
@@ -731,9 +732,9 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 #undef MB4_CALL
     return;
   }
-  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
+  dim3 grid((p.S + p.bs_matvec - 1) / p.bs_matvec, p.B);
   for (int a = 0; a < p.s; ++a)
-    launch_k(p.pdl != 0, k_matvec<TK>, grid, dim3(kSiteThreads), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a,
+    launch_k(p.pdl != 0, k_matvec<TK>, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a,
              (const InstConst*)b.ic, (const InstStatus*)b.is);
 }
 
@@ -825,9 +826,9 @@ __device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaG
 // first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
 // block of each instance runs its test: continue while ||r^l||_inf > rtol ||u0||_inf
 // (and, when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
-// for at most newton_max iterations.  Grid: (sites / 256, B).
+// for at most newton_max iterations.  Grid: (sites / bs_update, B).
 template <typename TK, int SK>
-__global__ void __launch_bounds__(kSiteThreads) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
+__global__ void __launch_bounds__(kSiteThreadsMax) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                 const double* __restrict__ coef, const double2* __restrict__ u,
                                                 double2* __restrict__ Ubar, InstStatus* is, BatchCtl* bc,
                                                 cudaGraphConditionalHandle h, int use_cond) {
@@ -943,9 +944,9 @@ __global__ void __launch_bounds__(kSiteThreads) k_update(StepParams p, const typ
 
 template <typename TK>
 void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long h, int use_cond, cudaStream_t s) {
-  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
+  dim3 grid((p.S + p.bs_update - 1) / p.bs_update, p.B);
 #define MB4_CALL(N)                                                                                      \
-  launch_k(p.pdl != 0, k_update<TK, N>, grid, dim3(kSiteThreads), 0, s, p, (const typename Vec2<TK>::type*)b.v, \
+  launch_k(p.pdl != 0, k_update<TK, N>, grid, dim3(p.bs_update), 0, s, p, (const typename Vec2<TK>::type*)b.v, \
            (const double*)b.coef, (const double2*)b.u, b.Ubar, b.is, b.bc, (cudaGraphConditionalHandle)h, use_cond)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
@@ -987,7 +988,7 @@ __device__ void choose_next_start(const StepParams& p, InstStatus& I) {
 // Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = u0 + sum_n T[2][n] dU_n, for the
 // instances that took part in the step and did not fail.  Block 0 of each instance
 // books the step and re-arms the instance for the next one.
-__global__ void __launch_bounds__(kSiteThreads) k_accept(StepParams p, double2* __restrict__ u,
+__global__ void __launch_bounds__(kSiteThreadsMax) k_accept(StepParams p, double2* __restrict__ u,
                                                 const double2* __restrict__ Ubar, double2* __restrict__ dUh,
                                                 InstStatus* is) {
   const int inst = blockIdx.y;
@@ -1031,8 +1032,8 @@ __global__ void __launch_bounds__(kSiteThreads) k_accept(StepParams p, double2* 
 }
 
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  dim3 grid((p.S + kSiteThreads - 1) / kSiteThreads, p.B);
-  k_accept<<<grid, kSiteThreads, 0, s>>>(p, b.u, b.Ubar, b.dU_hist, b.is);
+  dim3 grid((p.S + p.bs_site - 1) / p.bs_site, p.B);
+  k_accept<<<grid, p.bs_site, 0, s>>>(p, b.u, b.Ubar, b.dU_hist, b.is);
 }
 
 // Arms every enabled instance without an error for the next step (start of a call).

@@ -36,11 +36,12 @@ KERNEL_CLASSES = ("setup", "residual", "matvec", "gram", "update", "accept")
 # Every entry point include/mb4.h declares.
 EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", "mb4_get_state",
            "mb4_get_stages", "mb4_step", "mb4_step_async", "mb4_wait", "mb4_step_profiled", "mb4_energy",
-           "mb4_norm", "mb4_observables", "mb4_residual", "mb4_solve_shifted", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
+           "mb4_norm", "mb4_observables", "mb4_residual", "mb4_solve_shifted", "mb4_get_launch_shape",
+           "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
            "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
            "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
-           "mb4_batch_clear_errors", "mb4_batch_bytes", "mb4_server_create", "mb4_server_destroy",
-           "mb4_server_submit", "mb4_server_run", "mb4_server_result", "mb4_server_clock")
+           "mb4_batch_clear_errors", "mb4_batch_get_launch_shape", "mb4_batch_bytes", "mb4_server_create",
+           "mb4_server_destroy", "mb4_server_submit", "mb4_server_run", "mb4_server_result", "mb4_server_clock")
 
 
 class Grid(C.Structure):
@@ -60,7 +61,8 @@ class Options(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("krylov_s", C.c_int),
                 ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
-                ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int)]
+                ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int),
+                ("autotune", C.c_int), ("site_threads", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -116,6 +118,8 @@ def lib():
         L.mb4_get_stages.argtypes = [_P, _P, _P, C.c_int]
         L.mb4_step.argtypes = [_P, C.c_int, C.POINTER(Stats)]
         L.mb4_step_async.argtypes = [_P, C.c_int]
+        L.mb4_get_launch_shape.argtypes = [_P, C.POINTER(C.c_int)]
+        L.mb4_batch_get_launch_shape.argtypes = [_P, C.POINTER(C.c_int)]
         L.mb4_wait.argtypes = [_P, C.POINTER(Stats)]
         L.mb4_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), _D, C.POINTER(C.c_longlong)]
         L.mb4_energy.argtypes = [_P, _D, _D]
@@ -222,7 +226,8 @@ class Integrator:
 
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
         """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
-        stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive)."""
+        stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive,
+        autotune, site_threads)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -292,6 +297,12 @@ class Integrator:
         if check:
             _check(rc, "mb4_step")
         return (st.as_dict(), rc) if not check else st.as_dict()
+
+    def launch_shape(self):
+        """Threads per block of the per-site kernels: (set-up/accept, residual, basis, update)."""
+        out = (C.c_int * 4)()
+        _check(lib().mb4_get_launch_shape(self._ctx, out), "mb4_get_launch_shape")
+        return tuple(out)
 
     def step_async(self, nsteps=1):
         """Queue nsteps steps on the stream without waiting (see wait)."""
@@ -372,7 +383,7 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
              c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True,
-             newton_start=None, newton_start_adaptive=None):
+             newton_start=None, newton_start_adaptive=None, autotune=None, site_threads=None):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -389,6 +400,10 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
         opt.newton_start = int(newton_start)
     if newton_start_adaptive is not None:
         opt.newton_start_adaptive = 1 if newton_start_adaptive else 0
+    if autotune is not None:
+        opt.autotune = 1 if autotune else 0
+    if site_threads is not None:
+        opt.site_threads = int(site_threads)
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
@@ -483,6 +498,11 @@ class Batch:
 
     def clear_errors(self):
         _check(lib().mb4_batch_clear_errors(self._ctx), "mb4_batch_clear_errors")
+
+    def launch_shape(self):
+        out = (C.c_int * 4)()
+        _check(lib().mb4_batch_get_launch_shape(self._ctx, out), "mb4_batch_get_launch_shape")
+        return tuple(out)
 
 
 class Server:

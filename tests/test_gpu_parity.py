@@ -68,7 +68,8 @@ def test_residual_kernel_matches_oracle(mb4, nx, ny, precision):
                                              ("mixed", 8, 1e-5)])
 def test_shifted_solves_reduce_residual(mb4, precision, s, eta):
     """One s-step GMRES cycle reduces ||b - (I - h lam_i J) x|| / ||b|| below eta
-    for a random right-hand side on the 16x16 workload (h = 0.01)."""
+    for a random right-hand side on the 16x16 workload (h = 0.01), and lands within
+    the matching distance of the dense LU solution of each shifted system."""
     w = inputs.grid16_fp64()
     S = w.S
     V = w.potential()
@@ -85,6 +86,10 @@ def test_shifted_solves_reduce_residual(mb4, precision, s, eta):
         br = orc.to_real(b[i])
         res = br - (xr - w.h * lam[i] * (J @ xr))
         assert np.linalg.norm(res) <= eta * np.linalg.norm(br), (i, np.linalg.norm(res) / np.linalg.norm(br))
+        A = np.eye(2 * S) - w.h * lam[i] * (J.toarray() if hasattr(J, "toarray") else J)
+        xs = np.linalg.solve(A, br)                        # dense LU with partial pivoting
+        bound = np.linalg.norm(np.linalg.inv(A), 2) * eta * np.linalg.norm(br)
+        assert np.linalg.norm(xr - xs) <= 1.01 * bound, (i, np.linalg.norm(xr - xs), bound)
 
 
 # ---------------------------------------------------------------------------
@@ -240,6 +245,24 @@ def test_overlapped_launches_change_nothing(mb4, precision, use_graph):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_launch_shapes_change_nothing(mb4, precision):
+    """Every threads-per-block choice the autotuner can make gives the same step bit
+    for bit; the tuned shape is one of them."""
+    w = inputs.grid16_fp64()
+    out = []
+    for bs in (64, 128, 256):
+        with mb4.from_workload(w, precision=precision, site_threads=bs) as it:
+            assert it.launch_shape() == (bs,) * 4
+            it.step(8)
+            out.append(it.get_state())
+    assert all(np.array_equal(out[0], o) for o in out[1:])
+    with mb4.from_workload(w, precision=precision, autotune=True) as it:
+        assert set(it.launch_shape()) <= {64, 128, 256}
+        it.step(8)
+        assert np.array_equal(it.get_state(), out[0])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("start", [0, 2])
 def test_deterministic_and_resumable(mb4, precision, start):
     """Runs repeat bit for bit.  Resuming from a saved state repeats them bit for bit
@@ -329,7 +352,8 @@ def test_nonfinite_state_is_reported(mb4):
 
 
 def test_invalid_arguments_rejected(mb4):
-    for kw in ({"nx": 2, "ny": 8}, {"h": 0.0}, {"krylov_s": 11}, {"precision": 7}):
+    for kw in ({"nx": 2, "ny": 8}, {"h": 0.0}, {"krylov_s": 11}, {"precision": 7}, {"site_threads": 96},
+               {"newton_start": 4}):
         args = {"nx": 4, "ny": 4, "h": 0.01}
         args.update(kw)
         nx, ny = args.pop("nx"), args.pop("ny")
