@@ -71,7 +71,8 @@ def kernel_model(kclass, precision, s):
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_grid512.txt")
-KERNEL_SOURCES = ("paper_2003_04345_gb300/csrc/mb4_kernels.cu", "paper_2003_04345_gb300/csrc/mb4_internal.h")
+KERNEL_SOURCES = ("paper_2003_04345_gb300/csrc/mb4_kernels.cu", "paper_2003_04345_gb300/csrc/mb4_device.cuh",
+                  "paper_2003_04345_gb300/csrc/mb4_precond.cu", "paper_2003_04345_gb300/csrc/mb4_internal.h")
 
 
 def kernel_source_hash():

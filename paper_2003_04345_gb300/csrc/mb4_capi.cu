@@ -39,6 +39,7 @@ struct mb4_batch {
   std::vector<InstStatus> host_status;
   // device step counters at the last wait: stats report the steps since then
   std::vector<long long> base_steps, base_newton;
+  std::vector<double> ebar;       // per instance: mean of onsite + V (spectral preconditioner)
 };
 
 struct mb4_ctx : mb4_batch {};
@@ -93,6 +94,7 @@ int validate_options(const mb4_options* in, mb4_options* o) {
   if (o->autotune != 0 && o->autotune != 1) return MB4_ERR_INVALID_ARG;
   if (o->site_threads != 0 && o->site_threads != 64 && o->site_threads != 128 && o->site_threads != 256)
     return MB4_ERR_INVALID_ARG;
+  if (o->precondition != 0 && o->precondition != 1) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -149,6 +151,7 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.B = c->B;
   p.s = o.krylov_s;
   p.pdl = o.overlap_launches;
+  p.precond = o.precondition;
   p.bs_site = p.bs_residual = p.bs_matvec = p.bs_update = o.site_threads > 0 ? o.site_threads : 128;
   p.pred_order = o.newton_start;
   p.pred_adaptive = o.newton_start_adaptive;
@@ -338,6 +341,9 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
   t += round256(B * sizeof(InstConst)) + round256(B * sizeof(InstStatus)) + round256(sizeof(BatchCtl));
   t += 2 * round256(3 * S * 16) + round256(6 * std::max(BS, S) * 8);   // I/O scratch
   if (o.newton_start > 0) t += round256((size_t)o.newton_start * 3 * BS * 16);
+  if (o.precondition)
+    t += round256((size_t)(o.krylov_s + 1) * 3 * BS * 2 * tk) + 2 * round256((size_t)3 * BS * 2 * tk) +
+         round256((size_t)nx * 2 * tk) + round256((size_t)ny * 2 * tk);
   return (long long)t;
 }
 
@@ -428,6 +434,20 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
   return MB4_OK;
 }
 
+// Spectral preconditioner tables from the instances' mean on-site terms.
+int upload_precond_tables(mb4_batch* c) {
+  if (!c->p.precond) return MB4_OK;
+  if (c->precision == MB4_MIXED)
+    return precond_tables<float>(c->p, c->ebar.data(), c->p.hlam, c->b.pwx, c->b.pwy, c->b.pminv, c->stream);
+  return precond_tables<double>(c->p, c->ebar.data(), c->p.hlam, c->b.pwx, c->b.pwy, c->b.pminv, c->stream);
+}
+
+double mean_of(const double* x, size_t n) {
+  long double s = 0.0L;
+  for (size_t k = 0; k < n; ++k) s += x[k];
+  return (double)(s / (long double)n);
+}
+
 // Create a batch of B instances; V is host B*S doubles, chi host B doubles.
 int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const double* chi, double h,
                const mb4_options& o) {
@@ -451,7 +471,8 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B)
                                               : gram_blocks_per_system<double>(p.s, B);
   if (p.gram_blocks < 1) return MB4_ERR_CUDA;
-  p.use_powers = (o.precision == MB4_MIXED) ? 1 : 0;
+  if (p.precond && (grid->nx > MB4_MAX_PRECOND_SIDE || grid->ny > MB4_MAX_PRECOND_SIDE)) return MB4_ERR_INVALID_ARG;
+  p.use_powers = (o.precision == MB4_MIXED && !p.precond) ? 1 : 0;
   if (p.use_powers) MB4_CHECK(prepare_powers());
 
   DevBuffers& d = c->b;
@@ -463,6 +484,13 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(dalloc(c, (void**)&d.S0, BS * sizeof(double2)));
   MB4_CHECK(dalloc(c, (void**)&d.Ubar, 3 * BS * sizeof(double2)));
   if (p.pred_order > 0) MB4_CHECK(dalloc(c, (void**)&d.dU_hist, (size_t)p.pred_order * 3 * BS * sizeof(double2)));
+  if (p.precond) {
+    MB4_CHECK(dalloc(c, &d.pz, (size_t)(p.s + 1) * 3 * BS * 2 * tk));
+    MB4_CHECK(dalloc(c, &d.ptmp, (size_t)3 * BS * 2 * tk));
+    MB4_CHECK(dalloc(c, &d.pwx, (size_t)grid->nx * 2 * tk));
+    MB4_CHECK(dalloc(c, &d.pwy, (size_t)grid->ny * 2 * tk));
+    MB4_CHECK(dalloc(c, &d.pminv, (size_t)3 * BS * 2 * tk));
+  }
   MB4_CHECK(dalloc(c, &d.jc, BS * 4 * tk));
   MB4_CHECK(dalloc(c, &d.v, (size_t)(p.s + 1) * 3 * BS * 2 * tk));
   MB4_CHECK(dalloc(c, (void**)&d.gram_part, (size_t)B * 3 * p.gram_blocks * nent * sizeof(double)));
@@ -479,6 +507,9 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   for (int b = 0; b < B; ++b) c->host_status[b].enabled = 1;
   c->base_steps.assign(B, 0);
   c->base_newton.assign(B, 0);
+  c->ebar.assign(B, 0.0);
+  for (int b = 0; b < B; ++b) c->ebar[b] = mean_of(D.data() + (size_t)b * S, S);
+  MB4_CHECK(upload_precond_tables(c));
   MB4_TRY(cudaMemcpyAsync(d.V, V, BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(d.d, D.data(), BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(d.ic, ic.data(), B * sizeof(InstConst), cudaMemcpyHostToDevice, c->stream));
@@ -686,6 +717,8 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
   MB4_TRY(cudaMemcpyAsync(c->b.d + (size_t)instance * S, D.data(), S * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream));
   MB4_TRY(cudaMemcpyAsync(c->b.ic + instance, &ic, sizeof(ic), cudaMemcpyHostToDevice, c->stream));
+  c->ebar[instance] = mean_of(D.data(), S);
+  MB4_CHECK(upload_precond_tables(c));
   MB4_CHECK(mb4_batch_set_state(c, instance, re, im, on_device));
   MB4_CHECK(read_status(c));
   InstStatus fresh{};
@@ -940,7 +973,10 @@ int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
     P.run(MB4_K_SETUP, 1, [&] { launch_setup<TK>(c->p, c->b, s); });
     for (;;) {
       P.run(MB4_K_RESIDUAL, 1, [&] { launch_residual<TK>(c->p, c->b, true, s); });
-      P.run(MB4_K_MATVEC, c->p.s, [&] { launch_matvecs<TK>(c->p, c->b, s); });
+      P.run(MB4_K_MATVEC, c->p.s, [&] {
+        if (c->p.precond) launch_precond_basis<TK>(c->p, c->b, s);
+        else launch_matvecs<TK>(c->p, c->b, s);
+      });
       P.run(MB4_K_GRAM, 1, [&] { launch_gram<TK>(c->p, c->b, s); });
       P.run(MB4_K_UPDATE, 1, [&] { launch_update<TK>(c->p, c->b, 0ull, 0, s); });
       MB4_TRY(cudaGetLastError());

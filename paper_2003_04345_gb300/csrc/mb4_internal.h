@@ -40,6 +40,7 @@ struct StepParams {
   int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   int pdl;                 // programmatic dependent launch inside the Newton loop
+  int precond;             // spectral preconditioning of the shifted solves (mb4_precond.cu)
   int bs_site, bs_residual, bs_matvec, bs_update;   // threads per block of the per-site kernels
                                                     // (bs_site: k_setup, k_accept)
   int pred_order;          // Newton start: 0 = e3 (x) u0; m = extrapolate the last m increments
@@ -124,6 +125,13 @@ struct DevBuffers {
   double* obs_part;  // observables partial sums
   double* obs_out;   // B*6
   int* changed;      // B flags: set_state changed the instance's state
+  // spectral preconditioner (precond only): z_a = P v_a (layout of v), a DFT work plane
+  // triple per instance, twiddles along x and y, per-mode inverse multipliers B*3*S (TK2)
+  void* pz;
+  void* ptmp;
+  void* pwx;
+  void* pwy;
+  void* pminv;
   InstConst* ic;     // B
   InstStatus* is;    // B
   BatchCtl* bc;
@@ -163,6 +171,12 @@ template <typename TK> void launch_copy_solution_out(const StepParams& p, const 
 template <typename TK> void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3,
                                                 cudaStream_t st);
 void launch_pack(const double* re, const double* im, double2* z, size_t n, cudaStream_t st);
+// Preconditioned Krylov basis (mb4_precond.cu): z_a = P_i v_a, v_{a+1} = A_i z_a - v_a, a < s.
+template <typename TK> void launch_precond_basis(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// Twiddles and per-mode inverse multipliers 1 / (1 + i h lam_i (ebar_b + Khat(k))) (host-made).
+template <typename TK>
+int precond_tables(const StepParams& p, const double* ebar, const double* hlam_i, void* wx, void* wy, void* minv,
+                   cudaStream_t st);
 void launch_unpack(const double2* z, double* re, double* im, size_t n, cudaStream_t st);
 
 }  // namespace mb4

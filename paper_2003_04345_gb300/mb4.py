@@ -62,7 +62,7 @@ class Options(C.Structure):
                 ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
                 ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int),
-                ("autotune", C.c_int), ("site_threads", C.c_int)]
+                ("autotune", C.c_int), ("site_threads", C.c_int), ("precondition", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -227,7 +227,7 @@ class Integrator:
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
         """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
         stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive,
-        autotune, site_threads)."""
+        autotune, site_threads, precondition)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -383,7 +383,8 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
              c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True,
-             newton_start=None, newton_start_adaptive=None, autotune=None, site_threads=None):
+             newton_start=None, newton_start_adaptive=None, autotune=None, site_threads=None,
+             precondition=None):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -404,6 +405,8 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
         opt.autotune = 1 if autotune else 0
     if site_threads is not None:
         opt.site_threads = int(site_threads)
+    if precondition is not None:
+        opt.precondition = int(precondition)
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
