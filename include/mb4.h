@@ -215,9 +215,10 @@ int mb4_wait(mb4_ctx* ctx, mb4_stats* stats);
  * class and to launches[MB4_K_COUNT] its launch count (both nullable). */
 int mb4_step_profiled(mb4_ctx* ctx, int nsteps, mb4_stats* stats, double* ms, long long* launches);
 
-/* Threads per block the context launches its per-site kernels with:
- * shape4 = {set-up and accept, residual, Krylov basis (FP64 stencil), update}. */
-int mb4_get_launch_shape(const mb4_ctx* ctx, int* shape4);
+/* Launch shape of the context's per-site kernels, shape8[8]: threads per block of
+ * {set-up and accept, residual, Krylov basis (FP64 stencil), update}, then blocks per
+ * instance of the same four (one site per thread). */
+int mb4_get_launch_shape(const mb4_ctx* ctx, int* shape8);
 
 /* Energy H = U_K + U_E + U_nl of the current state (Sec. 2.1: U_K = u^H K u,
  * U_E = u^H V u, U_nl = -(gamma/2)||n||^2 = (chi/2) sum |u|^4), with compensated
@@ -298,7 +299,7 @@ int mb4_batch_observables(const mb4_batch* b, double* out);
 int mb4_batch_clear_errors(mb4_batch* b);
 
 /* As mb4_get_launch_shape, for a batch. */
-int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape4);
+int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);
 
 /* Device bytes a batch of this shape and options would allocate (for admission). */
 long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt);

@@ -351,13 +351,16 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
 // The per-site kernels (residual, FP64 Krylov basis, update) are timed with 64, 128
 // and 256 threads per block on the batch's own buffers (10 launches each after a
 // warm-up), and the fastest kept: 128 unless another is faster by more than 5%, a
-// margin above the launch-to-launch noise of these 10-80 us kernels.  Set-up and accept take the residual's
-// shape.  None of this changes results: those kernels compute each site alone.
-typedef std::tuple<int, int, int, int, int, int> TuneKey;   // device, precision, nx, ny, B, s
+// margin above the launch-to-launch noise of these 10-80 us kernels.  Set-up and
+// accept take the residual's shape.  None of this changes results: those kernels
+// compute each site alone.  (A grid-stride form one wave deep was tried as a further
+// candidate: its loop made the default launch 5% slower, so it is not offered.)
+typedef std::tuple<int, int, int, int, int, int, int> TuneKey;   // device, precision, nx, ny, B, s, precond
 std::mutex g_tune_mu;
 std::map<TuneKey, std::array<int, 4>> g_tune;
 
 int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  if (which == 1 && (c->precision == MB4_MIXED || c->p.precond)) return MB4_ERR_INVALID_ARG;   // FP64 buffers only
   StepParams p = c->p;
   if (which == 0) p.bs_residual = bs;
   else if (which == 1) p.bs_matvec = bs;
@@ -386,16 +389,21 @@ int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_
   return MB4_OK;
 }
 
+void apply_shape(StepParams& p, const std::array<int, 4>& t) {
+  p.bs_site = t[0];
+  p.bs_residual = t[1];
+  p.bs_matvec = t[2];
+  p.bs_update = t[3];
+}
+
 int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
-  const TuneKey key(c->device, c->precision, grid->nx, grid->ny, c->B, c->p.s);
+  const int mixed = (c->precision == MB4_MIXED);
+  const TuneKey key(c->device, c->precision, grid->nx, grid->ny, c->B, c->p.s, c->p.precond);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      c->p.bs_site = it->second[0];
-      c->p.bs_residual = it->second[1];
-      c->p.bs_matvec = it->second[2];
-      c->p.bs_update = it->second[3];
+      apply_shape(c->p, it->second);
       return MB4_OK;
     }
   }
@@ -409,7 +417,9 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
   int chosen[3] = {128, 128, 128};
   int rc = MB4_OK;
   for (int which = 0; which < 3 && rc == MB4_OK; ++which) {
-    if (which == 1 && c->precision == MB4_MIXED) continue;   // the FP32 basis uses matrix powers
+    // the FP64 stencil basis is timed only where it is the basis in use: not in mixed
+    // mode (FP32 buffers, matrix powers) nor with the preconditioner (DFT basis)
+    if (which == 1 && (mixed || c->p.precond)) continue;
     float t[3];
     for (int k = 0; k < 3 && rc == MB4_OK; ++k) rc = time_site_kernel(c, which, cand[k], e0, e1, &t[k]);
     if (rc != MB4_OK) break;
@@ -421,16 +431,14 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != MB4_OK) return rc;
-  c->p.bs_residual = chosen[0];
-  c->p.bs_matvec = chosen[1];
-  c->p.bs_update = chosen[2];
-  c->p.bs_site = chosen[0];
+  const std::array<int, 4> t = {chosen[0], chosen[0], chosen[1], chosen[2]};
+  apply_shape(c->p, t);
   // the timing launches wrote scratch, the increments and the status: start clean
   MB4_TRY(cudaMemsetAsync(c->b.Ubar, 0, (size_t)3 * c->B * c->p.S * sizeof(double2), c->stream));
   MB4_TRY(cudaMemsetAsync(c->b.bc, 0, sizeof(BatchCtl), c->stream));
   MB4_CHECK(write_status(c));
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {c->p.bs_site, c->p.bs_residual, c->p.bs_matvec, c->p.bs_update};
+  g_tune[key] = t;
   return MB4_OK;
 }
 
@@ -769,16 +777,17 @@ int mb4_batch_clear_errors(mb4_batch* c) {
   return clear_errors(c);
 }
 
-int mb4_batch_get_launch_shape(const mb4_batch* c, int* shape4) {
-  if (!c || !shape4) return MB4_ERR_INVALID_ARG;
-  shape4[0] = c->p.bs_site;
-  shape4[1] = c->p.bs_residual;
-  shape4[2] = c->p.bs_matvec;
-  shape4[3] = c->p.bs_update;
+int mb4_batch_get_launch_shape(const mb4_batch* c, int* shape8) {
+  if (!c || !shape8) return MB4_ERR_INVALID_ARG;
+  const int bs[4] = {c->p.bs_site, c->p.bs_residual, c->p.bs_matvec, c->p.bs_update};
+  for (int i = 0; i < 4; ++i) {
+    shape8[i] = bs[i];
+    shape8[4 + i] = (c->p.S + bs[i] - 1) / bs[i];
+  }
   return MB4_OK;
 }
 
-int mb4_get_launch_shape(const mb4_ctx* c, int* shape4) { return mb4_batch_get_launch_shape(c, shape4); }
+int mb4_get_launch_shape(const mb4_ctx* c, int* shape8) { return mb4_batch_get_launch_shape(c, shape8); }
 
 // ---- single contexts: a batch of one -------------------------------------
 

@@ -299,8 +299,9 @@ class Integrator:
         return (st.as_dict(), rc) if not check else st.as_dict()
 
     def launch_shape(self):
-        """Threads per block of the per-site kernels: (set-up/accept, residual, basis, update)."""
-        out = (C.c_int * 4)()
+        """Per-site kernels (set-up/accept, residual, basis, update): threads per block,
+        then blocks per instance."""
+        out = (C.c_int * 8)()
         _check(lib().mb4_get_launch_shape(self._ctx, out), "mb4_get_launch_shape")
         return tuple(out)
 
@@ -503,7 +504,7 @@ class Batch:
         _check(lib().mb4_batch_clear_errors(self._ctx), "mb4_batch_clear_errors")
 
     def launch_shape(self):
-        out = (C.c_int * 4)()
+        out = (C.c_int * 8)()
         _check(lib().mb4_batch_get_launch_shape(self._ctx, out), "mb4_batch_get_launch_shape")
         return tuple(out)
 

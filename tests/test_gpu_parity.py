@@ -252,12 +252,14 @@ def test_launch_shapes_change_nothing(mb4, precision):
     out = []
     for bs in (64, 128, 256):
         with mb4.from_workload(w, precision=precision, site_threads=bs) as it:
-            assert it.launch_shape() == (bs,) * 4
+            shape = it.launch_shape()
+            assert shape[:4] == (bs,) * 4 and shape[4:] == ((w.S + bs - 1) // bs,) * 4
             it.step(8)
             out.append(it.get_state())
     assert all(np.array_equal(out[0], o) for o in out[1:])
     with mb4.from_workload(w, precision=precision, autotune=True) as it:
-        assert set(it.launch_shape()) <= {64, 128, 256}
+        shape = it.launch_shape()
+        assert set(shape[:4]) <= {64, 128, 256} and all(g >= 1 for g in shape[4:])
         it.step(8)
         assert np.array_equal(it.get_state(), out[0])
 
