@@ -174,7 +174,9 @@ def kinetic_matrix(nx, ny, tx, ty, eps0):
 
 
 class Problem:
-    """Grid, hopping, on-site shift, potential V (length S) and chi = -gamma."""
+    """Grid, hopping, on-site shift, potential V (length S) and chi = -gamma:
+    one value, or one per site -- the appendix's m-site model with a nonlinear
+    energy U_I = -(1/2) sum_i gamma_i n_i^2, i.e. v_i = -gamma_i n_i."""
 
     def __init__(self, nx, ny, V, chi, tx=1.0, ty=None, eps0=0.0):
         self.nx, self.ny = int(nx), int(ny)
@@ -183,7 +185,7 @@ class Problem:
         self.ty = float(tx if ty is None else ty)
         self.eps0 = float(eps0)
         self.V = np.asarray(V, dtype=np.float64).reshape(self.S).copy()
-        self.chi = float(chi)
+        self.chi = float(chi) if np.ndim(chi) == 0 else np.asarray(chi, dtype=np.float64).reshape(self.S).copy()
         self.K = kinetic_matrix(self.nx, self.ny, self.tx, self.ty, self.eps0)
         self.A = sp.csr_matrix(self.K + sp.diags(self.V))   # A = K + V (eq. JL)
 
@@ -238,7 +240,8 @@ def residual_at_sites(nx, ny, V, chi, tx, ty, eps0, u0, U, h, sites,
           - ty * (Yat(nby[0]) + Yat(nby[1])))
     X = np.vstack([u0[sites][None, :], U[:, sites]])
     cub = np.einsum("iabd,ak,bk,dk->ik", C3, np.conj(X), X, X)
-    return U[:, sites] - u0[sites][None, :] - h * (-1j) * (AY + chi * cub)
+    chi_s = chi if np.ndim(chi) == 0 else np.asarray(chi, dtype=np.float64)[sites]
+    return U[:, sites] - u0[sites][None, :] - h * (-1j) * (AY + chi_s * cub)
 
 
 # ---------------------------------------------------------------------------
@@ -257,15 +260,15 @@ def to_complex(r, S):
 
 def jacobian_real(prob: Problem, u0):
     """J = J_K + J_E + J_I at u0 in the real [p; q] form: eq. (JL) + eq. (JR)
-    with gamma = -chi:
+    with gamma = -chi (per site when chi is):
       J_K + J_E = [[0, A], [-A, 0]],
-      J_I = gamma [[diag(-2 p q), diag(-p^2 - 3 q^2)], [diag(3 p^2 + q^2), diag(2 p q)]]."""
+      J_I = [[diag(-2 g p q), diag(-g (p^2 + 3 q^2))], [diag(g (3 p^2 + q^2)), diag(2 g p q)]]."""
     p0, q0 = np.real(u0), np.imag(u0)
-    gamma = -prob.chi
+    g = -prob.chi * np.ones_like(p0)
     A = prob.A
     JL = sp.bmat([[None, A], [-A, None]])
-    JI = gamma * sp.bmat([[sp.diags(-2 * p0 * q0), sp.diags(-p0 ** 2 - 3 * q0 ** 2)],
-                          [sp.diags(3 * p0 ** 2 + q0 ** 2), sp.diags(2 * p0 * q0)]])
+    JI = sp.bmat([[sp.diags(-2 * g * p0 * q0), sp.diags(-g * (p0 ** 2 + 3 * q0 ** 2))],
+                  [sp.diags(g * (3 * p0 ** 2 + q0 ** 2)), sp.diags(2 * g * p0 * q0)]])
     return sp.csr_matrix(JL + JI)
 
 

@@ -146,10 +146,17 @@ def test_alpha1_bound_printed_in_paper():
 # ---------------------------------------------------------------------------
 # Residual: exact-coefficient route vs brute-force quadrature.
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("nx,ny,chi,eps0", [(4, 3, 1.3, 0.0), (5, 6, -0.7, 0.45)])
+def _chi_field(S, seed):
+    """Per-site chi = -gamma_i (the appendix's m-site model), both signs."""
+    return np.random.default_rng(seed).uniform(-2.0, 2.0, S)
+
+
+@pytest.mark.parametrize("nx,ny,chi,eps0", [(4, 3, 1.3, 0.0), (5, 6, -0.7, 0.45), (5, 4, "field", 0.2)])
 def test_residual_matches_brute_force_quadrature(nx, ny, chi, eps0):
     rng = np.random.default_rng(7)
     S = nx * ny
+    if chi == "field":
+        chi = _chi_field(S, 17)
     V = rng.uniform(-1, 1, S)
     tx, ty = 1.1, 0.8
     prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
@@ -178,15 +185,19 @@ def test_residual_at_sites_matches_full_residual():
 # ---------------------------------------------------------------------------
 # Whole step.
 # ---------------------------------------------------------------------------
-def test_step_matches_brute_force_root():
+@pytest.mark.parametrize("field", [False, True])
+def test_step_matches_brute_force_root(field):
     """3x3 grid: the root of the brute-force Phi found by MINPACK (finite-difference
-    Jacobian, no decoupling, no E) equals the oracle's Newton result."""
+    Jacobian, no decoupling, no E) equals the oracle's Newton result; also with a
+    per-site chi."""
     rng = np.random.default_rng(11)
     nx, ny = 3, 3
     S = nx * ny
     V = rng.uniform(-1, 1, S)
     V[4] += 5.0
     chi, tx, ty, eps0, h = 1.7, 1.0, 0.9, 0.2, 0.05
+    if field:
+        chi = _chi_field(S, 23)
     prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
     u0 = _rand_state(rng, S, 0.5)
     u1_orc, U_orc, _ = orc.step(prob, u0, h, return_stages=True)
@@ -305,6 +316,29 @@ def test_energy_preserved_grid16():
     assert abs(orc.norm2(u) - n0) <= float(PAPER["norm_rel_drift_bound"][0])
 
 
+def test_chi_field_energy_preserved_and_uniform_field_is_scalar():
+    """The m-site model with site-dependent gamma_i is still of the form i u' =
+    grad H, so MB4 keeps H = u^H (K+V) u + (1/2) sum chi_i |u_i|^4 to rounding; a
+    uniform field gives the scalar-chi step bit for bit."""
+    rng = np.random.default_rng(31)
+    nx, ny = 8, 6
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    chi = _chi_field(S, 37)
+    prob = orc.Problem(nx, ny, V, chi, tx=1.1, ty=0.9, eps0=0.3)
+    u = _rand_state(rng, S, 0.4)
+    H0 = orc.energy(prob, u)[0]
+    drift = 0.0
+    for _ in range(30):
+        u = orc.step(prob, u, 0.02)
+        drift = max(drift, abs(orc.energy(prob, u)[0] - H0) / abs(H0))
+    assert drift <= 1e-13, drift
+    u0 = _rand_state(rng, S, 0.4)
+    a = orc.step(orc.Problem(nx, ny, V, 1.3, tx=1.1, ty=0.9, eps0=0.3), u0, 0.02)
+    b = orc.step(orc.Problem(nx, ny, V, np.full(S, 1.3), tx=1.1, ty=0.9, eps0=0.3), u0, 0.02)
+    assert np.array_equal(a, b)
+
+
 def test_time_reversal():
     """MB4 is symmetric: a step of -h undoes a step of h."""
     rng = np.random.default_rng(1)
@@ -372,15 +406,18 @@ def test_inputs_shapes_and_normalisation():
     assert w2.defects() == round(0.01 * 512 * 512)
 
 
-def test_jacobian_matches_finite_difference():
+@pytest.mark.parametrize("field", [False, True])
+def test_jacobian_matches_finite_difference(field):
     """J of eq. (JL) + eq. (JR) (real form, gamma = -chi) against central differences
     of the brute-force f.  J only steers the simplified Newton iteration, so a
-    wrong J would not move the root; this pins it directly."""
+    wrong J would not move the root; this pins it directly (also per-site chi)."""
     rng = np.random.default_rng(4)
     nx, ny = 4, 3
     S = nx * ny
     V = rng.uniform(-1, 1, S)
     chi, tx, ty, eps0 = 1.4, 1.2, 0.7, 0.3
+    if field:
+        chi = _chi_field(S, 29)
     prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
     u0 = _rand_state(rng, S)
     J = orc.jacobian_real(prob, u0).toarray()
