@@ -189,6 +189,25 @@ class Problem:
         self.K = kinetic_matrix(self.nx, self.ny, self.tx, self.ty, self.eps0)
         self.A = sp.csr_matrix(self.K + sp.diags(self.V))   # A = K + V (eq. JL)
 
+    @classmethod
+    def general(cls, K, V, chi):
+        """A site model with a given kinetic matrix K (S x S, real symmetric, sparse or
+        dense) instead of the grid stencil: the appendix's m-site model, in which K_kj
+        is the transfer between neighbouring sites.  nx = S, ny = 1 label the sites."""
+        K = sp.csr_matrix(K, dtype=np.float64)
+        S = K.shape[0]
+        if K.shape != (S, S) or abs(K - K.T).max() > 0:
+            raise ValueError("K must be square and symmetric")
+        self = cls.__new__(cls)
+        self.nx, self.ny, self.S = S, 1, S
+        self.tx = self.ty = float("nan")
+        self.eps0 = float("nan")
+        self.V = np.asarray(V, dtype=np.float64).reshape(S).copy()
+        self.chi = float(chi) if np.ndim(chi) == 0 else np.asarray(chi, dtype=np.float64).reshape(S).copy()
+        self.K = K
+        self.A = sp.csr_matrix(self.K + sp.diags(self.V))
+        return self
+
     def f(self, u):
         """f(u) = f_K + f_I + f_E = -i[(K+V)u + chi |u|^2 u]  (eq. fdivide..fEu, gamma = -chi)."""
         return -1j * (self.A @ u + self.chi * (np.abs(u) ** 2) * u)

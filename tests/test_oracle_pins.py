@@ -339,6 +339,62 @@ def test_chi_field_energy_preserved_and_uniform_field_is_scalar():
     assert np.array_equal(a, b)
 
 
+def _random_graph_K(S, deg, seed, onsite=0.3):
+    """A random real symmetric site model: each site linked to up to deg others."""
+    rng = np.random.default_rng(seed)
+    K = np.zeros((S, S))
+    for k in range(S):
+        for j in rng.choice(S, size=deg // 2, replace=False):
+            if j != k:
+                w = rng.uniform(-1.5, 1.5)
+                K[k, j] = K[j, k] = w
+    return K + onsite * np.eye(S)
+
+
+def _brute_phi_dense(K, V, chi, u0, U, h, nq=20):
+    """Brute-force residual (20-point Gauss-Legendre of the stage integrals) for a dense K."""
+    nodes = np.array([0.0] + [float(x) for x in C_PAPER])
+    zq, wq = np.polynomial.legendre.leggauss(nq)
+    zq, wq = 0.5 * (zq + 1.0), 0.5 * wq
+    lag = scipy.interpolate.BarycentricInterpolator(nodes, np.eye(4))
+    X = np.vstack([u0[None, :], U])
+    acc = np.zeros_like(U)
+    for z, w in zip(zq, wq):
+        lz = lag(z)
+        Uz = sum(lz[j] * X[j] for j in range(4))
+        fz = -1j * (K @ Uz + V * Uz + chi * np.abs(Uz) ** 2 * Uz)
+        for i in range(3):
+            acc[i] += w * _A_float(ALPHA_PAPER, float(C_PAPER[i]), z) * fz
+    return U - u0[None, :] - h * acc
+
+
+def test_general_site_model():
+    """A given kinetic matrix (the appendix's m-site model): the residual equals the
+    brute-force quadrature with a dense K, energy is conserved, and the 5-point
+    stencil handed over as a matrix reproduces the grid problem bit for bit."""
+    rng = np.random.default_rng(43)
+    S = 30
+    K = _random_graph_K(S, 6, 44)
+    V = rng.uniform(-1, 1, S)
+    chi = _chi_field(S, 45)
+    prob = orc.Problem.general(K, V, chi)
+    u0 = _rand_state(rng, S, 0.5)
+    U = u0[None, :] + 0.1 * np.vstack([_rand_state(rng, S) for _ in range(3)])
+    got = orc.residual(prob, u0, U, 0.03)
+    want = _brute_phi_dense(K, V, chi, u0, U, 0.03)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(U))
+    u, H0, drift = u0, orc.energy(prob, u0)[0], 0.0
+    for _ in range(30):
+        u = orc.step(prob, u, 0.02)
+        drift = max(drift, abs(orc.energy(prob, u)[0] - H0) / abs(H0))
+    assert drift <= 1e-13, drift
+    nx, ny = 5, 4
+    grid = orc.Problem(nx, ny, V[:20], 1.1, tx=1.2, ty=0.8, eps0=0.3)
+    gen = orc.Problem.general(grid.K, V[:20], 1.1)
+    w0 = _rand_state(rng, nx * ny, 0.5)
+    assert np.array_equal(orc.step(grid, w0, 0.02), orc.step(gen, w0, 0.02))
+
+
 def test_time_reversal():
     """MB4 is symmetric: a step of -h undoes a step of h."""
     rng = np.random.default_rng(1)
