@@ -140,6 +140,11 @@ typedef struct {
                             the paper's Laplacian (h ||K|| ~ 10 on its 70 x 70 grid, Sec. 3),
                             where the plain basis cannot reduce the residual in s vectors.
                             The root of each step is the same.                                */
+    int    site_chi;     /* 0 (default): chi is one value per context (per instance in a batch).
+                            1: chi is a per-site field (the m-site model of the paper's
+                            appendix, U_I = -(1/2) sum_i gamma_i n_i^2), set with
+                            mb4_set_chi_field / mb4_batch_set_chi_field and initialised to
+                            the scalar chi; costs S more doubles per instance.                */
 } mb4_options;
 
 #define MB4_MAX_PRECOND_SIDE 1024
@@ -168,6 +173,27 @@ int mb4_default_options(mb4_options* opt);
  * The state starts at zero; set it with mb4_set_state.  opt may be NULL. */
 int mb4_create(const mb4_grid* grid, const mb4_potential* pot, const mb4_nonlinearity* nl,
                double h, const mb4_options* opt, mb4_ctx** out);
+
+/* A general kinetic matrix in place of the grid stencil: the m-site model of the
+ * paper's appendix, where K_kj is the transfer between neighbouring sites (molecules).
+ * K = onsite * I + T with T real symmetric, at most max_degree nonzeros per row, given
+ * row-major: nbr[k * max_degree + e] is a neighbour of site k (or -1 for an unused slot),
+ * t[k * max_degree + e] the matching K_kj.  Both arrays are host memory, copied. */
+#define MB4_MAX_DEGREE 16
+typedef struct {
+    int S;                /* sites, >= 1                                              */
+    int max_degree;       /* 1..MB4_MAX_DEGREE                                        */
+    const int* nbr;       /* S * max_degree, values in -1..S-1, no self links          */
+    const double* t;      /* S * max_degree, finite; t(k,j) = t(j,k) (symmetric)       */
+    double onsite;        /* diagonal of K (V adds to it)                             */
+} mb4_sparse_kinetic;
+
+/* mb4_create for a general kinetic matrix (one instance).  Rejects a non-symmetric T,
+ * out-of-range or self-linked neighbours, and precondition = 1 (the spectral
+ * preconditioner needs the grid).  The FP32 path builds its Krylov basis one level per
+ * launch (no matrix-powers tiles).  Every other entry point of a context applies. */
+int mb4_create_sparse(const mb4_sparse_kinetic* K, const mb4_potential* pot, const mb4_nonlinearity* nl,
+                      double h, const mb4_options* opt, mb4_ctx** out);
 
 void mb4_destroy(mb4_ctx* ctx);
 
@@ -214,6 +240,12 @@ int mb4_wait(mb4_ctx* ctx, mb4_stats* stats);
  * for bit).  Adds to ms[MB4_K_COUNT] the summed device time of each kernel
  * class and to launches[MB4_K_COUNT] its launch count (both nullable). */
 int mb4_step_profiled(mb4_ctx* ctx, int nsteps, mb4_stats* stats, double* ms, long long* launches);
+
+/* Per-site nonlinearity chi_k = -gamma_k (S doubles, finite), for a context created
+ * with site_chi = 1 (else MB4_ERR_INVALID_ARG).  The energy becomes
+ * H = psi^H (K+V) psi + (1/2) sum_k chi_k |psi_k|^4 and the step its Hamiltonian flow;
+ * the history of newton_start is dropped.  Synchronises. */
+int mb4_set_chi_field(mb4_ctx* ctx, const double* chi, int on_device);
 
 /* Launch shape of the context's per-site kernels, shape8[8]: threads per block of
  * {set-up and accept, residual, Krylov basis (FP64 stencil), update}, then blocks per
@@ -297,6 +329,9 @@ int mb4_batch_observables(const mb4_batch* b, double* out);
 
 /* Clear the error of every instance (the state is the last accepted one). */
 int mb4_batch_clear_errors(mb4_batch* b);
+
+/* As mb4_set_chi_field, for one instance of a batch (instance >= 0). */
+int mb4_batch_set_chi_field(mb4_batch* b, int instance, const double* chi, int on_device);
 
 /* As mb4_get_launch_shape, for a batch. */
 int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);

@@ -40,6 +40,9 @@ struct mb4_batch {
   // device step counters at the last wait: stats report the steps since then
   std::vector<long long> base_steps, base_newton;
   std::vector<double> ebar;       // per instance: mean of onsite + V (spectral preconditioner)
+  int* ell_nbr = nullptr;         // general kinetic matrix (mb4_create_sparse), device
+  double* ell_w = nullptr;
+  void* ell_wt = nullptr;
 };
 
 struct mb4_ctx : mb4_batch {};
@@ -95,6 +98,7 @@ int validate_options(const mb4_options* in, mb4_options* o) {
   if (o->site_threads != 0 && o->site_threads != 64 && o->site_threads != 128 && o->site_threads != 256)
     return MB4_ERR_INVALID_ARG;
   if (o->precondition != 0 && o->precondition != 1) return MB4_ERR_INVALID_ARG;
+  if (o->site_chi != 0 && o->site_chi != 1) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -152,6 +156,7 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.s = o.krylov_s;
   p.pdl = o.overlap_launches;
   p.precond = o.precondition;
+  p.chi_field = o.site_chi;
   p.bs_site = p.bs_residual = p.bs_matvec = p.bs_update = o.site_threads > 0 ? o.site_threads : 128;
   p.pred_order = o.newton_start;
   p.pred_adaptive = o.newton_start_adaptive;
@@ -344,6 +349,7 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
   if (o.precondition)
     t += round256((size_t)(o.krylov_s + 1) * 3 * BS * 2 * tk) + 2 * round256((size_t)3 * BS * 2 * tk) +
          round256((size_t)nx * 2 * tk) + round256((size_t)ny * 2 * tk);
+  if (o.site_chi) t += round256(BS * 8);
   return (long long)t;
 }
 
@@ -457,8 +463,15 @@ double mean_of(const double* x, size_t n) {
 }
 
 // Create a batch of B instances; V is host B*S doubles, chi host B doubles.
+// A general kinetic matrix for make_batch: its off-diagonal in slot-major ELL form.
+struct EllHost {
+  int deg = 0;
+  std::vector<int> nbr;      // deg * S, nbr[e * S + k] = j or -1
+  std::vector<double> w;     // deg * S, K_kj
+};
+
 int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const double* chi, double h,
-               const mb4_options& o) {
+               const mb4_options& o, const EllHost* ell = nullptr) {
   MB4_CHECK(compute_constants(o.alpha1, o.c1, o.c2, &c->k));
   c->precision = o.precision;
   c->use_graph = o.use_graph ? 1 : 0;
@@ -476,11 +489,16 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
     if (!std::isfinite(chi[b])) return MB4_ERR_INVALID_ARG;
   fill_params(c, grid, h, o);
   StepParams& p = c->p;
+  if (ell) {
+    if (B != 1 || p.precond) return MB4_ERR_INVALID_ARG;   // one instance; no spectral preconditioner
+    p.ell = 1;
+    p.ell_deg = ell->deg;
+  }
   p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B)
                                               : gram_blocks_per_system<double>(p.s, B);
   if (p.gram_blocks < 1) return MB4_ERR_CUDA;
   if (p.precond && (grid->nx > MB4_MAX_PRECOND_SIDE || grid->ny > MB4_MAX_PRECOND_SIDE)) return MB4_ERR_INVALID_ARG;
-  p.use_powers = (o.precision == MB4_MIXED && !p.precond) ? 1 : 0;
+  p.use_powers = (o.precision == MB4_MIXED && !p.precond && !p.ell) ? 1 : 0;
   if (p.use_powers) MB4_CHECK(prepare_powers());
 
   DevBuffers& d = c->b;
@@ -510,7 +528,47 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(dalloc(c, (void**)&d.is, (size_t)B * sizeof(InstStatus)));
   MB4_CHECK(dalloc(c, (void**)&d.bc, sizeof(BatchCtl)));
   std::vector<InstConst> ic(B);
-  for (int b = 0; b < B; ++b) fill_inst_const(c, chi[b], instance_theta(c->p, V + (size_t)b * S, S), &ic[b]);
+  // with a chi field the per-instance constants carry chi = 1 and the kernels scale by chi_k
+  for (int b = 0; b < B; ++b) {
+    double theta = instance_theta(c->p, V + (size_t)b * S, S);
+    if (ell) {                                  // Gershgorin: max_k |d_k| + sum_j |K_kj|
+      theta = 0.0;
+      for (size_t k = 0; k < S; ++k) {
+        double r = std::fabs(D[k]);
+        for (int e = 0; e < ell->deg; ++e)
+          if (ell->nbr[(size_t)e * S + k] >= 0) r += std::fabs(ell->w[(size_t)e * S + k]);
+        theta = std::fmax(theta, r);
+      }
+      if (!(theta > 0.0)) theta = 1.0;
+    }
+    fill_inst_const(c, p.chi_field ? 1.0 : chi[b], theta, &ic[b]);
+  }
+  if (ell) {                                    // off-diagonal in FP64 and, scaled by 1/theta, in TK
+    const size_t n = (size_t)ell->deg * S;
+    MB4_CHECK(dalloc(c, (void**)&c->ell_nbr, n * sizeof(int)));
+    MB4_CHECK(dalloc(c, (void**)&c->ell_w, n * sizeof(double)));
+    MB4_CHECK(dalloc(c, &c->ell_wt, n * tk));
+    MB4_TRY(cudaMemcpy(c->ell_nbr, ell->nbr.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    MB4_TRY(cudaMemcpy(c->ell_w, ell->w.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    if (tk == sizeof(float)) {
+      std::vector<float> wt(n);
+      for (size_t q = 0; q < n; ++q) wt[q] = (float)(ell->w[q] * ic[0].inv_theta);
+      MB4_TRY(cudaMemcpy(c->ell_wt, wt.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<double> wt(n);
+      for (size_t q = 0; q < n; ++q) wt[q] = ell->w[q] * ic[0].inv_theta;
+      MB4_TRY(cudaMemcpy(c->ell_wt, wt.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    p.ell_nbr = c->ell_nbr;
+    p.ell_w = c->ell_w;
+    p.ell_wt = c->ell_wt;
+  }
+  if (p.chi_field) {
+    MB4_CHECK(dalloc(c, (void**)&d.chi, BS * sizeof(double)));
+    std::vector<double> field(BS);
+    for (int b = 0; b < B; ++b) std::fill(field.begin() + (size_t)b * S, field.begin() + (size_t)(b + 1) * S, chi[b]);
+    MB4_TRY(cudaMemcpy(d.chi, field.data(), BS * sizeof(double), cudaMemcpyHostToDevice));
+  }
   c->host_status.assign(B, InstStatus{});
   for (int b = 0; b < B; ++b) c->host_status[b].enabled = 1;
   c->base_steps.assign(B, 0);
@@ -719,7 +777,11 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
     D[k] = c->p.eps0 + V[k];
   }
   InstConst ic;
-  fill_inst_const(c, chi, instance_theta(c->p, V.data(), S), &ic);
+  fill_inst_const(c, c->p.chi_field ? 1.0 : chi, instance_theta(c->p, V.data(), S), &ic);
+  if (c->p.chi_field) {
+    const std::vector<double> field(S, chi);
+    MB4_TRY(cudaMemcpy(c->b.chi + (size_t)instance * S, field.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+  }
   MB4_TRY(cudaMemcpyAsync(c->b.V + (size_t)instance * S, V.data(), S * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream));
   MB4_TRY(cudaMemcpyAsync(c->b.d + (size_t)instance * S, D.data(), S * sizeof(double), cudaMemcpyHostToDevice,
@@ -777,6 +839,30 @@ int mb4_batch_clear_errors(mb4_batch* c) {
   return clear_errors(c);
 }
 
+int mb4_batch_set_chi_field(mb4_batch* c, int instance, const double* chi, int on_device) {
+  MB4_CHECK(check_instance(c, instance, false));
+  if (!chi || !c->p.chi_field) return MB4_ERR_INVALID_ARG;
+  const size_t S = (size_t)c->p.S;
+  std::vector<double> h(S);
+  if (on_device) {
+    MB4_TRY(cudaMemcpy(h.data(), chi, S * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h.data(), chi, S * sizeof(double));
+  }
+  for (size_t k = 0; k < S; ++k)
+    if (!std::isfinite(h[k])) return MB4_ERR_INVALID_ARG;
+  MB4_TRY(cudaMemcpyAsync(c->b.chi + (size_t)instance * S, h.data(), S * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  launch_forget_range(c->p, c->b, instance, 1, c->stream);   // another flow: the increments no longer fit
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaStreamSynchronize(c->stream));
+  return MB4_OK;
+}
+
+int mb4_set_chi_field(mb4_ctx* c, const double* chi, int on_device) {
+  return mb4_batch_set_chi_field(c, 0, chi, on_device);
+}
+
 int mb4_batch_get_launch_shape(const mb4_batch* c, int* shape8) {
   if (!c || !shape8) return MB4_ERR_INVALID_ARG;
   const int bs[4] = {c->p.bs_site, c->p.bs_residual, c->p.bs_matvec, c->p.bs_update};
@@ -808,6 +894,53 @@ int mb4_create(const mb4_grid* grid, const mb4_potential* pot, const mb4_nonline
   if (!c) return MB4_ERR_OUT_OF_MEMORY;
   const double chi = nl->chi;
   int rc = make_batch(c, grid, 1, V.data(), &chi, h, o);
+  if (rc != MB4_OK) {
+    mb4_batch_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MB4_OK;
+}
+
+int mb4_create_sparse(const mb4_sparse_kinetic* K, const mb4_potential* pot, const mb4_nonlinearity* nl, double h,
+                      const mb4_options* opt_in, mb4_ctx** out) {
+  if (!out) return MB4_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!K || K->S < 1 || K->S > (1 << 30) || K->max_degree < 1 || K->max_degree > MB4_MAX_DEGREE || !K->nbr ||
+      !K->t || !std::isfinite(K->onsite))
+    return MB4_ERR_INVALID_ARG;
+  if (!nl || !std::isfinite(nl->chi) || !std::isfinite(h) || h == 0.0) return MB4_ERR_INVALID_ARG;
+  mb4_options o;
+  MB4_CHECK(validate_options(opt_in, &o));
+  if (o.precondition) return MB4_ERR_INVALID_ARG;
+  const size_t S = (size_t)K->S;
+  const int deg = K->max_degree;
+  // row-major input -> slot-major ELL; entries in range, no self links, finite, symmetric
+  EllHost ell;
+  ell.deg = deg;
+  ell.nbr.assign((size_t)deg * S, -1);
+  ell.w.assign((size_t)deg * S, 0.0);
+  for (size_t k = 0; k < S; ++k)
+    for (int e = 0; e < deg; ++e) {
+      const int j = K->nbr[k * deg + e];
+      if (j < -1 || j >= K->S || j == (int)k) return MB4_ERR_INVALID_ARG;
+      if (j < 0) continue;
+      const double w = K->t[k * deg + e];
+      if (!std::isfinite(w)) return MB4_ERR_INVALID_ARG;
+      int found = 0;
+      for (int f = 0; f < deg; ++f)
+        if (K->nbr[(size_t)j * deg + f] == (int)k && K->t[(size_t)j * deg + f] == w) found = 1;
+      if (!found) return MB4_ERR_INVALID_ARG;   // K must be symmetric
+      ell.nbr[(size_t)e * S + k] = j;
+      ell.w[(size_t)e * S + k] = w;
+    }
+  std::vector<double> V;
+  MB4_CHECK(potential_to_host(pot, S, &V));
+  mb4_ctx* c = new (std::nothrow) mb4_ctx();
+  if (!c) return MB4_ERR_OUT_OF_MEMORY;
+  const mb4_grid g = {K->S, 1, 0.0, 0.0, K->onsite};
+  const double chi = nl->chi;
+  int rc = make_batch(c, &g, 1, V.data(), &chi, h, o, &ell);
   if (rc != MB4_OK) {
     mb4_batch_destroy(c);
     return rc;

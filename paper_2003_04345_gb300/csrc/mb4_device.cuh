@@ -128,6 +128,27 @@ template <> __device__ __forceinline__ float to_float<double>(double x) { return
 // not depend on it: each site is computed alone and the only reductions are maxima.
 constexpr int kSiteThreadsMax = 256;
 
+// sum_j K_kj x_j over the off-diagonal of a general kinetic matrix in slot-major ELL
+// form (nbr[e * S + k] = j or -1, w[e * S + k] = K_kj, e < deg), both parts of a
+// complex plane x.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 ell_offdiag(const int* __restrict__ nbr, const T* __restrict__ w, int deg, int S, int k,
+                                          const T2* __restrict__ x) {
+  T2 s;
+  s.x = 0;
+  s.y = 0;
+  for (int e = 0; e < deg; ++e) {
+    const int j = nbr[(size_t)e * S + k];
+    if (j >= 0) {
+      const T wv = w[(size_t)e * S + k];
+      const T2 xv = x[j];
+      s.x += wv * xv.x;
+      s.y += wv * xv.y;
+    }
+  }
+  return s;
+}
+
 // Offsets of instance b's data.
 __device__ __forceinline__ size_t plane(int b, int S) { return (size_t)b * S; }
 __device__ __forceinline__ size_t stage(int b, int m, int S) { return ((size_t)b * 3 + m) * S; }

@@ -41,6 +41,14 @@ struct StepParams {
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   int pdl;                 // programmatic dependent launch inside the Newton loop
   int precond;             // spectral preconditioning of the shifted solves (mb4_precond.cu)
+  int chi_field;           // chi per site (DevBuffers::chi); InstConst then holds chi = 1
+  // general kinetic matrix (mb4_create_sparse) instead of the grid stencil: K = onsite I + T,
+  // T's off-diagonal in slot-major ELL form, nbr[e * S + k] = j or -1, w = K_kj (FP64) and
+  // wt = K_kj / theta in the Krylov precision, e < ell_deg
+  int ell, ell_deg;
+  const int* ell_nbr;
+  const double* ell_w;
+  const void* ell_wt;
   int bs_site, bs_residual, bs_matvec, bs_update;   // threads per block of the per-site kernels
                                                     // (bs_site: k_setup, k_accept)
   int pred_order;          // Newton start: 0 = e3 (x) u0; m = extrapolate the last m increments
@@ -125,6 +133,7 @@ struct DevBuffers {
   double* obs_part;  // observables partial sums
   double* obs_out;   // B*6
   int* changed;      // B flags: set_state changed the instance's state
+  double* chi;       // per-site chi, B*S (chi_field only)
   // spectral preconditioner (precond only): z_a = P v_a (layout of v), a DFT work plane
   // triple per instance, twiddles along x and y, per-mode inverse multipliers B*3*S (TK2)
   void* pz;
@@ -158,6 +167,8 @@ void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 // instance whose state changes (any bit) forgets its Newton-start history.
 void launch_set_state(const StepParams& p, const DevBuffers& b, const double* re, const double* im, int first,
                       int ninst, cudaStream_t st);
+// Drop the Newton-start history of instances first .. first + ninst - 1.
+void launch_forget_range(const StepParams& p, const DevBuffers& b, int first, int ninst, cudaStream_t st);
 int obs_blocks_per_instance(int B);
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 // Y_j += sign * x on three complex planes of S sites.

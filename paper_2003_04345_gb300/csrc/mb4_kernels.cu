@@ -39,11 +39,12 @@ namespace mb4 {
 // H0 the newest), whose residual the first k_residual then evaluates.
 // Grid: (sites / bs_site, B).
 // ---------------------------------------------------------------------------
-template <typename TK>
+template <typename TK, bool ELL>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
                                                JCoef<TK>* __restrict__ jc, typename Vec2<TK>::type* __restrict__ v,
                                                const double2* __restrict__ dUh, double2* __restrict__ dUb,
+                                               const double* __restrict__ p_chi,
                                                const InstConst* __restrict__ ic, InstStatus* is) {
   const int b = blockIdx.y;
   if (!is[b].active) return;
@@ -53,19 +54,27 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const d
   const InstConst& C = ic[b];
   float m = 0.f;
   if (k < S) {
-    Nbr n = neighbours(k, p.nx, p.ny, S);
     const double2* ub = u + plane(b, S);
     double2 c = ub[k];
-    double2 a = ub[n.xm], bb = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
     double d = D[plane(b, S) + k];
     double2 s0;
-    s0.x = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
-    s0.y = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
+    if constexpr (ELL) {
+      const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, ub);
+      s0.x = fma(d, c.x, o.x);
+      s0.y = fma(d, c.y, o.y);
+    } else {
+      Nbr n = neighbours(k, p.nx, p.ny, S);
+      double2 a = ub[n.xm], bb = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
+      s0.x = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
+      s0.y = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
+    }
     S0[plane(b, S) + k] = s0;
     const TK pk = from_double<TK>(c.x), qk = from_double<TK>(c.y);
     const TK pp = pk * pk, qq = qk * qk, nn = pp + qq;
     const TK dt = from_double<TK>(d) * kval<TK>(C.inv_theta, C.f_inv_theta);
-    const TK ct = kval<TK>(C.chi_theta, C.f_chi_theta);
+    const double chik = p.chi_field ? p_chi[plane(b, S) + k] : 1.0;   // per-site chi (InstConst chi = 1)
+    TK ct = kval<TK>(C.chi_theta, C.f_chi_theta);
+    if (p.chi_field) ct *= from_double<TK>(chik);
     JCoef<TK> j;
     j.e1 = dt + ct * (pp + (TK)3 * qq);
     j.e2 = dt + ct * ((TK)3 * pp + qq);
@@ -90,7 +99,8 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const d
         dUb[stage(b, i, S) + k] = x;
       }
     } else {
-      const TK cn = kval<TK>(C.chi, C.f_chi) * nn;
+      TK cn = kval<TK>(C.chi, C.f_chi) * nn;
+      if (p.chi_field) cn *= from_double<TK>(chik);
       const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -110,8 +120,12 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const d
 template <typename TK>
 void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   dim3 grid((p.S + p.bs_site - 1) / p.bs_site, p.B);
-  k_setup<TK><<<grid, p.bs_site, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
-                                             b.dU_hist, b.Ubar, b.ic, b.is);
+  if (p.ell)
+    k_setup<TK, true><<<grid, p.bs_site, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
+                                                 b.dU_hist, b.Ubar, b.chi, b.ic, b.is);
+  else
+    k_setup<TK, false><<<grid, p.bs_site, 0, s>>>(p, b.u, b.d, b.S0, (JCoef<TK>*)b.jc, (typename Vec2<TK>::type*)b.v,
+                                                  b.dU_hist, b.Ubar, b.chi, b.ic, b.is);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,13 +137,13 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 // exact for the degree-11 integrand).  (The u0 terms: T^-1 E T = Lambda and
 // T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
 // ---------------------------------------------------------------------------
-template <typename TO>
+template <typename TO, bool CHIF, bool ELL>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
                                                   const double2* __restrict__ dUb,
                                                   typename Vec2<TO>::type* __restrict__ out, long long out_stride,
-                                                  int skip_first, const InstConst* __restrict__ ic,
-                                                  const InstStatus* is) {
+                                                  int skip_first, const double* __restrict__ p_chi,
+                                                  const InstConst* __restrict__ ic, const InstStatus* is) {
   pdl_wait();
   pdl_launch_dependents();
   const int b = blockIdx.y;
@@ -140,10 +154,12 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S) return;
   const InstConst& C = ic[b];
-  Nbr n = neighbours(k, p.nx, p.ny, S);
+  Nbr n;
+  if constexpr (!ELL) n = neighbours(k, p.nx, p.ny, S);
   const double2 u0 = u[plane(b, S) + k];
   const double2 s0 = S0[plane(b, S) + k];
   const double d = D[plane(b, S) + k];
+  const double chik = CHIF ? p_chi[plane(b, S) + k] : 1.0;   // per-site chi (InstConst chi = 1)
   // acc holds (Phibar.y + ... , -(Phibar.x)) in the form b = -Phibar = (acc.y, -acc.x):
   // acc.x = dU.y + hTc S0.x + h lam (K+V)dU.x + ..., acc.y = -dU.x + hTc S0.y + ...,
   // so that the dU term rides on the first FMA instead of a final subtraction.
@@ -151,10 +167,18 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const double2* P = dUb + stage(b, m, S);
-    double2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
+    const double2 c = P[k];
     dU[m] = c;
-    double sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
-    double sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
+    double sx, sy;
+    if constexpr (ELL) {
+      const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, P);
+      sx = fma(d, c.x, o.x);
+      sy = fma(d, c.y, o.y);
+    } else {
+      const double2 a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
+      sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
+      sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
+    }
     acc[m].x = fma(p.hlam[m], sx, fma(p.hTc[m], s0.x, c.y));
     acc[m].y = fma(p.hlam[m], sy, fma(p.hTc[m], s0.y, -c.x));
   }
@@ -165,7 +189,8 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
     Xy = fma(p.LT[q][1], dU[1].y, Xy);
     Xx = fma(p.LT[q][2], dU[2].x, Xx);
     Xy = fma(p.LT[q][2], dU[2].y, Xy);
-    const double nn = fma(Xx, Xx, Xy * Xy);
+    double nn = fma(Xx, Xx, Xy * Xy);
+    if (CHIF) nn *= chik;
     const double gx = nn * Xx, gy = nn * Xy;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -187,14 +212,31 @@ template <typename TK>
 void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, cudaStream_t s) {
   dim3 grid((p.S + p.bs_residual - 1) / p.bs_residual, p.B);
   // b_i of instance b goes to its level 0: level(b, 0, i) = b*(s+1)*3*S + i*S
-  k_residual<TK><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (typename Vec2<TK>::type*)b.v,
-                                      (long long)(p.s + 1) * 3 * p.S, skip_first ? 1 : 0, b.ic, b.is);
+  typedef typename Vec2<TK>::type TK2;
+  const long long os = (long long)(p.s + 1) * 3 * p.S;
+  const int sf = skip_first ? 1 : 0;
+#define MB4_RES(CF, EL) \
+  k_residual<TK, CF, EL><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (TK2*)b.v, os, sf, b.chi, b.ic, b.is)
+  if (p.ell) {
+    if (p.chi_field) MB4_RES(true, true); else MB4_RES(false, true);
+  } else {
+    if (p.chi_field) MB4_RES(true, false); else MB4_RES(false, false);
+  }
+#undef MB4_RES
 }
 
 template <typename TK>
 void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3, cudaStream_t s) {
   dim3 grid((p.S + p.bs_residual - 1) / p.bs_residual, p.B);
-  k_residual<double><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.ic, b.is);
+#define MB4_RES(CF, EL) \
+  k_residual<double, CF, EL><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.chi, \
+                                                            b.ic, b.is)
+  if (p.ell) {
+    if (p.chi_field) MB4_RES(true, true); else MB4_RES(false, true);
+  } else {
+    if (p.chi_field) MB4_RES(true, false); else MB4_RES(false, false);
+  }
+#undef MB4_RES
 }
 
 // ---------------------------------------------------------------------------
@@ -204,7 +246,7 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 // v_{a+1} = (J/theta) v_a is built for the three right-hand sides together, and
 // (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
 // ---------------------------------------------------------------------------
-template <typename TK>
+template <typename TK, bool ELL>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
                                                 const InstConst* __restrict__ ic, const InstStatus* is) {
@@ -216,19 +258,33 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S) return;
-  Nbr n = neighbours(k, p.nx, p.ny, S);
   const JCoef<TK> j = jc[plane(b, S) + k];
-  const TK tx = kval<TK>(ic[b].txt, ic[b].f_txt), ty = kval<TK>(ic[b].tyt, ic[b].f_tyt);
+  if constexpr (ELL) {
+    // (J x)_re = a xp + e1 xq + sum_j (K_kj / theta) xq_j, (J x)_im = -e2 xp - a xq - sum_j (K_kj / theta) xp_j
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const TK2* P = v + level(b, a_in, i, p.s, S);
-    TK2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-    TK2 o;
-    // (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
-    // (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
-    o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
-    o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
-    v[level(b, a_in + 1, i, p.s, S) + k] = o;
+    for (int i = 0; i < 3; ++i) {
+      const TK2* P = v + level(b, a_in, i, p.s, S);
+      const TK2 c = P[k];
+      const TK2 s = ell_offdiag<TK, TK2>(p.ell_nbr, (const TK*)p.ell_wt, p.ell_deg, S, k, P);
+      TK2 o;
+      o.x = j.a * c.x + j.e1 * c.y + s.y;
+      o.y = -j.e2 * c.x - j.a * c.y - s.x;
+      v[level(b, a_in + 1, i, p.s, S) + k] = o;
+    }
+  } else {
+    Nbr n = neighbours(k, p.nx, p.ny, S);
+    const TK tx = kval<TK>(ic[b].txt, ic[b].f_txt), ty = kval<TK>(ic[b].tyt, ic[b].f_tyt);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const TK2* P = v + level(b, a_in, i, p.s, S);
+      TK2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
+      TK2 o;
+      // (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
+      // (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
+      o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
+      o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
+      v[level(b, a_in + 1, i, p.s, S) + k] = o;
+    }
   }
 }
 
@@ -612,8 +668,12 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   }
   dim3 grid((p.S + p.bs_matvec - 1) / p.bs_matvec, p.B);
   for (int a = 0; a < p.s; ++a)
-    launch_k(p.pdl != 0, k_matvec<TK>, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a,
-             (const InstConst*)b.ic, (const InstStatus*)b.is);
+    if (p.ell)
+      launch_k(p.pdl != 0, k_matvec<TK, true>, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v,
+               a, (const InstConst*)b.ic, (const InstStatus*)b.is);
+    else
+      launch_k(p.pdl != 0, k_matvec<TK, false>, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v,
+               a, (const InstConst*)b.ic, (const InstStatus*)b.is);
 }
 
 template <typename TK, int SK>
@@ -963,6 +1023,11 @@ __global__ void k_forget_changed(const int* __restrict__ changed, InstStatus* is
   }
 }
 
+void launch_forget_range(const StepParams& p, const DevBuffers& b, int first, int ninst, cudaStream_t s) {
+  cudaMemsetAsync(b.changed + first, 0x01, (size_t)ninst * sizeof(int), s);   // nonzero flags
+  k_forget_changed<<<(ninst + 255) / 256, 256, 0, s>>>(b.changed + first, b.is + first, ninst);
+}
+
 void launch_set_state(const StepParams& p, const DevBuffers& b, const double* re, const double* im, int first,
                       int ninst, cudaStream_t s) {
   const size_t n = (size_t)ninst * p.S;
@@ -1029,8 +1094,9 @@ __device__ __forceinline__ void warp_sum_dd(DD (&x)[8], int lane) {
   }
 }
 
+template <bool ELL>
 __global__ void __launch_bounds__(256) k_observables(StepParams p, const double2* __restrict__ u,
-                                                     const double* __restrict__ Vp,
+                                                     const double* __restrict__ Vp, const double* __restrict__ p_chi,
                                                      const InstConst* __restrict__ ic, double* __restrict__ part) {
   const int inst = blockIdx.y;
   const int S = p.S;
@@ -1041,15 +1107,23 @@ __global__ void __launch_bounds__(256) k_observables(StepParams p, const double2
 #pragma unroll
   for (int o = 0; o < 8; ++o) acc[o].s = acc[o].c = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
-    Nbr n = neighbours(k, p.nx, p.ny, S);
-    double2 c = ub[k], a = ub[n.xm], b = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
-    double Kx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + b.x, p.eps0 * c.x));
-    double Ky = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + b.y, p.eps0 * c.y));
+    const double2 c = ub[k];
+    double Kx, Ky;
+    if constexpr (ELL) {
+      const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, ub);
+      Kx = fma(p.eps0, c.x, o.x);
+      Ky = fma(p.eps0, c.y, o.y);
+    } else {
+      Nbr n = neighbours(k, p.nx, p.ny, S);
+      const double2 a = ub[n.xm], b = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
+      Kx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + b.x, p.eps0 * c.x));
+      Ky = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + b.y, p.eps0 * c.y));
+    }
     double nn = fma(c.x, c.x, c.y * c.y);
     double n4 = nn * nn;
     two_sum_add(acc[0], fma(c.x, Kx, c.y * Ky));
     two_sum_add(acc[1], vb[k] * nn);
-    two_sum_add(acc[2], half_chi * n4);
+    two_sum_add(acc[2], (p.chi_field ? 0.5 * p_chi[plane(inst, S) + k] : half_chi) * n4);
     two_sum_add(acc[3], nn);
     two_sum_add(acc[4], n4);
   }
@@ -1110,7 +1184,8 @@ int obs_blocks_per_instance(int B) {
 
 void launch_observables(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   const int nb = obs_blocks_per_instance(p.B);
-  k_observables<<<dim3(nb, p.B), 256, 0, s>>>(p, b.u, b.V, b.ic, b.obs_part);
+  if (p.ell) k_observables<true><<<dim3(nb, p.B), 256, 0, s>>>(p, b.u, b.V, b.chi, b.ic, b.obs_part);
+  else k_observables<false><<<dim3(nb, p.B), 256, 0, s>>>(p, b.u, b.V, b.chi, b.ic, b.obs_part);
   k_observables_final<<<p.B, 32 * kParts, 0, s>>>(b.obs_part, nb, b.obs_out);
 }
 

@@ -34,13 +34,13 @@ MAX_KRYLOV_S = 10
 KERNEL_CLASSES = ("setup", "residual", "matvec", "gram", "update", "accept")
 
 # Every entry point include/mb4.h declares.
-EXPORTS = ("mb4_default_options", "mb4_create", "mb4_destroy", "mb4_set_state", "mb4_get_state",
+EXPORTS = ("mb4_default_options", "mb4_create", "mb4_create_sparse", "mb4_destroy", "mb4_set_state", "mb4_get_state",
            "mb4_get_stages", "mb4_step", "mb4_step_async", "mb4_wait", "mb4_step_profiled", "mb4_energy",
            "mb4_norm", "mb4_observables", "mb4_residual", "mb4_solve_shifted", "mb4_get_launch_shape",
-           "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
+           "mb4_set_chi_field", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
            "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
            "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
-           "mb4_batch_clear_errors", "mb4_batch_get_launch_shape", "mb4_batch_bytes", "mb4_server_create",
+           "mb4_batch_clear_errors", "mb4_batch_get_launch_shape", "mb4_batch_set_chi_field", "mb4_batch_bytes", "mb4_server_create",
            "mb4_server_destroy", "mb4_server_submit", "mb4_server_run", "mb4_server_result", "mb4_server_clock")
 
 
@@ -57,12 +57,18 @@ class Nonlinearity(C.Structure):
     _fields_ = [("chi", C.c_double)]
 
 
+class SparseKinetic(C.Structure):
+    _fields_ = [("S", C.c_int), ("max_degree", C.c_int), ("nbr", C.c_void_p), ("t", C.c_void_p),
+                ("onsite", C.c_double)]
+
+
 class Options(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("krylov_s", C.c_int),
                 ("precision", C.c_int), ("alpha1", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
                 ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int),
-                ("autotune", C.c_int), ("site_threads", C.c_int), ("precondition", C.c_int)]
+                ("autotune", C.c_int), ("site_threads", C.c_int), ("precondition", C.c_int),
+                ("site_chi", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -109,6 +115,8 @@ def lib():
             raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_2003_04345_gb300.build`")
         L = C.CDLL(LIB_PATH)
         L.mb4_default_options.argtypes = [C.POINTER(Options)]
+        L.mb4_create_sparse.argtypes = [C.POINTER(SparseKinetic), C.POINTER(Potential), C.POINTER(Nonlinearity),
+                                        C.c_double, C.POINTER(Options), C.POINTER(_P)]
         L.mb4_create.argtypes = [C.POINTER(Grid), C.POINTER(Potential), C.POINTER(Nonlinearity), C.c_double,
                                  C.POINTER(Options), C.POINTER(_P)]
         L.mb4_destroy.argtypes = [_P]
@@ -119,6 +127,8 @@ def lib():
         L.mb4_step.argtypes = [_P, C.c_int, C.POINTER(Stats)]
         L.mb4_step_async.argtypes = [_P, C.c_int]
         L.mb4_get_launch_shape.argtypes = [_P, C.POINTER(C.c_int)]
+        L.mb4_set_chi_field.argtypes = [_P, C.c_void_p, C.c_int]
+        L.mb4_batch_set_chi_field.argtypes = [_P, C.c_int, C.c_void_p, C.c_int]
         L.mb4_batch_get_launch_shape.argtypes = [_P, C.POINTER(C.c_int)]
         L.mb4_wait.argtypes = [_P, C.POINTER(Stats)]
         L.mb4_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), _D, C.POINTER(C.c_longlong)]
@@ -227,7 +237,7 @@ class Integrator:
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
         """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
         stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive,
-        autotune, site_threads, precondition)."""
+        autotune, site_threads, precondition, site_chi)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -251,6 +261,32 @@ class Integrator:
         _check(L.mb4_create(C.byref(grid), C.byref(pot), C.byref(Nonlinearity(float(chi))), self.h,
                             C.byref(opt), C.byref(self._ctx)), "mb4_create")
         del keep
+
+    @classmethod
+    def sparse(cls, K, V, chi, h, precision="fp64", **opts):
+        """A context for a general kinetic matrix (mb4_create_sparse): K is S x S, real
+        symmetric (dense or scipy sparse).  Its diagonal is folded into V."""
+        Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K, dtype=np.float64)
+        S = Kd.shape[0]
+        off = Kd - np.diag(np.diag(Kd))
+        deg = max(1, int((off != 0).sum(axis=1).max()))
+        nbr = -np.ones((S, deg), dtype=np.int32)
+        t = np.zeros((S, deg))
+        for k in range(S):
+            js = np.nonzero(off[k])[0]
+            nbr[k, :len(js)] = js
+            t[k, :len(js)] = off[k, js]
+        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(S) + np.diag(Kd))
+        self = cls.__new__(cls)
+        self.nx, self.ny, self.S, self.h = S, 1, S, float(h)
+        self.precision = precision
+        self._ctx = _P()
+        spk = SparseKinetic(S, deg, nbr.ctypes.data, t.ctypes.data, 0.0)
+        _check(lib().mb4_create_sparse(C.byref(spk), C.byref(Potential(Vh.ctypes.data, 0)),
+                                       C.byref(Nonlinearity(float(chi))), self.h,
+                                       C.byref(_options(precision=precision, **opts)), C.byref(self._ctx)),
+               "mb4_create_sparse")
+        return self
 
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:
@@ -297,6 +333,13 @@ class Integrator:
         if check:
             _check(rc, "mb4_step")
         return (st.as_dict(), rc) if not check else st.as_dict()
+
+    def set_chi_field(self, chi):
+        """Per-site chi (S values; the context needs site_chi=True)."""
+        a = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(-1))
+        if a.size != self.S:
+            raise ValueError("chi field must hold nx*ny values")
+        _check(lib().mb4_set_chi_field(self._ctx, a.ctypes.data, 0), "mb4_set_chi_field")
 
     def launch_shape(self):
         """Per-site kernels (set-up/accept, residual, basis, update): threads per block,
@@ -385,7 +428,7 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
              c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True,
              newton_start=None, newton_start_adaptive=None, autotune=None, site_threads=None,
-             precondition=None):
+             precondition=None, site_chi=None):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -408,6 +451,8 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
         opt.site_threads = int(site_threads)
     if precondition is not None:
         opt.precondition = int(precondition)
+    if site_chi is not None:
+        opt.site_chi = 1 if site_chi else 0
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
@@ -502,6 +547,12 @@ class Batch:
 
     def clear_errors(self):
         _check(lib().mb4_batch_clear_errors(self._ctx), "mb4_batch_clear_errors")
+
+    def set_chi_field(self, instance, chi):
+        a = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(-1))
+        if a.size != self.S:
+            raise ValueError("chi field must hold nx*ny values")
+        _check(lib().mb4_batch_set_chi_field(self._ctx, int(instance), a.ctypes.data, 0), "mb4_batch_set_chi_field")
 
     def launch_shape(self):
         out = (C.c_int * 8)()

@@ -353,6 +353,44 @@ def test_nonfinite_state_is_reported(mb4):
         assert np.isnan(after[17]) and np.array_equal(np.delete(after, 17), np.delete(psi, 17))
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_chi_field_matches_oracle(mb4, precision):
+    """Per-site chi (the appendix's m-site model, both signs) through set_chi_field:
+    the trajectory stays on the oracle's, the observables equal the oracle's energy
+    of the GPU state, and the field model's energy is conserved."""
+    nx, ny, h, steps = 24, 20, 0.01, 10
+    rng = np.random.default_rng(41)
+    V = inputs.potential(nx, ny, 1.0, 3, 20.0, 5)
+    chi = rng.uniform(-2.0, 2.0, nx * ny)
+    psi = inputs.wavepacket(nx, ny, 2.5, math.pi / 4, 0.0)
+    prob = orc.Problem(nx, ny, V, chi)
+    u = psi.copy()
+    for _ in range(steps):
+        u = orc.step(prob, u, h)
+    with mb4.Integrator(nx, ny, V, 0.0, h, precision=precision, site_chi=True) as it:
+        it.set_chi_field(chi)
+        it.set_state(psi)
+        H0 = it.energy()[0]
+        assert abs(H0 - orc.energy(prob, psi)[0]) <= 1e-14 * abs(H0)
+        it.step(steps)
+        got = it.get_state()
+        assert _rel(got, u) <= 1e-11, _rel(got, u)
+        H1 = it.energy()[0]
+        assert abs(H1 - orc.energy(prob, got)[0]) <= 1e-14 * abs(H1)
+        assert abs(H1 - H0) <= 1e-13 * abs(H0)
+    with mb4.Integrator(nx, ny, V, 1.0, h) as it:
+        with pytest.raises(mb4.MB4Error):
+            it.set_chi_field(chi)                        # the context has no field
+
+
+def test_uniform_chi_field_equals_scalar_chi(mb4):
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w) as a, mb4.from_workload(w, site_chi=True) as b:
+        a.step(10)
+        b.step(10)                                       # field initialised to the scalar chi
+        assert _rel(b.get_state(), a.get_state()) <= 1e-13
+
+
 def test_invalid_arguments_rejected(mb4):
     for kw in ({"nx": 2, "ny": 8}, {"h": 0.0}, {"krylov_s": 11}, {"precision": 7}, {"site_threads": 96},
                {"newton_start": 4}):
@@ -453,3 +491,65 @@ def test_energy_drift_long_run(mb4, precision):
             it.step(w.steps // 8)
             worst = max(worst, abs(it.energy()[0] - H0) / abs(H0))
     assert worst <= 1e-13, worst
+
+
+def _random_graph(S, deg, seed, onsite=0.3):
+    rng = np.random.default_rng(seed)
+    K = np.zeros((S, S))
+    for k in range(S):
+        for j in rng.choice(S, size=deg // 2, replace=False):
+            if j != k:
+                K[k, j] = K[j, k] = rng.uniform(-1.5, 1.5)
+    return K + onsite * np.eye(S)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_general_kinetic_matrix_matches_oracle(mb4, precision):
+    """A general sparse K (mb4_create_sparse; the appendix's m-site model on a random
+    graph, with a per-site chi): trajectory and energy against the oracle."""
+    S, h, steps = 300, 0.01, 10
+    K = _random_graph(S, 6, 51)
+    rng = np.random.default_rng(52)
+    V = rng.uniform(-1, 1, S)
+    chi = rng.uniform(-2, 2, S)
+    psi = (rng.normal(size=S) + 1j * rng.normal(size=S)) / np.sqrt(2 * S)
+    prob = orc.Problem.general(K, V, chi)
+    u = psi.copy()
+    for _ in range(steps):
+        u = orc.step(prob, u, h)
+    with mb4.Integrator.sparse(K, V, 0.0, h, precision=precision, site_chi=True) as it:
+        it.set_chi_field(chi)
+        it.set_state(psi)
+        H0 = it.energy()[0]
+        assert abs(H0 - orc.energy(prob, psi)[0]) <= 1e-14 * abs(H0)
+        it.step(steps)
+        got = it.get_state()
+        assert _rel(got, u) <= 1e-11, _rel(got, u)
+        assert abs(it.energy()[0] - H0) <= 1e-13 * abs(H0)
+
+
+def test_general_kinetic_matrix_of_the_grid_equals_the_grid(mb4):
+    """The 5-point stencil handed over as a matrix gives the grid context's step."""
+    w = inputs.grid16_fp64()
+    prob = orc.Problem(w.nx, w.ny, w.potential(), w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
+    with mb4.from_workload(w) as a, mb4.Integrator.sparse(prob.K, w.potential(), w.chi, w.h) as b:
+        b.set_state(w.psi0())
+        a.step(10)
+        b.step(10)
+        assert _rel(b.get_state(), a.get_state()) <= 1e-13
+
+
+def test_general_kinetic_matrix_rejects_bad_input(mb4):
+    from paper_2003_04345_gb300.mb4 import C, Nonlinearity, Potential, SparseKinetic, _P, _options, lib
+    S = 4
+    V = np.zeros(S)
+    for nbr, t in (([[1], [0], [3], [2]], [[1.0], [2.0], [1.0], [1.0]]),      # not symmetric
+                   ([[0], [0], [3], [2]], [[1.0], [1.0], [1.0], [1.0]]),      # a self link
+                   ([[5], [0], [3], [2]], [[1.0], [1.0], [1.0], [1.0]])):     # out of range
+        nb = np.ascontiguousarray(np.array(nbr, dtype=np.int32))
+        tt = np.ascontiguousarray(np.array(t, dtype=np.float64))
+        ctx = _P()
+        rc = lib().mb4_create_sparse(C.byref(SparseKinetic(S, 1, nb.ctypes.data, tt.ctypes.data, 0.0)),
+                                     C.byref(Potential(V.ctypes.data, 0)), C.byref(Nonlinearity(1.0)), 0.01,
+                                     C.byref(_options()), C.byref(ctx))
+        assert rc == mb4.MB4_ERR_INVALID_ARG and not ctx.value
