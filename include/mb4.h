@@ -51,9 +51,11 @@ extern "C" {
 #define MB4_ERR_CUDA                 -3  /* any other CUDA runtime error (no GPU, launch failure) */
 #define MB4_ERR_NEWTON_NOT_CONVERGED -4  /* ||r||_inf still above tolerance after newton_max
                                             iterations (Sec. 2.2: decrease h and redo)          */
-#define MB4_ERR_KRYLOV_BREAKDOWN     -5  /* the inner least-squares problem was singular          */
+#define MB4_ERR_KRYLOV_BREAKDOWN     -5  /* reserved: not returned by this build (the least squares
+                                            truncates a numerically dependent Krylov basis)      */
 #define MB4_ERR_NONFINITE            -6  /* NaN or Inf met in a Newton update                     */
-#define MB4_ERR_TIMEOUT              -7  /* a bounded device-side wait ran out                    */
+#define MB4_ERR_TIMEOUT              -7  /* reserved: not returned by this build (no kernel waits
+                                            on a device flag)                                    */
 #define MB4_ERR_ADMISSION_REJECTED   -8  /* a batch slot or memory budget is exhausted            */
 
 /* ---- precision modes --------------------------------------------------- */
@@ -166,7 +168,7 @@ typedef struct {
 int mb4_default_options(mb4_options* opt);
 
 /* Create a context on the current CUDA device: validates the arguments,
- * computes the MB4 constants (E, E_i0, Lambda, T, T^-1 -- Algorithm 1 lines 1-3,
+ * computes the MB4 constants (E, E_i0, Lambda, T, T^-1 -- the set-up of Algorithm 1,
  * Sec. 2.2 -- and a 6-node Gauss-Legendre rule that integrates the degree-11
  * stage integrand of eq. (fIu2) exactly), allocates every device buffer and,
  * with use_graph, builds the step graph.  h may be negative (MB4 is symmetric).

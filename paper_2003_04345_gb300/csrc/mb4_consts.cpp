@@ -1,4 +1,4 @@
-// Host-side MB4 constants (Sec. 2.2, Algorithm 1 lines 1-3), in long double.
+// Host-side MB4 constants (Sec. 2.2; the set-up of Algorithm 1), in long double.
 //
 // * A_{tau,zeta} = [tau, tau^2/2, tau^3/3] M(alpha1) [1, zeta, zeta^2]^T  (eq. Adefinition)
 // * l_j: Lagrange basis on (0, c1, c2, c3)                                   (eq. Lagrange)

@@ -27,7 +27,7 @@ namespace cg = cooperative_groups;
 namespace mb4 {
 
 // ---------------------------------------------------------------------------
-// Step set-up (Algorithm 1 lines 7-9 and the first residual): u0 = u(t); J at u0
+// Step set-up (Algorithm 1, start of a step, and the first residual): u0 = u(t); J at u0
 // as per-site coefficients; (K+V) u0; ||u0||_inf.  At U^0 = e3 (x) u0 every stage
 // polynomial value equals u0, so Phi_i(U^0) = -h c_i f(u0) and the first
 // right-hand side is b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].
@@ -129,7 +129,7 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Residual (Algorithm 1 lines 13-14, eq. Phidefinition, eq. fKu2, eq. fIu2) in
+// Residual (Algorithm 1; eq. Phidefinition, eq. fKu2, eq. fIu2) in
 // the eigenbasis, on the increments dU: b = -Phibar with
 //   Phibar_i = dU_i + i [ h lam_i (K+V) dU_i + h (T^-1 c)_i (K+V) u0
 //                         + sum_q h chi W~_iq |X_q|^2 X_q ],
@@ -240,7 +240,7 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 }
 
 // ---------------------------------------------------------------------------
-// Shifted solves (Algorithm 1 lines 15-17, eq. MB4_5): one s-step GMRES cycle per
+// Shifted solves (Algorithm 1; eq. MB4_5): one s-step GMRES cycle per
 // system.  The Krylov space K_s(I - h lam_i J, b_i) = span{b_i, Jb_i, .., J^{s-1} b_i}
 // is the same monomial space for all three shifts, so the basis
 // v_{a+1} = (J/theta) v_a is built for the three right-hand sides together, and
@@ -760,7 +760,7 @@ __device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaG
   }
 }
 
-// Newton update (Algorithm 1 lines 18-20) and loop test (line 12; failure rule of
+// Newton update (Algorithm 1) and the loop test of its Newton iteration (failure rule of
 // Sec. 2.2): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (from dU^0 = 0 the
 // first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
 // block of each instance runs its test: continue while ||r^l||_inf > rtol ||u0||_inf
@@ -925,7 +925,7 @@ __device__ void choose_next_start(const StepParams& p, InstStatus& I) {
   I.next_predicted = next;
 }
 
-// Algorithm 1 line 22 with c3 = 1: u(t+h) = U_c3 = u0 + sum_n T[2][n] dU_n, for the
+// The end of a step of Algorithm 1 with c3 = 1: u(t+h) = U_c3 = u0 + sum_n T[2][n] dU_n, for the
 // instances that took part in the step and did not fail.  Block 0 of each instance
 // books the step and re-arms the instance for the next one.
 __global__ void __launch_bounds__(kSiteThreadsMax) k_accept(StepParams p, double2* __restrict__ u,

@@ -2,7 +2,7 @@
 //
 // For stiff kinetic terms (the paper's own setup: K = -Laplacian with hx = 2 pi / 70,
 // so h ||K|| ~ 10) the monomial Krylov basis of J cannot resolve the shifted systems
-// (I - h lam_i J) x = b_i (Algorithm 1 lines 15-17) in a few vectors.  The constant-
+// (I - h lam_i J) x = b_i (Algorithm 1, the shifted solves) in a few vectors.  The constant-
 // coefficient part of J is diagonal in Fourier space: with the on-site term replaced
 // by its grid mean e and the cubic term's Jacobian dropped, J_c z = -i (K z + e z),
 // so A_i ~ I + i h lam_i (K + e) has the per-mode multiplier
