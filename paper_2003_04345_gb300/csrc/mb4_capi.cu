@@ -37,6 +37,7 @@ struct mb4_batch {
   double* io = nullptr;           // 6*max(B*S, S) doubles
   std::vector<void*> allocs;
   std::vector<InstStatus> host_status;
+  bool err_seen = false;          // a wait saw an instance error that clear_errors has not cleared
   // device step counters at the last wait: stats report the steps since then
   std::vector<long long> base_steps, base_newton;
   std::vector<double> ebar;       // per instance: mean of onsite + V (spectral preconditioner)
@@ -635,6 +636,7 @@ int wait_batch(mb4_batch* c, mb4_stats* stats, int* status) {
     if (status) status[b] = s.error;
     if (first == MB4_OK && s.error) first = s.error;
   }
+  if (first != MB4_OK) c->err_seen = true;
   return first;
 }
 
@@ -647,6 +649,7 @@ int clear_errors(mb4_batch* c) {
   }
   std::fill(c->base_steps.begin(), c->base_steps.end(), 0LL);
   std::fill(c->base_newton.begin(), c->base_newton.end(), 0LL);
+  c->err_seen = false;
   return write_status(c);
 }
 
@@ -974,7 +977,9 @@ int mb4_get_stages(const mb4_ctx* cc, double* re3, double* im3, int on_device) {
 int mb4_step(mb4_ctx* c, int nsteps, mb4_stats* stats) {
   if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  MB4_CHECK(clear_errors(c));   // every call starts from the last accepted state
+  // every call starts from the last accepted state: clear an error a previous call left
+  // (the status round trip is skipped when there is none to clear)
+  if (c->err_seen) MB4_CHECK(clear_errors(c));
   MB4_CHECK(step_async(c, nsteps));
   return wait_batch(c, stats, nullptr);
 }

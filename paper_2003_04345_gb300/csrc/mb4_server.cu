@@ -311,7 +311,8 @@ int mb4_server_run(mb4_server* s, double until, long long* n_done) {
       if (c->chunk == 0) continue;
       stats.resize(c->slots);
       codes.resize(c->slots);
-      mb4_batch_wait(c->b, stats.data(), codes.data());
+      const int wrc = mb4_batch_wait(c->b, stats.data(), codes.data());
+      if (wrc != MB4_OK && wrc != MB4_ERR_NEWTON_NOT_CONVERGED && wrc != MB4_ERR_NONFINITE) return wrc;   // the call failed
       bool finished = false;
       for (int sl = 0; sl < c->slots; ++sl) {
         const long long id = c->slot_req[sl];
@@ -324,7 +325,8 @@ int mb4_server_run(mb4_server* s, double until, long long* n_done) {
       }
       if (!finished) continue;
       obs.resize((size_t)c->slots * 6);
-      mb4_batch_observables(c->b, obs.data());
+      const int orc = mb4_batch_observables(c->b, obs.data());
+      if (orc != MB4_OK) return orc;
       for (int sl = 0; sl < c->slots; ++sl) {
         const long long id = c->slot_req[sl];
         if (id < 0) continue;
