@@ -354,6 +354,7 @@ def run_ours(args):
         line["grid2048"] = bench_grid2048(args, flush)
         line["served"] = bench_served(args)
         line["served"]["rate_sweep"] = [bench_served(args, n_requests=8, rate=r) for r in (1.0, 4.0)]
+        line["paper_setups"] = bench_paper_setups(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if rank == 0:
@@ -470,6 +471,39 @@ def bench_served(args, n_requests=24, rate=200.0):
             "value": site_steps / makespan, "unit": UNIT, "makespan_s": makespan,
             "site_steps": site_steps, "energy_drift_max": drift,
             "errors": int(sum(1 for r in res if r["status"] != 0)), "setup_s": t0}
+
+
+def bench_paper_setups(args, K=60):
+    """The paper's own setups (Sec. 3), spectrally preconditioned: the 70x70
+    Laplacian run (u0 = 1 + 2 cos x + 2 cos y, gamma = 0.1, h = 0.01; K steps from
+    t = 0, inside the collapse-free part of the run) and the 100x100 delta-potential
+    run (gamma = 0.05, V0 = -50 at the origin).  Time per step, Newton iterations,
+    energy drift."""
+    import numpy as np
+    import torch
+    from paper_2003_04345_gb300 import inputs, mb4
+    out = {}
+    for name, n, gamma, V in (("paper70", 70, 0.1, None), ("paper_delta100", 100, 0.05, -50.0)):
+        tx, ty, e0 = inputs.paper_laplacian_hopping(n, n)
+        pot = np.zeros(n * n) if V is None else inputs.delta_potential(n, n, V)
+        line = {"nx": n, "ny": n, "gamma": gamma, "h": 0.01, "steps": K}
+        for precision in ("fp64", "mixed"):
+            with mb4.Integrator(n, n, pot, -gamma, 0.01, tx=tx, ty=ty, onsite=e0, precision=precision,
+                                precondition=1, newton_rtol=2e-14, stream=torch.cuda.current_stream()) as it:
+                it.set_state(inputs.paper_initial_state(n, n))
+                H0 = it.energy()[0]
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                it.step_async(K)
+                b.record()
+                st = it.wait()
+                torch.cuda.synchronize()
+                H1 = it.energy()[0]
+            line[precision] = {"ms_per_step": a.elapsed_time(b) / K, "newton_per_step": st["newton_iters_total"] / K,
+                               "energy_drift": abs(H1 - H0) / abs(H0)}
+        out[name] = line
+    return out
 
 
 def _oracle_sample(n=64):
