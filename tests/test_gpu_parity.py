@@ -391,6 +391,34 @@ def test_uniform_chi_field_equals_scalar_chi(mb4):
         assert _rel(b.get_state(), a.get_state()) <= 1e-13
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_degenerate_inputs(mb4, precision):
+    """Zero steps leave everything as it was; the zero state is a fixed point (its
+    residual is exactly 0, so one Newton iteration confirms it); a single-site-wide
+    ragged grid and a negative h run like any other."""
+    w = inputs.grid16_fp64()
+    with mb4.from_workload(w, precision=precision) as it:
+        u0 = it.get_state()
+        st = it.step(0)
+        assert st["steps_done"] == 0 and np.array_equal(it.get_state(), u0)
+        it.set_state(np.zeros(w.S, dtype=np.complex128))
+        st = it.step(3)
+        assert st["steps_done"] == 3 and not np.any(it.get_state())
+        assert it.energy()[0] == 0.0
+    nx, ny = 3, 41                                        # 3 x 41 periodic strip
+    rng = np.random.default_rng(61)
+    V = rng.uniform(-1, 1, nx * ny)
+    psi = rng.normal(size=nx * ny) + 1j * rng.normal(size=nx * ny)
+    prob = orc.Problem(nx, ny, V, 0.8, tx=0.9, ty=1.1, eps0=0.1)
+    u = psi.copy()
+    for _ in range(4):
+        u = orc.step(prob, u, -0.01)
+    with mb4.Integrator(nx, ny, V, 0.8, -0.01, tx=0.9, ty=1.1, onsite=0.1, precision=precision) as it:
+        it.set_state(psi)
+        it.step(4)
+        assert _rel(it.get_state(), u) <= 1e-11
+
+
 def test_invalid_arguments_rejected(mb4):
     for kw in ({"nx": 2, "ny": 8}, {"h": 0.0}, {"krylov_s": 11}, {"precision": 7}, {"site_threads": 96},
                {"newton_start": 4}):
