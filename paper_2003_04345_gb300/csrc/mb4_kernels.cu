@@ -292,7 +292,11 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
 // TX x TY tile from v_0 and the J coefficients loaded once, with an SK-wide
 // periodic halo in shared memory; level a is valid on the tile grown by SK - a,
 // so no block needs another block's result.  Replaces SK stencil launches by
-// one at the price of recomputing the shrinking halo (cheap in FP32).
+// one at the price of recomputing the shrinking halo (cheap in FP32).  Each
+// thread owns fixed positions of the extended tile (columns tx0 + 32 ix, rows
+// ty0 + 8 iy) at every level, so their J coefficients stay in registers and
+// shared memory holds only the two level buffers: 4 blocks per SM at SK = 4,
+// which puts a 512 x 512 grid's 512 tiles in one wave.
 constexpr int kPowTX = 32, kPowTY = 16, kPowThreads = 256;
 
 template <int SK>
@@ -301,7 +305,7 @@ template <int SK>
 __host__ __device__ constexpr int pow_ext_y() { return kPowTY + 2 * SK; }
 template <int SK>
 constexpr size_t pow_smem_bytes() {
-  return (size_t)pow_ext_x<SK>() * pow_ext_y<SK>() * (sizeof(float4) + 2 * 3 * sizeof(float2));
+  return (size_t)pow_ext_x<SK>() * pow_ext_y<SK>() * (2 * 3 * sizeof(float2));
 }
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -318,9 +322,9 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   const int b = blockIdx.y;
   if (!is[b].active) return;
   constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
+  constexpr int NCX = (EX + 31) / 32, NCY = (EY + 7) / 8;      // positions per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* sj = reinterpret_cast<float4*>(smem_raw);
-  float2* buf0 = reinterpret_cast<float2*>(sj + EA);     // [3][EA]
+  float2* buf0 = reinterpret_cast<float2*>(smem_raw);     // [3][EA]
   float2* buf1 = buf0 + 3 * EA;                           // [3][EA]
   const int S = p.S, nx = p.nx, ny = p.ny;
   const int tiles_x = (nx + kPowTX - 1) / kPowTX;
@@ -328,14 +332,20 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   const int x0 = txi * kPowTX - SK, y0 = tyi * kPowTY - SK;
   const float4* jb = jc + plane(b, S);
   const int tx0 = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // 32 x 8 thread layout
-  for (int ly = ty0; ly < EY; ly += kPowThreads / 32) {
-    const int grow = wrap(y0 + ly, ny) * nx;
-    for (int lx = tx0; lx < EX; lx += 32) {
-      const int t = ly * EX + lx;
-      const int g = grow + wrap(x0 + lx, nx);
-      sj[t] = jb[g];
+  float4 jr[NCY][NCX];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) buf0[i * EA + t] = v[level(b, 0, i, SK, S) + g];
+  for (int iy = 0; iy < NCY; ++iy) {
+    const int ly = ty0 + 8 * iy;
+#pragma unroll
+    for (int ix = 0; ix < NCX; ++ix) {
+      const int lx = tx0 + 32 * ix;
+      if (ly < EY && lx < EX) {
+        const int t = ly * EX + lx;
+        const int g = wrap(y0 + ly, ny) * nx + wrap(x0 + lx, nx);
+        jr[iy][ix] = jb[g];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) buf0[i * EA + t] = v[level(b, 0, i, SK, S) + g];
+      }
     }
   }
   __syncthreads();
@@ -344,18 +354,24 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   float2* dst = buf1;
 #pragma unroll 1
   for (int a = 1; a <= SK; ++a) {
-    for (int ly = a + ty0; ly < EY - a; ly += kPowThreads / 32)
-    for (int lx = a + tx0; lx < EX - a; lx += 32) {
-      const int c = ly * EX + lx;
-      const float4 j = sj[c];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float2* P = src + i * EA;
-        const float2 cc = P[c], xa = P[c - 1], xb = P[c + 1], ya = P[c - EX], yb = P[c + EX];
-        float2 o;
-        o.x = j.z * cc.x + j.x * cc.y - tx * (xa.y + xb.y) - ty * (ya.y + yb.y);
-        o.y = -j.y * cc.x - j.z * cc.y + tx * (xa.x + xb.x) + ty * (ya.x + yb.x);
-        dst[i * EA + c] = o;
+    for (int iy = 0; iy < NCY; ++iy) {
+      const int ly = ty0 + 8 * iy;
+#pragma unroll
+      for (int ix = 0; ix < NCX; ++ix) {
+        const int lx = tx0 + 32 * ix;
+        if (ly < a || ly >= EY - a || lx < a || lx >= EX - a) continue;   // level a lives on the tile grown by SK - a
+        const int c = ly * EX + lx;
+        const float4 j = jr[iy][ix];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float2* P = src + i * EA;
+          const float2 cc = P[c], xa = P[c - 1], xb = P[c + 1], ya = P[c - EX], yb = P[c + EX];
+          float2 o;
+          o.x = j.z * cc.x + j.x * cc.y - tx * (xa.y + xb.y) - ty * (ya.y + yb.y);
+          o.y = -j.y * cc.x - j.z * cc.y + tx * (xa.x + xb.x) + ty * (ya.x + yb.x);
+          dst[i * EA + c] = o;
+        }
       }
     }
     __syncthreads();
