@@ -305,7 +305,10 @@ int mb4_batch_set_state(mb4_batch* b, int instance, const double* re, const doub
 int mb4_batch_get_state(const mb4_batch* b, int instance, double* re, double* im, int on_device);
 
 /* Reuse one slot: new potential (S doubles), chi and state; clears the
- * instance's error and counters and enables it. */
+ * instance's error and counters and enables it.  MB4_ERR_INVALID_ARG for a
+ * non-finite input and, in an FP64 batch without preconditioning on a grid with
+ * tx != 0 (whose Krylov basis is scaled by tx), for a potential whose Gershgorin
+ * bound max|onsite + V| + 2|tx| + 2|ty| exceeds 4096 |tx|. */
 int mb4_batch_load(mb4_batch* b, int instance, const double* v, double chi, const double* re, const double* im,
                    int on_device);
 

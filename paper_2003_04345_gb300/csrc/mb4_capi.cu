@@ -121,6 +121,24 @@ double instance_theta(const StepParams& p, const double* V, size_t S) {
   return (theta > 0.0) ? theta : 1.0;
 }
 
+// D / tx for the residual's factored stencil (kin_unit); false if a ratio overflows.
+bool fill_dtx(const StepParams& p, const double* D, size_t n, std::vector<double>* out) {
+  out->resize(n);
+  for (size_t k = 0; k < n; ++k) {
+    (*out)[k] = D[k] / p.tx;
+    if (!std::isfinite((*out)[k])) return false;
+  }
+  return true;
+}
+
+// The basis scale of an instance: tx with mv_unit (refused, -1, when the Gershgorin
+// bound exceeds kUnitGrowthMax |tx|), else the Gershgorin bound.
+double basis_theta(const StepParams& p, const double* V, size_t S) {
+  const double g = instance_theta(p, V, S);
+  if (!p.mv_unit) return g;
+  return (g <= kUnitGrowthMax * std::fabs(p.tx)) ? p.tx : -1.0;
+}
+
 void fill_inst_const(const mb4_batch* c, double chi, double theta, InstConst* out) {
   const Constants& K = c->k;
   std::memset(out, 0, sizeof(*out));
@@ -170,8 +188,10 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.ty = grid->ty;
   p.eps0 = grid->onsite;
   p.h = h;
+  p.rty = (grid->tx != 0.0) ? grid->ty / grid->tx : 0.0;
   for (int i = 0; i < 3; ++i) {
     p.hlam[i] = h * K.lam[i];
+    p.hltx[i] = p.hlam[i] * grid->tx;
     double tc = 0;
     for (int j = 0; j < 3; ++j) tc += K.Tinv[i][j] * K.c[j];
     p.hTc[i] = h * tc;
@@ -501,6 +521,14 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   if (p.precond && (grid->nx > MB4_MAX_PRECOND_SIDE || grid->ny > MB4_MAX_PRECOND_SIDE)) return MB4_ERR_INVALID_ARG;
   p.use_powers = (o.precision == MB4_MIXED && !p.precond && !p.ell) ? 1 : 0;
   if (p.use_powers) MB4_CHECK(prepare_powers());
+  std::vector<double> Dtx;
+  p.kin_unit = (!p.ell && grid->tx != 0.0 && std::isfinite(p.rty) && fill_dtx(p, D.data(), BS, &Dtx)) ? 1 : 0;
+  p.mv_unit = 0;
+  if (p.kin_unit && o.precision == MB4_FP64 && !p.precond) {
+    p.mv_unit = 1;
+    for (int b = 0; b < B && p.mv_unit; ++b)
+      if (basis_theta(p, V + (size_t)b * S, S) < 0.0) p.mv_unit = 0;
+  }
 
   DevBuffers& d = c->b;
   const size_t tk = c->tk;
@@ -508,6 +536,7 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(dalloc(c, (void**)&d.u, BS * sizeof(double2)));
   MB4_CHECK(dalloc(c, (void**)&d.V, BS * sizeof(double)));
   MB4_CHECK(dalloc(c, (void**)&d.d, BS * sizeof(double)));
+  if (p.kin_unit) MB4_CHECK(dalloc(c, (void**)&d.dtx, BS * sizeof(double)));
   MB4_CHECK(dalloc(c, (void**)&d.S0, BS * sizeof(double2)));
   MB4_CHECK(dalloc(c, (void**)&d.Ubar, 3 * BS * sizeof(double2)));
   if (p.pred_order > 0) MB4_CHECK(dalloc(c, (void**)&d.dU_hist, (size_t)p.pred_order * 3 * BS * sizeof(double2)));
@@ -531,7 +560,7 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   std::vector<InstConst> ic(B);
   // with a chi field the per-instance constants carry chi = 1 and the kernels scale by chi_k
   for (int b = 0; b < B; ++b) {
-    double theta = instance_theta(c->p, V + (size_t)b * S, S);
+    double theta = basis_theta(c->p, V + (size_t)b * S, S);
     if (ell) {                                  // Gershgorin: max_k |d_k| + sum_j |K_kj|
       theta = 0.0;
       for (size_t k = 0; k < S; ++k) {
@@ -579,6 +608,8 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(upload_precond_tables(c));
   MB4_TRY(cudaMemcpyAsync(d.V, V, BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(d.d, D.data(), BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (p.kin_unit)
+    MB4_TRY(cudaMemcpyAsync(d.dtx, Dtx.data(), BS * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(d.ic, ic.data(), B * sizeof(InstConst), cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemsetAsync(d.u, 0, BS * sizeof(double2), c->stream));
   MB4_TRY(cudaMemsetAsync(d.Ubar, 0, 3 * BS * sizeof(double2), c->stream));
@@ -779,8 +810,12 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
     if (!std::isfinite(V[k])) return MB4_ERR_INVALID_ARG;
     D[k] = c->p.eps0 + V[k];
   }
+  std::vector<double> Dtx;
+  if (c->p.kin_unit && !fill_dtx(c->p, D.data(), S, &Dtx)) return MB4_ERR_INVALID_ARG;
+  const double theta = basis_theta(c->p, V.data(), S);
+  if (c->p.mv_unit && theta < 0.0) return MB4_ERR_INVALID_ARG;   // outside the batch's basis scaling
   InstConst ic;
-  fill_inst_const(c, c->p.chi_field ? 1.0 : chi, instance_theta(c->p, V.data(), S), &ic);
+  fill_inst_const(c, c->p.chi_field ? 1.0 : chi, theta, &ic);
   if (c->p.chi_field) {
     const std::vector<double> field(S, chi);
     MB4_TRY(cudaMemcpy(c->b.chi + (size_t)instance * S, field.data(), S * sizeof(double), cudaMemcpyHostToDevice));
@@ -789,6 +824,9 @@ int mb4_batch_load(mb4_batch* c, int instance, const double* v, double chi, cons
                           c->stream));
   MB4_TRY(cudaMemcpyAsync(c->b.d + (size_t)instance * S, D.data(), S * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream));
+  if (c->p.kin_unit)
+    MB4_TRY(cudaMemcpyAsync(c->b.dtx + (size_t)instance * S, Dtx.data(), S * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream));
   MB4_TRY(cudaMemcpyAsync(c->b.ic + instance, &ic, sizeof(ic), cudaMemcpyHostToDevice, c->stream));
   c->ebar[instance] = mean_of(D.data(), S);
   MB4_CHECK(upload_precond_tables(c));

@@ -16,6 +16,7 @@ constexpr int kGramCap = 152;      // Gram blocks per (instance, system), at mos
 constexpr int kGramCluster = 8;    // thread-block cluster size of the Gram reduction
 constexpr int kObsBlocksTotal = 152;   // observables: blocks over the whole batch
 constexpr int kObsBlocksMax = 152;     // ... and per instance, at most
+constexpr double kUnitGrowthMax = 4096.0;   // mv_unit: largest Gershgorin bound / |tx| accepted
 
 // MB4 constants in FP64, computed on the host (mb4_consts.cpp).
 struct Constants {
@@ -46,6 +47,13 @@ struct StepParams {
   // T's off-diagonal in slot-major ELL form, nbr[e * S + k] = j or -1, w = K_kj (FP64) and
   // wt = K_kj / theta in the Krylov precision, e < ell_deg
   int ell, ell_deg;
+  // grid stencil with the x hopping factored out (tx != 0): the residual reads D / tx
+  // (DevBuffers::dtx) and forms h lam_i tx (D/tx x - (x_x- + x_x+) - (ty/tx)(x_y- + x_y+)),
+  // one FP64 instruction less per component than h lam_i (D x - tx (..) - ty (..))
+  int kin_unit;
+  // FP64 basis built from J / tx (theta = tx): the x neighbours' coefficient is then 1
+  // and the matvec spends 5 FP64 instructions per component instead of 6
+  int mv_unit;
   const int* ell_nbr;
   const double* ell_w;
   const void* ell_wt;
@@ -58,6 +66,8 @@ struct StepParams {
   double tx, ty, eps0, h;
   // residual in the eigenbasis of E on the increments dU = Tinv (U - e3 (x) u0)
   double hlam[3];          // h * lambda_i
+  double hltx[3];          // h * lambda_i * tx (kin_unit)
+  double rty;              // ty / tx (kin_unit)
   double hTc[3];           // h * (Tinv c)_i : the (K+V) u0 coefficient, and Phibar^0 = i hTc_i f(u0)-part
   double LT[kGauss][3];    // sum_m l_m(zeta_q) T[m][n]:  X_q = u0 + sum_n LT[q][n] dU_n
   double T[3][3];          // r = T rbar ;  u1 = u0 + sum_n T[2][n] dU_n
@@ -70,9 +80,11 @@ struct StepParams {
   float f_hTc[3];
 };
 
-// Per-instance constants (device array of B).  theta bounds the spectral radius
-// of J (Gershgorin: max|onsite + V| + 2|tx| + 2|ty|); the Krylov basis is built
-// from J/theta so that its vectors stay O(1).
+// Per-instance constants (device array of B).  theta scales the monomial basis,
+// v_{a+1} = (J/theta) v_a.  By default it bounds the spectral radius of J
+// (Gershgorin: max|onsite + V| + 2|tx| + 2|ty|), so that the vectors stay O(1); with
+// mv_unit it is tx, and level a grows by at most (Gershgorin bound / |tx|)^a, a factor
+// kept below kUnitGrowthMax per level.
 struct InstConst {
   double hchiW[3][kGauss]; // h chi (Tinv W)_iq, W_jq = w_q A_{c_j}(zeta_q)
   double chi, chi_theta;
@@ -123,6 +135,7 @@ struct DevBuffers {
   double2* u;        // state, B*S
   double* V;         // potential, B*S
   double* d;         // onsite + V, B*S
+  double* dtx;       // (onsite + V) / tx, B*S (kin_unit only)
   double2* S0;       // (K+V) u0, B*S
   double2* Ubar;     // transformed stage increments dU, B*3*S
   double2* dU_hist;  // converged dU of the last pred_order steps, newest first: B*pred_order*3*S (or null)

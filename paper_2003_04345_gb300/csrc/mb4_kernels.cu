@@ -136,8 +136,10 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 //   X_q = u0 + sum_n (L T)_qn dU_n   (the stage polynomial at the 6 Gauss nodes;
 // exact for the degree-11 integrand).  (The u0 terms: T^-1 E T = Lambda and
 // T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
+// KM selects the kinetic term: 0 the grid stencil, 1 the grid stencil with tx factored
+// out (StepParams::kin_unit), 2 the general sparse K (ELL).
 // ---------------------------------------------------------------------------
-template <typename TO, bool CHIF, bool ELL>
+template <typename TO, bool CHIF, int KM>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
                                                   const double2* __restrict__ dUb,
@@ -155,32 +157,41 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
   if (k >= S) return;
   const InstConst& C = ic[b];
   Nbr n;
-  if constexpr (!ELL) n = neighbours(k, p.nx, p.ny, S);
+  if constexpr (KM != 2) n = neighbours(k, p.nx, p.ny, S);
   const double2 u0 = u[plane(b, S) + k];
   const double2 s0 = S0[plane(b, S) + k];
-  const double d = D[plane(b, S) + k];
+  const double d = D[plane(b, S) + k];           // D / tx when KM == 1
   const double chik = CHIF ? p_chi[plane(b, S) + k] : 1.0;   // per-site chi (InstConst chi = 1)
-  // acc holds (Phibar.y + ... , -(Phibar.x)) in the form b = -Phibar = (acc.y, -acc.x):
-  // acc.x = dU.y + hTc S0.x + h lam (K+V)dU.x + ..., acc.y = -dU.x + hTc S0.y + ...,
-  // so that the dU term rides on the first FMA instead of a final subtraction.
-  double2 dU[3], acc[3];
+  // b = -Phibar is accumulated directly.  With Phibar = dU + i Q,
+  //   Q = h lam (K+V) dU + hTc (K+V) u0 + sum_q h chi W~_q |X_q|^2 X_q,
+  // b.x = -dU.x + Q.y and b.y = -dU.y - Q.x: the dU terms ride on the first FMAs and
+  // every sign is an operand modifier.
+  double2 dU[3], bo[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const double2* P = dUb + stage(b, m, S);
     const double2 c = P[k];
     dU[m] = c;
-    double sx, sy;
-    if constexpr (ELL) {
+    double sx, sy, hl;
+    if constexpr (KM == 2) {
       const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, P);
       sx = fma(d, c.x, o.x);
       sy = fma(d, c.y, o.y);
+      hl = p.hlam[m];
+    } else if constexpr (KM == 1) {
+      // (K+V) x / tx = D/tx x - (x_x- + x_x+) - (ty/tx) (x_y- + x_y+)
+      const double2 a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
+      sx = fma(d, c.x, -fma(p.rty, e.x + f.x, a.x + bb.x));
+      sy = fma(d, c.y, -fma(p.rty, e.y + f.y, a.y + bb.y));
+      hl = p.hltx[m];
     } else {
       const double2 a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
       sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
       sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
+      hl = p.hlam[m];
     }
-    acc[m].x = fma(p.hlam[m], sx, fma(p.hTc[m], s0.x, c.y));
-    acc[m].y = fma(p.hlam[m], sy, fma(p.hTc[m], s0.y, -c.x));
+    bo[m].x = fma(hl, sy, fma(p.hTc[m], s0.y, -c.x));
+    bo[m].y = fma(-hl, sx, fma(-p.hTc[m], s0.x, -c.y));
   }
 #pragma unroll
   for (int q = 0; q < kGauss; ++q) {
@@ -194,19 +205,22 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
     const double gx = nn * Xx, gy = nn * Xy;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      acc[i].x = fma(C.hchiW[i][q], gx, acc[i].x);
-      acc[i].y = fma(C.hchiW[i][q], gy, acc[i].y);
+      bo[i].x = fma(C.hchiW[i][q], gy, bo[i].x);
+      bo[i].y = fma(-C.hchiW[i][q], gx, bo[i].y);
     }
   }
   TO2* ob = out + (size_t)b * (size_t)out_stride;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     TO2 o;
-    o.x = from_double<TO>(acc[i].y);
-    o.y = from_double<TO>(-acc[i].x);
+    o.x = from_double<TO>(bo[i].x);
+    o.y = from_double<TO>(bo[i].y);
     ob[(size_t)i * S + k] = o;
   }
 }
+
+// Kinetic mode of the residual and the FP64 basis (template argument KM).
+inline int kin_mode(const StepParams& p) { return p.ell ? 2 : (p.kin_unit ? 1 : 0); }
 
 template <typename TK>
 void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, cudaStream_t s) {
@@ -215,12 +229,13 @@ void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, 
   typedef typename Vec2<TK>::type TK2;
   const long long os = (long long)(p.s + 1) * 3 * p.S;
   const int sf = skip_first ? 1 : 0;
-#define MB4_RES(CF, EL) \
-  k_residual<TK, CF, EL><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, (TK2*)b.v, os, sf, b.chi, b.ic, b.is)
-  if (p.ell) {
-    if (p.chi_field) MB4_RES(true, true); else MB4_RES(false, true);
-  } else {
-    if (p.chi_field) MB4_RES(true, false); else MB4_RES(false, false);
+  const double* D = p.kin_unit ? b.dtx : b.d;
+#define MB4_RES(CF, KM) \
+  k_residual<TK, CF, KM><<<grid, p.bs_residual, 0, s>>>(p, b.u, D, b.S0, b.Ubar, (TK2*)b.v, os, sf, b.chi, b.ic, b.is)
+  switch (kin_mode(p)) {
+    case 2: if (p.chi_field) MB4_RES(true, 2); else MB4_RES(false, 2); break;
+    case 1: if (p.chi_field) MB4_RES(true, 1); else MB4_RES(false, 1); break;
+    default: if (p.chi_field) MB4_RES(true, 0); else MB4_RES(false, 0); break;
   }
 #undef MB4_RES
 }
@@ -228,13 +243,14 @@ void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, 
 template <typename TK>
 void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phibar3, cudaStream_t s) {
   dim3 grid((p.S + p.bs_residual - 1) / p.bs_residual, p.B);
-#define MB4_RES(CF, EL) \
-  k_residual<double, CF, EL><<<grid, p.bs_residual, 0, s>>>(p, b.u, b.d, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.chi, \
+  const double* D = p.kin_unit ? b.dtx : b.d;
+#define MB4_RES(CF, KM) \
+  k_residual<double, CF, KM><<<grid, p.bs_residual, 0, s>>>(p, b.u, D, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.chi, \
                                                             b.ic, b.is)
-  if (p.ell) {
-    if (p.chi_field) MB4_RES(true, true); else MB4_RES(false, true);
-  } else {
-    if (p.chi_field) MB4_RES(true, false); else MB4_RES(false, false);
+  switch (kin_mode(p)) {
+    case 2: if (p.chi_field) MB4_RES(true, 2); else MB4_RES(false, 2); break;
+    case 1: if (p.chi_field) MB4_RES(true, 1); else MB4_RES(false, 1); break;
+    default: if (p.chi_field) MB4_RES(true, 0); else MB4_RES(false, 0); break;
   }
 #undef MB4_RES
 }
@@ -246,7 +262,7 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 // v_{a+1} = (J/theta) v_a is built for the three right-hand sides together, and
 // (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
 // ---------------------------------------------------------------------------
-template <typename TK, bool ELL>
+template <typename TK, int KM>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
                                                 const InstConst* __restrict__ ic, const InstStatus* is) {
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S) return;
   const JCoef<TK> j = jc[plane(b, S) + k];
-  if constexpr (ELL) {
+  if constexpr (KM == 2) {
     // (J x)_re = a xp + e1 xq + sum_j (K_kj / theta) xq_j, (J x)_im = -e2 xp - a xq - sum_j (K_kj / theta) xp_j
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -281,8 +297,13 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
       TK2 o;
       // (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
       // (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
-      o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
-      o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
+      if constexpr (KM == 1) {                 // theta = tx: tx / theta = 1
+        o.x = fma(j.a, c.x, fma(j.e1, c.y, -fma(ty, e.y + f.y, a.y + bb.y)));
+        o.y = fma(-j.e2, c.x, fma(-j.a, c.y, fma(ty, e.x + f.x, a.x + bb.x)));
+      } else {
+        o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
+        o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
+      }
       v[level(b, a_in + 1, i, p.s, S) + k] = o;
     }
   }
@@ -472,8 +493,9 @@ __device__ __forceinline__ void warp_sums(const GramAcc<double> (&acc)[NE], doub
 //     min_c || b - (I - h lam_i J) sum_a c_a v_a ||:
 //       (B^T G B) c = B^T G e_0,  B = [I; 0] - sig_i [0; I]  (s x s),
 //  3. factors them with one warp (right-looking Cholesky; the basis is truncated
-//     at the first pivot below trunc_rel times the leading one, a numerically
-//     exhausted Krylov space; b = 0 gives c = 0) and solves.
+//     at the first pivot below trunc_rel times the larger of the leading one and
+//     its own diagonal entry before elimination, a numerically exhausted Krylov
+//     space whatever the scale of the levels; b = 0 gives c = 0) and solves.
 // The three systems finish on three different blocks, in parallel.
 template <typename TK, int SK, int CL>
 __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
@@ -567,6 +589,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   __shared__ double G[NE];
   __shared__ double Nm[SK][SK + 1];             // [.., SK] holds the right-hand side
   __shared__ double rinv[SK];
+  __shared__ double Ndiag[SK];                  // diagonal of the normal matrix before elimination
   for (int t = threadIdx.x; t < SLICES * NE; t += blockDim.x) {
     const int sl = t / NE, e = t - sl * NE;
     const int b0 = sl * nb / SLICES, b1 = (sl + 1) * nb / SLICES;
@@ -600,6 +623,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
     const int a = t / (SK + 1), c = t - a * (SK + 1);
     Nm[a][c] = (c < SK) ? g(a, c) - sg * (g(a + 1, c) + g(a, c + 1)) + sg * sg * g(a + 1, c + 1)
                         : g(a, 0) - sg * g(a + 1, 0);
+    if (c == a) Ndiag[a] = Nm[a][c];
   }
   __syncthreads();
   // 3. one warp: Cholesky in place (lower triangle), then the two triangular solves,
@@ -609,7 +633,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
     const double lead = Nm[0][0];
     for (int a = 0; a < dim; ++a) {
       const double dg = Nm[a][a];
-      if (!(dg > (double)p.trunc_rel * lead)) { dim = a; break; }
+      if (!(dg > (double)p.trunc_rel * fmax(lead, Ndiag[a]))) { dim = a; break; }
       const double il = rsqrt(dg);
       __syncwarp();
       for (int b2 = a + 1 + lane; b2 < SK; b2 += 32) Nm[b2][a] *= il;
@@ -683,13 +707,10 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
     return;
   }
   dim3 grid((p.S + p.bs_matvec - 1) / p.bs_matvec, p.B);
+  auto kern = p.ell ? k_matvec<TK, 2> : (sizeof(TK) == sizeof(double) && p.mv_unit) ? k_matvec<TK, 1> : k_matvec<TK, 0>;
   for (int a = 0; a < p.s; ++a)
-    if (p.ell)
-      launch_k(p.pdl != 0, k_matvec<TK, true>, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v,
-               a, (const InstConst*)b.ic, (const InstStatus*)b.is);
-    else
-      launch_k(p.pdl != 0, k_matvec<TK, false>, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v,
-               a, (const InstConst*)b.ic, (const InstStatus*)b.is);
+    launch_k(p.pdl != 0, kern, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a,
+             (const InstConst*)b.ic, (const InstStatus*)b.is);
 }
 
 template <typename TK, int SK>
