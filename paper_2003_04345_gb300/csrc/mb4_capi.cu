@@ -301,11 +301,32 @@ int ensure_scratch(mb4_batch* c) {
 }
 
 // Bring n (re, im) doubles onto the device, planar; host data is staged through c->io.
+// The device address of a host buffer that is page-locked and mapped (cudaHostAlloc,
+// cudaMallocHost, or cudaHostRegister with mapping: with unified addressing every
+// page-locked buffer is), else null.  Kernels then read or write such a buffer in
+// place over the host link, with no staging copy.
+template <typename T>
+T* mapped_host(T* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();                          // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? static_cast<T*>(a.devicePointer) : nullptr;
+}
+
 int stage_in(mb4_batch* c, const double* re, const double* im, size_t n, int on_device, const double** dre,
              const double** dim) {
   if (on_device) {
     *dre = re;
     *dim = im;
+    return MB4_OK;
+  }
+  const double* mre = mapped_host(re);
+  const double* mim = mapped_host(im);
+  if (mre && mim) {                              // the pack kernel reads the host buffers in place
+    *dre = mre;
+    *dim = mim;
     return MB4_OK;
   }
   MB4_TRY(cudaMemcpyAsync(c->io, re, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -318,6 +339,14 @@ int stage_in(mb4_batch* c, const double* re, const double* im, size_t n, int on_
 int stage_out(mb4_batch* c, const double2* z, double* re, double* im, size_t n, int on_device) {
   if (on_device) {
     launch_unpack(z, re, im, n, c->stream);
+    MB4_TRY(cudaGetLastError());
+    MB4_TRY(cudaStreamSynchronize(c->stream));
+    return MB4_OK;
+  }
+  double* mre = mapped_host(re);
+  double* mim = mapped_host(im);
+  if (mre && mim) {                              // the unpack kernel writes the host buffers in place
+    launch_unpack(z, mre, mim, n, c->stream);
     MB4_TRY(cudaGetLastError());
     MB4_TRY(cudaStreamSynchronize(c->stream));
     return MB4_OK;

@@ -763,9 +763,10 @@ int gram_blocks_per_system(int s_dim, int B) {
 #undef MB4_OCC
   }
   if (e != cudaSuccess || occ < 1 || sms < 1) return 0;
-  // The FP64 kernel is bound by the FP64 pipe: two blocks per SM already overlap
-  // the loads with the arithmetic, and fewer blocks mean fewer partial sums.
-  if (sizeof(TK) == sizeof(double) && occ > 2) occ = 2;
+  // The FP64 kernel is bound by the FP64 pipe: one block per SM (8 warps, each with
+  // the loads of 4 sites in flight) keeps it busy, spreads evenly over the SMs and
+  // leaves the fewest partial sums (measured at 512x512: 54 us against 57 us with two).
+  if (sizeof(TK) == sizeof(double)) occ = 1;
   long long nb = (long long)sms * occ / (3LL * (B > 0 ? B : 1));
   if (nb > kGramCap) nb = kGramCap;   // more blocks only lengthen the last block's reduction
   if (sizeof(TK) == sizeof(float) && nb >= kGramCluster) nb -= nb % kGramCluster;   // whole clusters

@@ -113,6 +113,30 @@ def test_disable_and_load_slots(mb4):
         assert _rel(bt.get_state(0), _solo(mb4, nx, ny, V[0], chi[0], psi[0], h, 5, "mixed")) <= 1e-12
 
 
+def test_fp64_load_and_its_basis_scale_limit(mb4):
+    """An FP64 batch scales its Krylov basis by tx: a reloaded slot gives its solo run,
+    and a potential whose Gershgorin bound exceeds 4096 |tx| is refused (the mixed batch,
+    scaled by that bound, takes it)."""
+    nx, ny, B, h = 16, 24, 2, 0.01
+    V, chi, psi = _problems(nx, ny, B, seed0=11)
+    V2 = inputs.potential(nx, ny, 1.0, 4, 20.0, 123)
+    psi2 = inputs.wavepacket(nx, ny, 2.0, math.pi / 4, 0.0)
+    Vbig = V2.copy()
+    Vbig[5] = 5000.0
+    with mb4.Batch(nx, ny, V, chi, h, precision="fp64") as bt:
+        bt.set_state(psi)
+        bt.step(2)
+        bt.load(1, V2, 0.7, psi2)
+        stats, codes = bt.step(5)
+        assert codes == [0, 0]
+        assert _rel(bt.get_state(1), _solo(mb4, nx, ny, V2, 0.7, psi2, h, 5, "fp64")) <= 1e-12
+        with pytest.raises(mb4.MB4Error) as e:
+            bt.load(1, Vbig, 0.7, psi2)
+        assert e.value.code == mb4.MB4_ERR_INVALID_ARG
+    with mb4.Batch(nx, ny, V, chi, h, precision="mixed") as bt:
+        bt.load(1, Vbig, 0.7, psi2)
+
+
 def test_ensemble_1024_grid128_full_size(mb4):
     """The 1024-member 128x128 ensemble (chi ~ U[0, 2] per seed, 1% defects,
     sigma = 8, h = 0.01), mixed precision: two steps of the whole batch; sampled

@@ -199,6 +199,33 @@ def test_small_and_ragged_grids_match_oracle(mb4, nx, ny):
             assert _rel(it.get_state(), u) <= 1e-11
 
 
+@pytest.mark.parametrize("tx,ty", [(0.0, 0.8), (-0.7, 1.3), (0.002, 1.0)])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_stencil_forms_match_oracle(mb4, tx, ty, precision):
+    """The three forms of the grid stencil: tx = 0 (the residual's plain stencil and the
+    Gershgorin-scaled basis), tx < 0 (x hopping factored out, the FP64 basis scaled by a
+    negative tx) and a tx so small that the FP64 basis keeps the Gershgorin scale while the
+    residual still factors tx out."""
+    nx, ny = 24, 20
+    rng = np.random.default_rng(int(1000 * abs(tx)) + 31)
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    V[rng.integers(0, S, 3)] += 20.0
+    chi, eps0, h = 0.9, 0.2, 0.01
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    u0 = _rand_state(rng, S, 0.3)
+    U = u0[None, :] + 0.05 * np.vstack([_rand_state(rng, S, 0.3) for _ in range(3)])
+    u = u0
+    for _ in range(5):
+        u = orc.step(prob, u, h)
+    with mb4.Integrator(nx, ny, V, chi, h, tx=tx, ty=ty, onsite=eps0, precision=precision) as it:
+        got = it.residual(u0, U)
+        assert np.max(np.abs(got - orc.residual(prob, u0, U, h))) <= 1e-13 * np.max(np.abs(U))
+        it.set_state(u0)
+        it.step(5)
+        assert _rel(it.get_state(), u) <= 1e-11
+
+
 def test_observables_match_oracle(mb4):
     rng = np.random.default_rng(8)
     nx, ny = 48, 20
@@ -306,6 +333,34 @@ def test_async_steps_equal_synchronous_steps(mb4, precision):
         assert st_b["steps_done"] == 7 and st_b["newton_iters_total"] == st_a["newton_iters_total"]
         b.step_async(1)
         assert b.wait()["steps_done"] == 1          # counts restart at every wait
+
+
+def test_pinned_host_buffers_equal_pageable_ones(mb4):
+    """Page-locked host buffers are read and written in place by the pack and unpack
+    kernels; pageable ones go through a staging copy.  Both give the same bits."""
+    import torch
+    w = inputs.grid16_fp64()
+    psi = w.psi0()
+    S = w.nx * w.ny
+    hre = torch.from_numpy(np.ascontiguousarray(psi.real)).pin_memory()
+    him = torch.from_numpy(np.ascontiguousarray(psi.imag)).pin_memory()
+    outs = []
+    for pinned in (False, True):
+        with mb4.Integrator(w.nx, w.ny, w.potential(), w.chi, w.h, tx=w.tx, ty=w.ty, onsite=w.eps0) as it:
+            if pinned:
+                it.set_state_ptr(hre.data_ptr(), him.data_ptr(), 0)
+            else:
+                it.set_state(psi)
+            it.step(3)
+            if pinned:
+                a = torch.empty(S, dtype=torch.float64).pin_memory()
+                b = torch.empty(S, dtype=torch.float64).pin_memory()
+                it.get_state_ptr(a.data_ptr(), b.data_ptr(), 0)
+                outs.append(a.numpy() + 1j * b.numpy())
+                assert np.array_equal(outs[-1], it.get_state())
+            else:
+                outs.append(it.get_state())
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_async_failure_is_reported_by_wait(mb4):
