@@ -106,7 +106,6 @@ struct InstStatus {
   int last_newton_iters;
   unsigned int u0max_bits;           // ||u0||_inf of the current step (float bits, >= 0)
   unsigned int ticket_gram[3];       // last-block tickets, one per shifted system (reset by the last block)
-  unsigned int ticket_update;
   int pred_count;                    // converged increments kept for the Newton start (<= pred_order)
   int predicted;                     // the current step started from an extrapolation
   int next_predicted;                // start chosen for the next step (adaptive mode)
@@ -124,10 +123,8 @@ struct InstStatus {
 
 // Batch-wide loop control.
 struct BatchCtl {
-  unsigned int ticket_inst;          // instances that finished the current update
-  int n_cont;                        // of which continue
-  int any_cont;
-  int pad;
+  int any_cont;                      // some instance continues its Newton loop (k_newton_test)
+  int pad[3];
 };
 
 // Device buffers of one batch.

@@ -782,50 +782,27 @@ void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   launch_gram<TK>(p, b, s);
 }
 
-// Records instance b's loop decision; the last instance to do so (over the whole
-// batch) sets the WHILE condition: continue while any instance continues.
-__device__ void instance_done(const StepParams& p, BatchCtl* bc, int cont, cudaGraphConditionalHandle h,
-                              int use_cond) {
-  if (cont) atomicAdd(&bc->n_cont, 1);
-  __threadfence();
-  const unsigned int t = atomicAdd(&bc->ticket_inst, 1u);
-  if (t == (unsigned int)(p.B - 1)) {
-    __threadfence();
-    const int any = atomicExch(&bc->n_cont, 0) > 0;
-    bc->ticket_inst = 0u;
-    bc->any_cont = any;
-    if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
-  }
-}
-
-// Newton update (Algorithm 1) and the loop test of its Newton iteration (failure rule of
-// Sec. 2.2): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (from dU^0 = 0 the
-// first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar; NaN/Inf flagged.  The last
-// block of each instance runs its test: continue while ||r^l||_inf > rtol ||u0||_inf
-// (and, when enabled, the predicted remaining error is above newton_predict ||u0||_inf),
-// for at most newton_max iterations.  Grid: (sites / bs_update, B).
+// Newton update (Algorithm 1): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (from
+// dU^0 = 0 the first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar, merged over
+// the blocks with an atomic max; NaN/Inf flagged.  No block waits for another: the loop
+// test runs in k_newton_test once the whole grid has finished.  Grid: (sites / bs_update, B).
 template <typename TK, int SK>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
-                                                const double* __restrict__ coef, const double2* __restrict__ u,
-                                                double2* __restrict__ Ubar, InstStatus* is, BatchCtl* bc,
-                                                cudaGraphConditionalHandle h, int use_cond) {
+                                                const double* __restrict__ coef, double2* __restrict__ Ubar,
+                                                InstStatus* is) {
   pdl_wait();
   pdl_launch_dependents();
   const int inst = blockIdx.y;
   InstStatus& I = is[inst];
-  if (!I.active) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) instance_done(p, bc, 0, h, use_cond);
-    return;
-  }
+  if (!I.active) return;
   typedef typename Vec2<TK>::type TK2;
   __shared__ TK cs[3][SK];
   __shared__ float wmax[8];
   __shared__ int wbad[8];
-  __shared__ bool is_last;
   if (threadIdx.x < 3 * SK)
     cs[threadIdx.x / SK][threadIdx.x % SK] =
         (TK)coef[((size_t)inst * 3 + threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
-  const bool first = (*(volatile int*)&I.newton_iter) == 0 && !I.predicted;
+  const bool first = I.newton_iter == 0 && !I.predicted;
   __syncthreads();
   const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -882,41 +859,53 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_update(StepParams p, const 
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { bm = fmaxf(bm, wmax[w]); bb |= wbad[w]; }
     if (bm > 0.f) atomicMax(&I.rmax_bits, dbits((double)bm));
     if (bb) atomicOr(&I.nonfinite, 1);
-    __threadfence();
-    unsigned int t = atomicAdd(&I.ticket_update, 1u);
-    is_last = (t == gridDim.x - 1);
   }
-  __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
-  __threadfence();
-  I.ticket_update = 0u;
-  int cont = 0;
-  const int it = I.newton_iter;                  // iteration index l of this update
-  const double r = __longlong_as_double((long long)atomicOr(&I.rmax_bits, 0ull));
-  const double u0n = (double)__uint_as_float(atomicOr(&I.u0max_bits, 0u));
-  const int nonfinite = atomicOr(&I.nonfinite, 0);
-  if (it < 8) I.hist[it] = r;
-  I.last_rmax = r;
-  I.last_u0max = u0n;
-  I.newton_iter = it + 1;
-  if (nonfinite || !isfinite(r)) {
-    I.error = MB4_ERR_NONFINITE;
-  } else if (r <= p.newton_rtol * u0n) {
-    cont = 0;
-  } else if (p.newton_predict > 0.0 && it >= 1 && r < 0.5 * I.prev_rmax &&
-             (r / I.prev_rmax) / (1.0 - r / I.prev_rmax) * r <= p.newton_predict * u0n) {
-    cont = 0;
-  } else if (it + 1 >= p.newton_max) {
-    I.error = MB4_ERR_NEWTON_NOT_CONVERGED;
-  } else {
-    cont = 1;
+}
+
+// The loop test of a Newton iteration (failure rule of Sec. 2.2), one thread per instance
+// that iterated: continue while ||r^l||_inf > rtol ||u0||_inf (and, when enabled, while the
+// predicted remaining error is above newton_predict ||u0||_inf), for at most newton_max
+// iterations.  The block then sets the WHILE condition: continue while any instance
+// continues.  One block of up to 1024 threads.
+__global__ void k_newton_test(StepParams p, InstStatus* is, BatchCtl* bc, cudaGraphConditionalHandle h,
+                              int use_cond) {
+  pdl_wait();
+  int any = 0;
+  for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
+    InstStatus& I = is[b];
+    if (!I.active) continue;
+    int cont = 0;
+    const int it = I.newton_iter;                // iteration index l of this update
+    const double r = __longlong_as_double((long long)I.rmax_bits);
+    const double u0n = (double)__uint_as_float(I.u0max_bits);
+    if (it < 8) I.hist[it] = r;
+    I.last_rmax = r;
+    I.last_u0max = u0n;
+    I.newton_iter = it + 1;
+    if (I.nonfinite || !isfinite(r)) {
+      I.error = MB4_ERR_NONFINITE;
+    } else if (r <= p.newton_rtol * u0n) {
+      cont = 0;
+    } else if (p.newton_predict > 0.0 && it >= 1 && r < 0.5 * I.prev_rmax &&
+               (r / I.prev_rmax) / (1.0 - r / I.prev_rmax) * r <= p.newton_predict * u0n) {
+      cont = 0;
+    } else if (it + 1 >= p.newton_max) {
+      I.error = MB4_ERR_NEWTON_NOT_CONVERGED;
+    } else {
+      cont = 1;
+    }
+    I.prev_rmax = r;
+    I.last_newton_iters = it + 1;
+    I.rmax_bits = 0ull;
+    I.cont = cont;
+    if (!cont) I.active = 0;
+    any |= cont;
   }
-  I.prev_rmax = r;
-  I.last_newton_iters = it + 1;
-  I.rmax_bits = 0ull;
-  I.cont = cont;
-  if (!cont) I.active = 0;
-  instance_done(p, bc, cont, h, use_cond);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    bc->any_cont = any;
+    if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
 }
 
 template <typename TK>
@@ -925,9 +914,12 @@ void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long 
   const void* basis = p.precond ? b.pz : b.v;      // rbar = sum_a c_a z_a when preconditioned
 #define MB4_CALL(N)                                                                                      \
   launch_k(p.pdl != 0, k_update<TK, N>, grid, dim3(p.bs_update), 0, s, p, (const typename Vec2<TK>::type*)basis, \
-           (const double*)b.coef, (const double2*)b.u, b.Ubar, b.is, b.bc, (cudaGraphConditionalHandle)h, use_cond)
+           (const double*)b.coef, b.Ubar, b.is)
   MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL
+  const int nt = p.B >= 1024 ? 1024 : ((p.B + 31) / 32) * 32;
+  launch_k(p.pdl != 0, k_newton_test, dim3(1), dim3(nt), 0, s, p, b.is, b.bc, (cudaGraphConditionalHandle)h,
+           use_cond);
 }
 
 // Newton start of the next step (option newton_start).  Fixed mode: extrapolate.
@@ -1017,11 +1009,7 @@ void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 // Arms every enabled instance without an error for the next step (start of a call).
 __global__ void k_arm(int B, int pred_order, InstStatus* is, BatchCtl* bc) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b == 0) {
-    bc->ticket_inst = 0u;
-    bc->n_cont = 0;
-    bc->any_cont = 0;
-  }
+  if (b == 0) bc->any_cont = 0;
   if (b >= B) return;
   InstStatus& I = is[b];
   I.newton_iter = 0;
@@ -1030,7 +1018,6 @@ __global__ void k_arm(int B, int pred_order, InstStatus* is, BatchCtl* bc) {
   I.u0max_bits = 0u;
   I.prev_rmax = 0.0;
   I.ticket_gram[0] = I.ticket_gram[1] = I.ticket_gram[2] = 0u;
-  I.ticket_update = 0u;
   const int go = I.enabled && !I.error;
   I.in_step = go;
   I.active = go;
