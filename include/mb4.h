@@ -137,8 +137,9 @@ typedef struct {
     int    precondition; /* 0 (default): the shifted solves use the monomial Krylov basis of J.
                             1: right-precondition each shifted system with the inverse of its
                             constant-coefficient part, I + i h lam_i (K + mean(onsite + V)),
-                            applied by 2D DFTs (hand-written, O(n) work per site and pass;
-                            nx, ny <= MB4_MAX_PRECOND_SIDE).  For stiff kinetic terms such as
+                            applied by 2D FFTs (hand-written mixed-radix; a side with a large
+                            prime factor p costs O(p) per site and pass; nx, ny <=
+                            MB4_MAX_PRECOND_SIDE).  For stiff kinetic terms such as
                             the paper's Laplacian (h ||K|| ~ 10 on its 70 x 70 grid, Sec. 3),
                             where the plain basis cannot reduce the residual in s vectors.
                             The root of each step is the same.                                */

@@ -548,6 +548,10 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
                                               : gram_blocks_per_system<double>(p.s, B);
   if (p.gram_blocks < 1) return MB4_ERR_CUDA;
   if (p.precond && (grid->nx > MB4_MAX_PRECOND_SIDE || grid->ny > MB4_MAX_PRECOND_SIDE)) return MB4_ERR_INVALID_ARG;
+  if (p.precond) {
+    p.fft_nrx = fft_radices(grid->nx, p.fft_rx);
+    p.fft_nry = fft_radices(grid->ny, p.fft_ry);
+  }
   p.use_powers = (o.precision == MB4_MIXED && !p.precond && !p.ell) ? 1 : 0;
   if (p.use_powers) MB4_CHECK(prepare_powers());
   std::vector<double> Dtx;

@@ -17,6 +17,7 @@ constexpr int kGramCluster = 8;    // thread-block cluster size of the Gram redu
 constexpr int kObsBlocksTotal = 152;   // observables: blocks over the whole batch
 constexpr int kObsBlocksMax = 152;     // ... and per instance, at most
 constexpr double kUnitGrowthMax = 4096.0;   // mv_unit: largest Gershgorin bound / |tx| accepted
+constexpr int kMaxFftStages = 12;  // radices of one FFT length <= MB4_MAX_PRECOND_SIDE (1024 = 4^5)
 
 // MB4 constants in FP64, computed on the host (mb4_consts.cpp).
 struct Constants {
@@ -42,6 +43,9 @@ struct StepParams {
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
   int pdl;                 // programmatic dependent launch inside the Newton loop
   int precond;             // spectral preconditioning of the shifted solves (mb4_precond.cu)
+  // radices of the preconditioner's FFTs along x and y (product nx, ny; none for 1)
+  int fft_nrx, fft_nry;
+  int fft_rx[kMaxFftStages], fft_ry[kMaxFftStages];
   int chi_field;           // chi per site (DevBuffers::chi); InstConst then holds chi = 1
   // general kinetic matrix (mb4_create_sparse) instead of the grid stencil: K = onsite I + T,
   // T's off-diagonal in slot-major ELL form, nbr[e * S + k] = j or -1, w = K_kj (FP64) and
@@ -194,6 +198,8 @@ template <typename TK> void launch_residual_out(const StepParams& p, const DevBu
 void launch_pack(const double* re, const double* im, double2* z, size_t n, cudaStream_t st);
 // Preconditioned Krylov basis (mb4_precond.cu): z_a = P_i v_a, v_{a+1} = A_i z_a - v_a, a < s.
 template <typename TK> void launch_precond_basis(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// Radices of an FFT of length n: 4s, then 2, 3, 5, 7, then any other prime factor.
+int fft_radices(int n, int* rad);
 // Twiddles and per-mode inverse multipliers 1 / (1 + i h lam_i (ebar_b + Khat(k))) (host-made).
 template <typename TK>
 int precond_tables(const StepParams& p, const double* ebar, const double* hlam_i, void* wx, void* wy, void* minv,

@@ -113,8 +113,16 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const d
     }
     m = fmaxf(absf_of(c.x), absf_of(c.y));
   }
+  // one atomic per block: same-address atomics queue at one L2 slice
   m = warp_max(m);
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&is[b].u0max_bits, __float_as_uint(m));
+  __shared__ float wm[kSiteThreadsMax / 32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float bm = wm[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) bm = fmaxf(bm, wm[w]);
+    if (bm > 0.f) atomicMax(&is[b].u0max_bits, __float_as_uint(bm));
+  }
 }
 
 template <typename TK>

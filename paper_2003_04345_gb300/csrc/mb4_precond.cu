@@ -16,13 +16,16 @@
 // correction is rbar_i = sum_a c_a z_a (flexible form: the z_a are stored, so the
 // rounding of P does not enter the relation).  The root of the step does not change.
 //
-// The DFTs run in the Krylov precision TK, one block per grid line with the line and
-// its twiddle factors in shared memory (at most 3 x 1024 x 16 B = 48 KB), O(n) per
-// element: meant for the paper's grids (n <= 1024 per side, MB4_MAX_PRECOND_SIDE),
-// not for large production grids.
+// The DFTs are mixed-radix FFTs in the Krylov precision TK (self-sorting Stockham form:
+// each stage of radix R maps sub-transforms of length Ns to length Ns R, with the
+// twiddles exp(-2 pi i m / n) from one table), one block per grid line with the line, a
+// scratch line and the twiddles in shared memory (at most 3 x 1024 x 16 B = 48 KB).
+// A stage of radix R costs R complex multiply-adds per element: 14 for n = 70 (2, 5, 7),
+// 20 for n = 1024 (4^5), n for a prime n.  Sides up to MB4_MAX_PRECOND_SIDE.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <initializer_list>
 #include <vector>
 
 #include "mb4_device.cuh"
@@ -38,34 +41,67 @@ __device__ __forceinline__ typename Vec2<TK>::type cmul(typename Vec2<TK>::type 
   return r;
 }
 
-// DFT of one line of n values in shared memory (line[]), twiddles w[m] = exp(-2 pi i m / n)
-// (conjugated when inverse): out_k = scale sum_j line_j w^(j k).  Thread t writes
-// k = t, t + T, ...; out may be shared or global memory.
-template <typename TK>
-__device__ void dft_line(const typename Vec2<TK>::type* line, const typename Vec2<TK>::type* w, int n, bool inverse,
-                         TK scale, typename Vec2<TK>::type* out) {
-  typedef typename Vec2<TK>::type TK2;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    TK sx = 0, sy = 0;
-    int m = 0;                                   // (j k) mod n
-    for (int j = 0; j < n; ++j) {
-      TK2 t = w[m];
-      if (inverse) t.y = -t.y;
-      const TK2 x = line[j];
-      sx += x.x * t.x - x.y * t.y;
-      sy += x.x * t.y + x.y * t.x;
-      m += k;
-      if (m >= n) m -= n;
+// Radices of an FFT of length n (host): 4s first, then 2, 3, 5, 7, then the other primes.
+int fft_radices(int n, int* rad) {
+  int k = 0;
+  for (int r : {4, 2, 3, 5, 7})
+    while (n > 1 && n % r == 0) {
+      rad[k++] = r;
+      n /= r;
     }
-    TK2 o;
-    o.x = sx * scale;
-    o.y = sy * scale;
-    out[k] = o;
+  for (int r = 11; n > 1; r += 2)
+    while (n % r == 0) {
+      rad[k++] = r;
+      n /= r;
+    }
+  return k;
+}
+
+// FFT of one line of n values in shared memory, out_k = sum_j a_j w^(j k) with the
+// twiddles w[m] = exp(-2 pi i m / n) (conjugated when inverse).  Stage q of radix R
+// (Ns = product of the earlier radices): output (j, t), j < n/R, t < R, k = j mod Ns, is
+//   sum_s a[j + s n/R] exp(-2 pi i s (k / (Ns R) + t / R)),
+// written to (j / Ns) Ns R + k + t Ns.  a and b alternate as input and output; returns
+// the buffer holding the result.  Every thread of the block takes part (stages sync).
+template <typename TK>
+__device__ typename Vec2<TK>::type* fft_line(typename Vec2<TK>::type* a, typename Vec2<TK>::type* b,
+                                             const typename Vec2<TK>::type* w, int n, const int* rad, int nrad,
+                                             bool inverse) {
+  typedef typename Vec2<TK>::type TK2;
+  int Ns = 1;
+  for (int q = 0; q < nrad; ++q) {
+    const int R = rad[q], nb = n / R, tw = n / (Ns * R);
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+      const int t = o / nb, j = o - t * nb, k = j % Ns;
+      int e = k * tw + t * nb;                   // < 2n
+      if (e >= n) e -= n;
+      TK sx = 0, sy = 0;
+      int m = 0;                                 // (s e) mod n
+      for (int s = 0; s < R; ++s) {
+        TK2 c = w[m];
+        if (inverse) c.y = -c.y;
+        const TK2 x = a[j + s * nb];
+        sx += x.x * c.x - x.y * c.y;
+        sy += x.x * c.y + x.y * c.x;
+        m += e;
+        if (m >= n) m -= n;
+      }
+      TK2 r;
+      r.x = sx;
+      r.y = sy;
+      b[(j / Ns) * Ns * R + k + t * Ns] = r;
+    }
+    __syncthreads();
+    TK2* tmp = a;
+    a = b;
+    b = tmp;
+    Ns *= R;
   }
+  return a;
 }
 
 // Row pass: src level (rows of nx) -> dst, forward or inverse (inverse scales by scale).
-// Grid (ny, 3, B); dynamic shared memory 2 * nx TK2.
+// Grid (ny, 3, B); dynamic shared memory 3 * nx TK2.
 template <typename TK>
 __global__ void k_dft_rows(StepParams p, const typename Vec2<TK>::type* __restrict__ src, size_t src_inst_stride,
                            typename Vec2<TK>::type* __restrict__ dst, size_t dst_inst_stride,
@@ -79,6 +115,7 @@ __global__ void k_dft_rows(StepParams p, const typename Vec2<TK>::type* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TK2* line = reinterpret_cast<TK2*>(smem_raw);
   TK2* w = line + p.nx;
+  TK2* scratch = w + p.nx;
   const size_t off_s = (size_t)b * src_inst_stride + (size_t)i * p.S + (size_t)y * p.nx;
   const size_t off_d = (size_t)b * dst_inst_stride + (size_t)i * p.S + (size_t)y * p.nx;
   for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
@@ -86,11 +123,17 @@ __global__ void k_dft_rows(StepParams p, const typename Vec2<TK>::type* __restri
     w[x] = wx[x];
   }
   __syncthreads();
-  dft_line<TK>(line, w, p.nx, inverse != 0, scale, dst + off_d);
+  const TK2* r = fft_line<TK>(line, scratch, w, p.nx, p.fft_rx, p.fft_nrx, inverse != 0);
+  for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+    TK2 o = r[x];
+    o.x *= scale;
+    o.y *= scale;
+    dst[off_d + x] = o;
+  }
 }
 
-// Column pass on buf (in place): forward DFT along y, multiply by 1 / m_i(kx, ky),
-// inverse DFT along y.  Grid (nx, 3, B); dynamic shared memory 3 * ny TK2.
+// Column pass on buf (in place): forward FFT along y, multiply by 1 / m_i(kx, ky),
+// inverse FFT along y.  Grid (nx, 3, B); dynamic shared memory 3 * ny TK2.
 template <typename TK>
 __global__ void k_dft_cols_apply(StepParams p, typename Vec2<TK>::type* __restrict__ buf, size_t inst_stride,
                                  const typename Vec2<TK>::type* __restrict__ wy,
@@ -111,13 +154,11 @@ __global__ void k_dft_cols_apply(StepParams p, typename Vec2<TK>::type* __restri
     w[y] = wy[y];
   }
   __syncthreads();
-  dft_line<TK>(line, w, p.ny, false, (TK)1, tmp);
+  TK2* f = fft_line<TK>(line, tmp, w, p.ny, p.fft_ry, p.fft_nry, false);
+  for (int k = threadIdx.x; k < p.ny; k += blockDim.x) f[k] = cmul<TK>(f[k], mi[(size_t)k * p.nx]);
   __syncthreads();
-  for (int k = threadIdx.x; k < p.ny; k += blockDim.x) line[k] = cmul<TK>(tmp[k], mi[(size_t)k * p.nx]);
-  __syncthreads();
-  dft_line<TK>(line, w, p.ny, true, (TK)1, tmp);
-  __syncthreads();
-  for (int y = threadIdx.x; y < p.ny; y += blockDim.x) col[(size_t)y * p.nx] = tmp[y];
+  const TK2* r = fft_line<TK>(f, f == line ? tmp : line, w, p.ny, p.fft_ry, p.fft_nry, true);
+  for (int y = threadIdx.x; y < p.ny; y += blockDim.x) col[(size_t)y * p.nx] = r[y];
 }
 
 // v_{a+1} = A_i z_a - v_a = z_a - sig_i (J/theta) z_a - v_a, J/theta from the per-site
@@ -168,11 +209,11 @@ void launch_precond_basis(const StepParams& p, const DevBuffers& b, cudaStream_t
   for (int a = 0; a < p.s; ++a) {
     const size_t lev = (size_t)a * 3 * p.S;
     // z_a = P v_a: rows forward (v_a -> t), columns forward / 1/m / inverse (t), rows inverse (t -> z_a)
-    launch_k(p.pdl != 0, k_dft_rows<TK>, dim3(p.ny, 3, p.B), dim3(rows_threads), 2 * p.nx * sizeof(TK2), s, p,
+    launch_k(p.pdl != 0, k_dft_rows<TK>, dim3(p.ny, 3, p.B), dim3(rows_threads), 3 * p.nx * sizeof(TK2), s, p,
              (const TK2*)(v + lev), vstride, t, tstride, (const TK2*)b.pwx, 0, (TK)1, (const InstStatus*)b.is);
     launch_k(p.pdl != 0, k_dft_cols_apply<TK>, dim3(p.nx, 3, p.B), dim3(cols_threads), 3 * p.ny * sizeof(TK2), s, p,
              t, tstride, (const TK2*)b.pwy, (const TK2*)b.pminv, (const InstStatus*)b.is);
-    launch_k(p.pdl != 0, k_dft_rows<TK>, dim3(p.ny, 3, p.B), dim3(rows_threads), 2 * p.nx * sizeof(TK2), s, p,
+    launch_k(p.pdl != 0, k_dft_rows<TK>, dim3(p.ny, 3, p.B), dim3(rows_threads), 3 * p.nx * sizeof(TK2), s, p,
              (const TK2*)t, tstride, z + lev, vstride, (const TK2*)b.pwx, 1, scale, (const InstStatus*)b.is);
     launch_k(p.pdl != 0, k_pmatvec<TK>, gsite, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, v,
              (const TK2*)z, a, (const InstConst*)b.ic, (const InstStatus*)b.is);

@@ -62,6 +62,29 @@ def test_preconditioned_shifted_solves_match_dense_lu(mb4, precision):
         assert np.linalg.norm(xr - xs) <= 1.01 * np.linalg.norm(np.linalg.inv(A), 2) * eta * np.linalg.norm(br)
 
 
+@pytest.mark.parametrize("nx,ny,lx", [(21, 13, 2 * np.pi), (12, 31, 2 * np.pi), (1024, 3, 1024.0)])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_preconditioned_fft_lengths(mb4, nx, ny, lx, precision):
+    """The preconditioner's FFTs on sides of mixed radix (21 = 3 x 7, 12 = 4 x 3), prime
+    (13, 31, 3) and the largest (1024 = 4^5, on a domain of length 1024 so that the oracle's
+    unpreconditioned solves stay cheap): preconditioned steps on a 5-point Laplacian with a
+    disorder potential match the oracle."""
+    tx, ty, e0 = inputs.paper_laplacian_hopping(nx, ny, lx=lx)
+    rng = np.random.default_rng(nx * 7 + ny)
+    V = rng.uniform(-1.0, 1.0, nx * ny)
+    u0 = inputs.paper_initial_state(nx, ny) * 0.5
+    h, steps = 0.002, 3
+    prob = orc.Problem(nx, ny, V, -GAMMA, tx=tx, ty=ty, eps0=e0)
+    u = u0.copy()
+    for _ in range(steps):
+        u = orc.step(prob, u, h)
+    with mb4.Integrator(nx, ny, V, -GAMMA, h, precision=precision, precondition=1, newton_rtol=RTOL,
+                        tx=tx, ty=ty, onsite=e0) as it:
+        it.set_state(u0)
+        it.step(steps)
+        assert _rel(it.get_state(), u) <= 1e-11
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_paper_setup_32_matches_oracle(mb4, precision):
     n, steps = 32, 10
