@@ -214,6 +214,39 @@ def test_step_matches_brute_force_root(field):
     assert np.max(np.abs(Ub - U_orc)) <= 1e-13 * np.max(np.abs(u0))
 
 
+def test_quadrature_below_six_nodes_breaks_energy_preservation():
+    """Negative control for the exact integration of the cubic term (Sec. 2.2): the stage
+    integrand has degree 11 in zeta, so Gauss rules of 6 nodes integrate it exactly and of
+    5 or 3 nodes (exact to degrees 9 and 5) do not.  Stages from the brute-force residual
+    with each rule, solved by MINPACK on a 3x3 grid over 10 steps: 6 nodes keep H to the
+    root finder's accuracy, 5 and 3 nodes lose it by orders of magnitude."""
+    rng = np.random.default_rng(31)
+    nx, ny = 3, 3
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    chi, tx, ty, eps0, h = 2.0, 1.0, 0.9, 0.2, 0.1
+    u0 = _rand_state(rng, S, 0.8)
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    drift = {}
+    for nq in (6, 5, 3):
+        u = u0.copy()
+        H0 = orc.energy(prob, u)[0]
+        d = 0.0
+        for _ in range(10):
+            def F(x, u=u):
+                U = (x[:3 * S] + 1j * x[3 * S:]).reshape(3, S)
+                P = brute_phi(nx, ny, V, chi, tx, ty, eps0, u, U, h, nq=nq)
+                return np.concatenate([P.real.ravel(), P.imag.ravel()])
+            U0 = np.tile(u, 3)
+            sol = scipy.optimize.root(F, np.concatenate([U0.real, U0.imag]), method="hybr", tol=1e-15)
+            assert np.max(np.abs(F(sol.x))) < 1e-12
+            u = sol.x[2 * S:3 * S] + 1j * sol.x[5 * S:6 * S]
+            d = max(d, abs(orc.energy(prob, u)[0] - H0) / abs(H0))
+        drift[nq] = d
+    assert drift[6] <= 1e-12, drift
+    assert drift[5] >= 1e-6 and drift[3] >= 1e-6, drift
+
+
 def _stability_function():
     """R(z) of MB4 from the continuous stage equation (eq. MB4_1) for u' = lambda u,
     u0 = 1: U_tau is a cubic in tau; equating coefficients gives R(z) = U_1
