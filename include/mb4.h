@@ -385,11 +385,14 @@ int mb4_server_create(long long hbm_budget_bytes, int max_slots, int keep_states
 void mb4_server_destroy(mb4_server* s);
 
 /* Queue a request; *id receives its index (0, 1, ...).  MB4_ERR_ADMISSION_REJECTED
- * if a single instance of its class cannot fit the budget at all. */
+ * if a single instance of its class cannot fit the budget at all; MB4_ERR_INVALID_ARG
+ * for a bad grid, h, chi or step count, or a non-finite v, re or im. */
 int mb4_server_submit(mb4_server* s, const mb4_request* req, long long* id);
 
 /* Run the serving loop until every submitted request is done or the server clock
- * reaches `until` seconds; *n_done (nullable) receives the number done so far. */
+ * reaches `until` seconds; *n_done (nullable) receives the number done so far.  A
+ * request that its class batch refuses at admission (mb4_batch_load) is done with that
+ * status and no steps; the others go on. */
 int mb4_server_run(mb4_server* s, double until, long long* n_done);
 
 /* Result of request id; re/im (nullable, S doubles each, host) receive the final

@@ -197,6 +197,8 @@ int mb4_server_submit(mb4_server* s, const mb4_request* q, long long* id) {
   r.nsteps = q->nsteps;
   r.arrival = q->arrival;
   const size_t S = (size_t)g.nx * g.ny;
+  for (size_t k = 0; k < S; ++k)
+    if (!std::isfinite(q->v[k]) || !std::isfinite(q->re[k]) || !std::isfinite(q->im[k])) return MB4_ERR_INVALID_ARG;
   r.v.assign(q->v, q->v + S);
   r.re.assign(q->re, q->re + S);
   r.im.assign(q->im, q->im + S);
@@ -252,6 +254,15 @@ int mb4_server_run(mb4_server* s, double until, long long* n_done) {
         continue;
       }
       int rc = mb4_batch_load(c->b, slot, r.v.data(), r.chi, r.re.data(), r.im.data(), 0);
+      if (rc == MB4_ERR_INVALID_ARG) {           // this request's inputs do not fit its class: it fails alone
+        r.res.status = rc;
+        r.res.done = 1;
+        r.res.admitted = r.res.completed = s->now();
+        r.queued = false;
+        s->n_done += 1;
+        it = s->queue.erase(it);
+        continue;
+      }
       if (rc != MB4_OK) return rc;
       c->slot_req[slot] = *it;
       c->running += 1;

@@ -123,3 +123,28 @@ def test_request_larger_than_budget_is_rejected(mb4):
         with pytest.raises(mb4.MB4Error) as e:
             srv.submit(64, 64, V, 1.0, psi, 0.01, 10)
         assert e.value.code == mb4.MB4_ERR_ADMISSION_REJECTED
+
+
+def test_request_outside_its_class_fails_alone(mb4):
+    """In an FP64 server the Krylov basis of a class is scaled by its x hopping, so a
+    potential whose Gershgorin bound exceeds 4096 |tx| cannot join the class: that request
+    ends with MB4_ERR_INVALID_ARG while the others run to completion.  Non-finite inputs
+    are refused at submission."""
+    reqs = _trace(3, seed=5, span=0.0)
+    bad = dict(reqs[1])
+    bad["V"] = bad["V"].copy()
+    bad["V"][3] = 1.0e4
+    reqs[1] = bad
+    with mb4.Server(1 << 30, max_slots=4, keep_states=True, precision="fp64") as srv:
+        ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], q["arrival"])
+               for q in reqs]
+        nan_psi = reqs[0]["psi"].copy()
+        nan_psi[0] = np.nan
+        with pytest.raises(mb4.MB4Error) as e:
+            srv.submit(reqs[0]["nx"], reqs[0]["ny"], reqs[0]["V"], 1.0, nan_psi, 0.01, 3)
+        assert e.value.code == mb4.MB4_ERR_INVALID_ARG
+        assert srv.run() == 3
+        res = [srv.result(i) for i in ids]
+    assert res[1]["done"] == 1 and res[1]["status"] == mb4.MB4_ERR_INVALID_ARG and res[1]["steps_done"] == 0
+    for k in (0, 2):
+        assert res[k]["status"] == mb4.MB4_OK and res[k]["steps_done"] == reqs[k]["nsteps"]
