@@ -300,7 +300,6 @@ int ensure_scratch(mb4_batch* c) {
   return MB4_OK;
 }
 
-// Bring n (re, im) doubles onto the device, planar; host data is staged through c->io.
 // The device address of a host buffer that is page-locked and mapped (cudaHostAlloc,
 // cudaMallocHost, or cudaHostRegister with mapping: with unified addressing every
 // page-locked buffer is), else null.  Kernels then read or write such a buffer in
@@ -315,6 +314,8 @@ T* mapped_host(T* p) {
   return (a.type == cudaMemoryTypeHost && a.devicePointer) ? static_cast<T*>(a.devicePointer) : nullptr;
 }
 
+// Bring n (re, im) doubles onto the device, planar: device and mapped host buffers are
+// used in place, other host data is staged through c->io.
 int stage_in(mb4_batch* c, const double* re, const double* im, size_t n, int on_device, const double** dre,
              const double** dim) {
   if (on_device) {
@@ -336,6 +337,8 @@ int stage_in(mb4_batch* c, const double* re, const double* im, size_t n, int on_
   return MB4_OK;
 }
 
+// Unpack n complex values to (re, im) and synchronise: device and mapped host buffers are
+// written in place, other host buffers through c->io.
 int stage_out(mb4_batch* c, const double2* z, double* re, double* im, size_t n, int on_device) {
   if (on_device) {
     launch_unpack(z, re, im, n, c->stream);
