@@ -589,7 +589,6 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(dalloc(c, (void**)&d.coef, (size_t)B * 3 * kMaxS * sizeof(double)));
   MB4_CHECK(dalloc(c, (void**)&d.obs_part, (size_t)B * obs_blocks_per_instance(B) * 12 * sizeof(double)));
   MB4_CHECK(dalloc(c, (void**)&d.obs_out, (size_t)B * 6 * sizeof(double)));
-  MB4_CHECK(dalloc(c, (void**)&d.changed, (size_t)B * sizeof(int)));
   MB4_CHECK(dalloc(c, (void**)&d.ic, (size_t)B * sizeof(InstConst)));
   MB4_CHECK(dalloc(c, (void**)&d.is, (size_t)B * sizeof(InstStatus)));
   MB4_CHECK(dalloc(c, (void**)&d.bc, sizeof(BatchCtl)));

@@ -106,7 +106,6 @@ struct InstStatus {
   int active;                        // still iterating in the current step
   int newton_iter;                   // iterations of the current step
   int nonfinite;                     // set by update kernels
-  int cont;
   int last_newton_iters;
   unsigned int u0max_bits;           // ||u0||_inf of the current step (float bits, >= 0)
   unsigned int ticket_gram[3];       // last-block tickets, one per shifted system (reset by the last block)
@@ -146,7 +145,6 @@ struct DevBuffers {
   double* coef;      // B*3*kMaxS least-squares coefficients
   double* obs_part;  // observables partial sums
   double* obs_out;   // B*6
-  int* changed;      // B flags: set_state changed the instance's state
   double* chi;       // per-site chi, B*S (chi_field only)
   // spectral preconditioner (precond only): z_a = P v_a (layout of v), a DFT work plane
   // triple per instance, twiddles along x and y, per-mode inverse multipliers B*3*S (TK2)

@@ -905,7 +905,6 @@ __global__ void k_newton_test(StepParams p, InstStatus* is, BatchCtl* bc, cudaGr
     I.prev_rmax = r;
     I.last_newton_iters = it + 1;
     I.rmax_bits = 0ull;
-    I.cont = cont;
     if (!cont) I.active = 0;
     any |= cont;
   }
@@ -1032,42 +1031,43 @@ __global__ void k_arm(int B, int pred_order, InstStatus* is, BatchCtl* bc) {
   I.predicted = go && pred_order > 0 && I.pred_count > 0 && I.next_predicted;
 }
 
-// set_state: pack (re, im) into the state and flag the instances whose state changes
-// (bitwise); those forget their Newton-start history, which no longer fits.
+// Forget the Newton-start history of an instance (it no longer fits the state).  Every
+// writer stores the same zeros, so concurrent writers need no ordering.
+__device__ __forceinline__ void forget_history(InstStatus& I) {
+  I.pred_count = 0;
+  I.start_known = 0;
+  I.explore_in = 0;
+}
+
+// set_state: pack (re, im) into the state; an instance whose state changes (any bit)
+// forgets its Newton-start history.
 __global__ void k_set_state(const double* __restrict__ re, const double* __restrict__ im, double2* __restrict__ z,
-                            size_t n, int S, int* changed) {
+                            size_t n, int S, InstStatus* is) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double2 old = z[k];
   const double2 v = make_double2(re[k], im[k]);
   z[k] = v;
   if (dbits(old.x) != dbits(v.x) || dbits(old.y) != dbits(v.y)) {
-    int* f = changed + k / (size_t)S;
-    if (!*(volatile int*)f) atomicOr(f, 1);
+    InstStatus& I = is[k / (size_t)S];
+    if (*(volatile int*)&I.pred_count || *(volatile int*)&I.start_known) forget_history(I);
   }
 }
 
-__global__ void k_forget_changed(const int* __restrict__ changed, InstStatus* is, int ninst) {
+__global__ void k_forget_range(InstStatus* is, int ninst) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < ninst && changed[b]) {
-    is[b].pred_count = 0;
-    is[b].start_known = 0;
-    is[b].explore_in = 0;
-  }
+  if (b < ninst) forget_history(is[b]);
 }
 
 void launch_forget_range(const StepParams& p, const DevBuffers& b, int first, int ninst, cudaStream_t s) {
-  cudaMemsetAsync(b.changed + first, 0x01, (size_t)ninst * sizeof(int), s);   // nonzero flags
-  k_forget_changed<<<(ninst + 255) / 256, 256, 0, s>>>(b.changed + first, b.is + first, ninst);
+  k_forget_range<<<(ninst + 255) / 256, 256, 0, s>>>(b.is + first, ninst);
 }
 
 void launch_set_state(const StepParams& p, const DevBuffers& b, const double* re, const double* im, int first,
                       int ninst, cudaStream_t s) {
   const size_t n = (size_t)ninst * p.S;
-  cudaMemsetAsync(b.changed + first, 0, (size_t)ninst * sizeof(int), s);
   if (n) k_set_state<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(re, im, b.u + (size_t)first * p.S, n, p.S,
-                                                                  b.changed + first);
-  k_forget_changed<<<(ninst + 255) / 256, 256, 0, s>>>(b.changed + first, b.is + first, ninst);
+                                                                  b.is + first);
 }
 
 void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t s) {

@@ -535,13 +535,21 @@ def test_grid512_translation_equivariance(mb4):
 
 def test_grid2048_mixed_matches_fp64(mb4):
     """2048x2048 (W = 2, 1% defects, chi = 2, h = 0.002): FP32 inner solves do not
-    move the root -- mixed and FP64 agree to the parity tolerance after 3 steps."""
+    move the root -- mixed and FP64 agree to the parity tolerance after 3 steps, and in
+    both the third step's stages satisfy the oracle's Phi(U) = 0 at sampled sites."""
     w = inputs.grid2048_mixed()
+    V = w.potential()
     finals = {}
     for precision in PRECISIONS:
         with mb4.from_workload(w, precision=precision) as it:
             H0 = it.energy()[0]
-            it.step(3)
+            it.step(2)
+            u0 = it.get_state()
+            it.step(1)
+            U = it.stages()
+            sites = _sample_sites(w, 300, 7)
+            phi = orc.residual_at_sites(w.nx, w.ny, V, w.chi, w.tx, w.ty, w.eps0, u0, U, w.h, sites)
+            assert np.max(np.abs(phi)) <= 1e-13 * np.max(np.abs(u0)), np.max(np.abs(phi))
             finals[precision] = it.get_state()
             assert abs(it.energy()[0] - H0) <= 1e-13 * abs(H0)
     assert _rel(finals["mixed"], finals["fp64"]) <= 1e-11
