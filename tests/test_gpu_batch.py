@@ -164,14 +164,15 @@ def test_ensemble_1024_grid128_full_size(mb4):
     assert _rel(got[5], u) <= 1e-11
 
 
-def test_batch_with_chi_field_and_preconditioner_matches_solo(mb4):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_batch_with_chi_field_and_preconditioner_matches_solo(mb4, precision):
     """Per-instance chi fields and the spectral preconditioner in a batch: each
     instance equals its own run."""
     nx, ny, B, h, steps = 24, 20, 3, 0.01, 6
     V, chi, psi = _problems(nx, ny, B, seed0=21)
     rng = np.random.default_rng(22)
     fields = rng.uniform(-2.0, 2.0, (B, nx * ny))
-    with mb4.Batch(nx, ny, V, chi, h, precision="mixed", site_chi=True, precondition=1) as bt:
+    with mb4.Batch(nx, ny, V, chi, h, precision=precision, site_chi=True, precondition=1) as bt:
         for b in range(B):
             bt.set_chi_field(b, fields[b])
         bt.set_state(psi)
@@ -179,7 +180,7 @@ def test_batch_with_chi_field_and_preconditioner_matches_solo(mb4):
         got = bt.get_state()
     assert codes == [0] * B
     for b in range(B):
-        with mb4.Integrator(nx, ny, V[b], chi[b], h, precision="mixed", site_chi=True, precondition=1) as it:
+        with mb4.Integrator(nx, ny, V[b], chi[b], h, precision=precision, site_chi=True, precondition=1) as it:
             it.set_chi_field(fields[b])
             it.set_state(psi[b])
             it.step(steps)
