@@ -247,8 +247,9 @@ def run_ours(args):
             "newton_per_step": newton / K, "energy_drift": drift,
             "norm_drift": abs(o1["norm2"] - o0["norm2"]), "krylov_s": s_dim,
             # per step: arm, setup, accept; per Newton iteration: residual, s basis
-            # launches (one matrix-powers launch in mixed mode), Gram, update, loop test;
-            # 2 per log
+            # launches (one matrix-powers launch in mixed mode), Gram, update, loop test
+            # (a step graph always runs its first two iterations, and every step here
+            # takes at least two); 2 per log
             "launches": K * 3 + newton * ((s_dim if precision.startswith("fp64") else 1) + 4) + 2 * obs_calls,
             "obs_calls": obs_calls,
         }

@@ -234,8 +234,8 @@ void enqueue_setup(mb4_batch* c, cudaStream_t s) {
   else launch_setup<double>(c->p, c->b, s);
 }
 
-// One MB4 step as a graph: setup -> WHILE(any instance continues){residual, basis, gram+lsq,
-// update+test} -> accept.
+// One MB4 step as a graph: setup -> kUnrolledNewton x {residual, basis, gram+lsq, update,
+// test} -> WHILE(any instance continues){the same} -> accept.
 int build_graph(mb4_batch* c) {
   cudaStream_t cap;
   MB4_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -254,6 +254,14 @@ int build_graph(mb4_batch* c) {
     }
     cudaGraphConditionalHandle h;
     if ((rc = cuda_rc(cudaGraphConditionalHandleCreate(&h, capg, 1, cudaGraphCondAssignDefault))) != MB4_OK) {
+      cudaStreamEndCapture(cap, &g);
+      break;
+    }
+    // The first Newton iterations are unrolled into the step graph, so their kernels chain by
+    // programmatic dependent launch; their loop tests set the WHILE node's condition.  An
+    // instance that has already converged makes them no-ops (every kernel skips it).
+    for (int u = 0; u < kUnrolledNewton; ++u) enqueue_body(c, cap, (unsigned long long)h, 1);
+    if ((rc = cuda_rc(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &capg, &deps, nullptr, &ndeps))) != MB4_OK) {
       cudaStreamEndCapture(cap, &g);
       break;
     }

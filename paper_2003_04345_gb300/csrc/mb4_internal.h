@@ -17,6 +17,7 @@ constexpr int kGramCluster = 8;    // thread-block cluster size of the Gram redu
 constexpr int kObsBlocksTotal = 152;   // observables: blocks over the whole batch
 constexpr int kObsBlocksMax = 152;     // ... and per instance, at most
 constexpr double kUnitGrowthMax = 4096.0;   // mv_unit: largest Gershgorin bound / |tx| accepted
+constexpr int kUnrolledNewton = 2;  // Newton iterations of a step graph before its WHILE node
 constexpr int kMaxFftStages = 12;  // radices of one FFT length <= MB4_MAX_PRECOND_SIDE (1024 = 4^5)
 
 // MB4 constants in FP64, computed on the host (mb4_consts.cpp).

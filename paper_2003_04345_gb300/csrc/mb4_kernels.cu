@@ -238,8 +238,10 @@ void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, 
   const long long os = (long long)(p.s + 1) * 3 * p.S;
   const int sf = skip_first ? 1 : 0;
   const double* D = p.kin_unit ? b.dtx : b.d;
-#define MB4_RES(CF, KM) \
-  k_residual<TK, CF, KM><<<grid, p.bs_residual, 0, s>>>(p, b.u, D, b.S0, b.Ubar, (TK2*)b.v, os, sf, b.chi, b.ic, b.is)
+#define MB4_RES(CF, KM)                                                                                     \
+  launch_k(p.pdl != 0, k_residual<TK, CF, KM>, grid, dim3(p.bs_residual), 0, s, p, (const double2*)b.u, D,     \
+           (const double2*)b.S0, (const double2*)b.Ubar, (TK2*)b.v, os, sf, (const double*)b.chi,               \
+           (const InstConst*)b.ic, (const InstStatus*)b.is)
   switch (kin_mode(p)) {
     case 2: if (p.chi_field) MB4_RES(true, 2); else MB4_RES(false, 2); break;
     case 1: if (p.chi_field) MB4_RES(true, 1); else MB4_RES(false, 1); break;
