@@ -584,6 +584,60 @@ def profile_case(precision):
     print(json.dumps({"profile_case": precision, "newton_iters_last": st["newton_iters_last"]}))
 
 
+def full_runs():
+    """The 2048x2048 configuration (500 steps) and the 1024-member 128x128 ensemble (2000
+    steps) over their whole stated step counts, in both precisions: the largest relative
+    energy drift over each run (H read every 10 and every 100 steps), Newton iterations per
+    step and wall time; for 2048x2048 also mixed against FP64 at the end.  Prints one JSON
+    line; a validation run, not a bench line."""
+    import numpy as np
+    import torch
+    from paper_2003_04345_gb300 import inputs, mb4
+    out = {}
+    w = inputs.grid2048_mixed()
+    res, finals = {}, {}
+    for precision in ("mixed", "fp64"):
+        with mb4.from_workload(w, precision=precision, stream=torch.cuda.current_stream()) as it:
+            H0 = it.energy()[0]
+            drift, newton = 0.0, 0
+            t0 = time.perf_counter()
+            for _ in range(w.steps // 10):
+                newton += it.step(10)["newton_iters_total"]
+                drift = max(drift, abs(it.energy()[0] - H0) / abs(H0))
+            wall = time.perf_counter() - t0
+            finals[precision] = it.get_state()
+        res[precision] = {"steps": w.steps, "energy_drift_max": drift, "newton_per_step": newton / w.steps,
+                          "wall_s": wall}
+    a, b = finals["mixed"], finals["fp64"]
+    res["mixed_vs_fp64_rel_linf"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    out["grid2048_mixed"] = res
+    B, n = 1024, 128
+    ws = [inputs.ensemble128(seed) for seed in range(B)]
+    V = np.stack([x.potential() for x in ws])
+    chi = np.array([x.chi for x in ws])
+    psi = np.stack([x.psi0() for x in ws])
+    steps = ws[0].steps
+    res = {}
+    for precision in ("mixed", "fp64"):
+        with mb4.Batch(n, n, V, chi, ws[0].h, precision=precision, stream=torch.cuda.current_stream()) as bt:
+            bt.set_state(psi)
+            H0 = bt.observables()[:, 0]
+            drift, newton = 0.0, 0
+            t0 = time.perf_counter()
+            for _ in range(steps // 100):
+                stats, codes = bt.step(100)
+                if any(codes):
+                    raise RuntimeError(f"ensemble step failed: {sorted(set(codes))}")
+                newton += sum(st["newton_iters_total"] for st in stats)
+                H = bt.observables()[:, 0]
+                drift = max(drift, float(np.max(np.abs(H - H0) / np.abs(H0))))
+            wall = time.perf_counter() - t0
+        res[precision] = {"members": B, "steps": steps, "energy_drift_max": drift,
+                          "newton_per_member_step": newton / (B * steps), "wall_s": wall}
+    out["ensemble1024_grid128"] = res
+    print(json.dumps({"full_runs": out}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,9 +650,15 @@ def main():
                     help="run 6 host-driven steps of the 512x512 workload for ncu and exit")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the ensemble, 2048^2 and served-stream lines")
+    ap.add_argument("--full-runs", action="store_true",
+                    help="run the 2048^2 and ensemble configurations over their whole step counts "
+                         "(energy drift, Newton counts) and exit")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.full_runs:
+        full_runs()
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
