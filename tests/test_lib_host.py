@@ -85,3 +85,49 @@ def test_create_fails_loudly_without_gpu(mb4):
 def test_status_strings(mb4):
     assert mb4.status_string(0) == "ok"
     assert "Newton" in mb4.status_string(mb4.MB4_ERR_NEWTON_NOT_CONVERGED)
+
+
+def _build_c_demo(tmp_path):
+    """Compile tests/c/abi_demo.c with the host C compiler against include/mb4.h and
+    the in-tree libmb4.so (found at run time through its rpath)."""
+    import shutil
+    import subprocess
+    from paper_2003_04345_gb300 import mb4 as m
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.dirname(m.LIB_PATH)
+    exe = str(tmp_path / "abi_demo")
+    subprocess.run([cc, "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_demo.c"), "-o", exe, "-L", lib_dir, "-lmb4",
+                    f"-Wl,-rpath,{lib_dir}", "-lm"], check=True)
+    return exe
+
+
+def test_c_program_uses_the_abi_and_fails_loudly_without_gpu(mb4, tmp_path):
+    """A plain C program compiles against include/mb4.h, links libmb4.so and, with no
+    GPU, gets MB4_ERR_CUDA from mb4_create (exit status 3): no CPU fallback."""
+    import subprocess
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present: the GPU test runs the program")
+    except ImportError:
+        pass
+    exe = _build_c_demo(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 3, (r.returncode, r.stdout, r.stderr)
+    assert "mb4_create" in r.stdout
+
+
+@pytest.mark.gpu
+def test_c_program_steps_and_conserves_energy(mb4, tmp_path):
+    """The same C program on a GPU: 100 steps, |dH/H| <= 1e-13 (exit status 0)."""
+    import subprocess
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    exe = _build_c_demo(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "steps 100" in r.stdout
