@@ -168,6 +168,33 @@ def test_residual_matches_brute_force_quadrature(nx, ny, chi, eps0):
     assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(U))
 
 
+def test_residual_matches_brute_force_quadrature_random_cases():
+    """Property form of the pin above: random grid shapes (3..6 per side), hoppings of
+    either sign, on-site shifts, chi (scalar or per site), step sizes and states; the
+    oracle's exact-coefficient residual equals the 20-point brute-force quadrature of
+    eq. (MB4_3) to rounding."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=25, deadline=None, derandomize=True)
+    @hyp.given(nx=st.integers(3, 6), ny=st.integers(3, 6), tx=st.floats(-2, 2), ty=st.floats(-2, 2),
+               eps0=st.floats(-1, 1), chi=st.floats(-3, 3), field=st.booleans(), h=st.floats(0.001, 0.1),
+               seed=st.integers(0, 2 ** 31 - 1))
+    def check(nx, ny, tx, ty, eps0, chi, field, h, seed):
+        rng = np.random.default_rng(seed)
+        S = nx * ny
+        V = rng.uniform(-2, 2, S)
+        c = rng.uniform(-3, 3, S) if field else chi
+        prob = orc.Problem(nx, ny, V, c, tx=tx, ty=ty, eps0=eps0)
+        u0 = _rand_state(rng, S)
+        U = u0[None, :] + 0.2 * np.vstack([_rand_state(rng, S) for _ in range(3)])
+        got = orc.residual(prob, u0, U, h)
+        want = brute_phi(nx, ny, V, c, tx, ty, eps0, u0, U, h)
+        assert np.max(np.abs(got - want)) <= 1e-13 * max(1.0, np.max(np.abs(U)) ** 3)
+
+    check()
+
+
 def test_residual_at_sites_matches_full_residual():
     rng = np.random.default_rng(3)
     nx, ny = 7, 5
