@@ -400,10 +400,11 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
   const size_t tk = (o.precision == MB4_MIXED) ? 4 : 8;
   const int nent = (o.krylov_s + 1) * (o.krylov_s + 2) / 2;
   size_t t = 0;
-  t += round256(BS * 16) + 2 * round256(BS * 8) + round256(BS * 16) + round256(3 * BS * 16);
+  // u, V, onsite + V, D/tx (grids with tx != 0; counted always), (K+V) u0, dU
+  t += round256(BS * 16) + 3 * round256(BS * 8) + round256(BS * 16) + round256(3 * BS * 16);
   t += round256(BS * 4 * tk) + round256((size_t)(o.krylov_s + 1) * 3 * BS * 2 * tk);
   t += round256((size_t)B * 3 * kGramCap * nent * 8) + round256((size_t)B * 3 * kMaxS * 8);
-  t += round256((size_t)B * kObsBlocksMax * 12 * 8) + round256((size_t)B * 6 * 8) + round256((size_t)B * 4);
+  t += round256((size_t)B * kObsBlocksMax * 12 * 8) + round256((size_t)B * 6 * 8);
   t += round256(B * sizeof(InstConst)) + round256(B * sizeof(InstStatus)) + round256(sizeof(BatchCtl));
   t += 2 * round256(3 * S * 16) + round256(6 * std::max(BS, S) * 8);   // I/O scratch
   if (o.newton_start > 0) t += round256((size_t)o.newton_start * 3 * BS * 16);

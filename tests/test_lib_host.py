@@ -131,3 +131,17 @@ def test_c_program_steps_and_conserves_energy(mb4, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert "steps 100" in r.stdout
+
+
+def test_batch_bytes_counts_the_planes_a_batch_allocates(mb4):
+    """mb4_batch_bytes (host arithmetic, no GPU): at least the per-site planes a batch
+    allocates -- u 16, V 8, onsite+V 8, D/tx 8, (K+V)u0 16, dU 48, J 4 tk, basis
+    (s+1) 6 tk, two history steps 96 -- linear in the batch, and smaller in mixed mode."""
+    S = 512 * 512
+    for precision, tk in (("fp64", 8), ("mixed", 4)):
+        per_site = 16 + 8 + 8 + 8 + 16 + 48 + 4 * tk + 5 * 6 * tk + 96
+        one = mb4.batch_bytes(512, 512, 1, precision=precision)
+        assert one >= per_site * S
+        assert mb4.batch_bytes(512, 512, 4, precision=precision) >= 4 * per_site * S
+    assert mb4.batch_bytes(512, 512, 1, precision="mixed") < mb4.batch_bytes(512, 512, 1, precision="fp64")
+    assert mb4.batch_bytes(2, 512, 1) == -1
