@@ -149,6 +149,39 @@ def test_energy_without_the_half(monkeypatch):
     assert _fails(pins.test_energy_preserved_grid16)
 
 
+def test_kinetic_and_potential_energy_swapped(monkeypatch):
+    """energy() returning U_E in the place of U_K and U_K in the place of U_E (their
+    sum, H, unchanged -- so energy conservation alone cannot see it)."""
+    good = orc.energy
+
+    def bad(prob, u):
+        H, UK, UE, UI = good(prob, u)
+        return H, UE, UK, UI
+    monkeypatch.setattr(orc, "energy", bad)
+    assert _fails(pins.test_energy_preserved_grid16) is False      # H is still conserved
+    assert _fails(pins.test_observables_of_a_plane_wave, False)
+    assert _fails(pins.test_observables_of_a_site_state)
+
+
+def test_participation_with_the_wrong_power(monkeypatch):
+    """p = sum |u|^2 (the norm) instead of sum |u|^4 (Sec. 3.2)."""
+    monkeypatch.setattr(orc, "participation", lambda u: orc.norm2(u))
+    assert _fails(pins.test_participation_ratio_of_spread_states)
+    assert _fails(pins.test_observables_of_a_plane_wave, True)
+
+
+def test_factor_moved_between_energy_parts(monkeypatch):
+    """A factor moved from U_I to U_E (chi/2 |u|^4 counted with the potential term),
+    again with H unchanged."""
+    good = orc.energy
+
+    def bad(prob, u):
+        H, UK, UE, UI = good(prob, u)
+        return H, UK, UE + UI, 0.0
+    monkeypatch.setattr(orc, "energy", bad)
+    assert _fails(pins.test_observables_of_a_site_state)
+
+
 def test_unmutated_oracle_passes_the_same_pins():
     """The control: with the oracle as it stands, every pin used above passes."""
     pins.test_E_row_sums_are_the_nodes()
@@ -159,4 +192,8 @@ def test_unmutated_oracle_passes_the_same_pins():
     pins.test_step_matches_brute_force_root(False)
     pins.test_energy_preserved_grid16()
     pins.test_linear_step_equals_stability_function()
+    pins.test_observables_of_a_plane_wave(False)
+    pins.test_observables_of_a_plane_wave(True)
+    pins.test_observables_of_a_site_state()
+    pins.test_participation_ratio_of_spread_states()
     assert Fraction(orc.C_PAPER[2]) == 1

@@ -563,3 +563,108 @@ def test_oracle_linear_solvers_agree():
     ul, _ = orc.run(prob, u0, w.h, 3, solver="lu")
     ug, _ = orc.run(prob, u0, w.h, 3, solver="gmres")
     assert np.max(np.abs(ul - ug)) <= 1e-15 * np.max(np.abs(ul))
+
+
+# ---------------------------------------------------------------------------
+# Observables: the split of H into U_K, U_E, U_I (Sec. 2.1, eq. U_K .. U_E) and the
+# participation ratio p = sum |u|^4 (Sec. 3.2), pinned by closed forms, by special
+# states and by an independent Fourier route -- not by the oracle's own formulas.
+# ---------------------------------------------------------------------------
+def _plane_wave(nx, ny, mx, my, a):
+    kx, ky = 2 * math.pi * mx / nx, 2 * math.pi * my / ny
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    return (a * np.exp(1j * (kx * x + ky * y))).ravel(), kx, ky
+
+
+@pytest.mark.parametrize("field", [False, True])
+def test_observables_of_a_plane_wave(field):
+    """psi = a exp(i k.x) is an eigenvector of the 5-point K with eigenvalue
+    eps0 - 2 tx cos kx - 2 ty cos ky, and |psi|^2 = |a|^2 at every site, so
+    U_K = S |a|^2 (eps0 - 2 tx cos kx - 2 ty cos ky), U_E = |a|^2 sum_k V_k (for any V),
+    U_I = (|a|^4 / 2) sum_k chi_k, sum |u|^2 = S |a|^2 and p = S |a|^4."""
+    rng = np.random.default_rng(71)
+    nx, ny = 7, 5
+    S = nx * ny
+    tx, ty, eps0 = 1.3, -0.6, 0.45
+    V = rng.uniform(-2, 3, S)
+    chi = _chi_field(S, 72) if field else 1.7
+    chis = np.broadcast_to(chi, (S,))
+    a = 0.37 * np.exp(0.8j)
+    u, kx, ky = _plane_wave(nx, ny, 2, 3, a)
+    prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=eps0)
+    H, UK, UE, UI = orc.energy(prob, u)
+    A2 = abs(a) ** 2
+    want_K = S * A2 * (eps0 - 2 * tx * math.cos(kx) - 2 * ty * math.cos(ky))
+    want_E = A2 * math.fsum(V.tolist())
+    want_I = 0.5 * A2 * A2 * math.fsum(chis.tolist())
+    for got, want in ((UK, want_K), (UE, want_E), (UI, want_I), (H, want_K + want_E + want_I)):
+        assert abs(got - want) <= 1e-14 * (abs(want_K) + abs(want_E) + abs(want_I)), (got, want)
+    assert abs(orc.norm2(u) - S * A2) <= 1e-15 * S * A2
+    assert abs(orc.participation(u) - S * A2 * A2) <= 1e-15 * S * A2 * A2
+
+
+def test_kinetic_energy_by_parseval():
+    """The 5-point K is diagonal in Fourier space, so for ANY state
+    U_K = (1/S) sum_m eps_m |uhat_m|^2 with uhat the 2D DFT of u and
+    eps_m = eps0 - 2 tx cos(2 pi mx / nx) - 2 ty cos(2 pi my / ny); likewise
+    sum |u|^2 = (1/S) sum |uhat|^2 (Parseval).  A route through numpy's FFT that
+    shares nothing with the oracle's sparse K."""
+    rng = np.random.default_rng(73)
+    nx, ny = 9, 6
+    S = nx * ny
+    tx, ty, eps0 = 0.8, 1.9, -0.3
+    V = rng.uniform(-1, 1, S)
+    u = _rand_state(rng, S, 0.3)
+    prob = orc.Problem(nx, ny, V, 1.1, tx=tx, ty=ty, eps0=eps0)
+    uh = np.fft.fft2(u.reshape(ny, nx))
+    mx = np.arange(nx)[None, :]
+    my = np.arange(ny)[:, None]
+    eps = eps0 - 2 * tx * np.cos(2 * math.pi * mx / nx) - 2 * ty * np.cos(2 * math.pi * my / ny)
+    want_K = float(np.sum(eps * np.abs(uh) ** 2)) / S
+    _, UK, _, _ = orc.energy(prob, u)
+    assert abs(UK - want_K) <= 1e-13 * float(np.sum(np.abs(eps) * np.abs(uh) ** 2)) / S
+    assert abs(orc.norm2(u) - float(np.sum(np.abs(uh) ** 2)) / S) <= 1e-13 * orc.norm2(u)
+
+
+def test_observables_of_a_site_state():
+    """u = c e_j (all weight on site j): U_K = eps0 |c|^2 (K's diagonal), U_E = V_j |c|^2,
+    U_I = (chi_j / 2) |c|^4, p = |c|^4 -- each term picks out its own coefficient, so a
+    term assigned to the wrong part, or a wrong power of |u|, changes the numbers."""
+    rng = np.random.default_rng(74)
+    nx, ny = 5, 4
+    S = nx * ny
+    V = rng.uniform(-3, 3, S)
+    chi = _chi_field(S, 75)
+    prob = orc.Problem(nx, ny, V, chi, tx=0.9, ty=1.4, eps0=0.65)
+    c = 0.6 - 0.5j
+    n = abs(c) ** 2
+    for j in (0, 7, S - 1):
+        u = np.zeros(S, dtype=np.complex128)
+        u[j] = c
+        H, UK, UE, UI = orc.energy(prob, u)
+        assert abs(UK - 0.65 * n) <= 1e-15
+        assert abs(UE - V[j] * n) <= 1e-15 * max(1.0, abs(V[j]))
+        assert abs(UI - 0.5 * chi[j] * n * n) <= 1e-15
+        assert abs(H - (0.65 + V[j]) * n - 0.5 * chi[j] * n * n) <= 1e-14
+        assert abs(orc.participation(u) - n * n) <= 1e-16
+        assert abs(orc.norm2(u) - n) <= 1e-16
+
+
+def test_participation_ratio_of_spread_states():
+    """Sec. 3.2: p = sum |u|^4 equals 1/(Nx Ny) for a normalised state of uniform
+    density (the paper's own value, 1e-4 on its 100 x 100 grid) and grows as the
+    state localises: 1/M for a normalised state spread evenly over M sites, 1 on one
+    site.  sum |u|^2 is 1 in every case, so p is not the norm."""
+    rng = np.random.default_rng(76)
+    nx = ny = 100
+    S = nx * ny
+    phase = np.exp(2j * math.pi * rng.uniform(size=S))
+    uniform = phase / math.sqrt(S)
+    assert abs(orc.participation(uniform) - 1e-4) <= 1e-17
+    for M in (1, 3, 250):
+        u = np.zeros(S, dtype=np.complex128)
+        sites = rng.choice(S, size=M, replace=False)
+        u[sites] = phase[sites] / math.sqrt(M)
+        assert abs(orc.norm2(u) - 1.0) <= 1e-15
+        assert abs(orc.participation(u) - 1.0 / M) <= 1e-15 / M
