@@ -36,6 +36,8 @@ UNIT = "site-steps/s"
 FP64_PEAK_DERIVED = 152 * 2070e6 * 2 * 2   # SMs x max SM clock x 2 DFMA/clk/SM x 2 flop (GB300, FP64)
 FP64_ISSUE_PEAK = 152 * 2070e6 * 2         # FP64 instructions (per thread) per second
 LOG_EVERY = 10
+HBM_GBS = 6792.4                   # replaced by MEASURED_PEAKS.json's figure in run_ours
+FP64_RATE = FP64_PEAK_DERIVED      # replaced by the FP64 rate measured in run_ours
 
 
 def _peaks():
@@ -47,29 +49,53 @@ def _peaks():
 
 
 # Algorithmic work per kernel launch, per site (flops: FMA = 2), and bytes per site.
-def kernel_model(kclass, precision, s):
+def kernel_model(kclass, precision, s, powers=True):
     """Algorithmic work of one launch per site: flops (FMA = 2), FP64 instructions
-    (DFMA, DADD and DMUL one each: what occupies the FP64 pipe) and bytes (each
-    array read or written once)."""
+    (DFMA, DADD and DMUL one each: what occupies the FP64 pipe) and bytes (each array
+    read or written once; neighbours counted once).  ``powers``: the FP32 basis is the
+    one-launch matrix-powers kernel (grid problems without preconditioning)."""
     tk = 8 if precision == "fp64" else 4
     ne = (s + 1) * (s + 2) // 2
     f64 = precision == "fp64"
     # FP64 instruction counts of the grid-stencil kernels with the x hopping factored
-    # out (the 512x512 workloads; ncu counts 102 DFMA + 12 DADD + 18 DMUL and 18 + 12 + 0)
-    if kclass == "residual":
+    # out (ncu counts 102 DFMA + 12 DADD + 18 DMUL and 18 + 12 + 0)
+    if kclass == "residual":   # u0, (K+V)u0, D/tx, dU in; b = -Phibar (level 0) out
         return {"flops": 240, "fp64_ops": 132, "bytes": 16 + 16 + 8 + 48 + 6 * tk, "fp64": True}
     if kclass == "matvec":
+        if not f64 and powers:  # J coefficients and level 0 in, levels 1..s out
+            return {"flops": 54 * s, "fp64_ops": 0, "bytes": 4 * tk + 6 * tk + s * 6 * tk, "fp64": False}
         return {"flops": 54, "fp64_ops": 30 if f64 else 0, "bytes": 6 * tk + 4 * tk + 6 * tk, "fp64": f64}
-    if kclass == "gram":   # Gram partial sums (+ the last block's reduction and least squares)
+    if kclass == "gram":       # all s+1 levels of the three systems in
         return {"flops": 3 * ne * 4, "fp64_ops": 3 * ne * 2 if f64 else 0, "bytes": (s + 1) * 6 * tk, "fp64": f64}
-    if kclass == "update":
+    if kclass == "update":     # s levels and dU in, dU out
         return {"flops": 3 * s * 4 + 6, "fp64_ops": 6 * (s + 1) if f64 else 6,
                 "bytes": s * 6 * tk + 48 + 48, "fp64": f64}
-    if kclass == "setup":
-        return {"flops": 40, "fp64_ops": 0, "bytes": 16 + 8 + 16 + 48 + 4 * tk + 6 * tk, "fp64": True}
-    if kclass == "accept":
-        return {"flops": 12, "fp64_ops": 0, "bytes": 48 + 16, "fp64": True}
+    if kclass == "setup":      # u, D in; (K+V)u0, J coefficients, level 0 out
+        return {"flops": 40, "fp64_ops": 0, "bytes": 16 + 8 + 16 + 4 * tk + 6 * tk, "fp64": True}
+    if kclass == "accept":     # u, dU in; u out (history shifts not counted)
+        return {"flops": 12, "fp64_ops": 0, "bytes": 48 + 16 + 16, "fp64": True}
     return {"flops": 0, "fp64_ops": 0, "bytes": 0, "fp64": False}
+
+
+def kernel_rooflines(prof, precision, s, sites, hbm_gbs, fp64_flops, powers=True):
+    """Per kernel class: microseconds per launch, algorithmic GB/s and its fraction of the
+    measured HBM copy bandwidth, and for FP64 kernels the FP64 flop rate and its fraction
+    of the measured FP64 FMA rate.  ``sites`` = sites one launch covers."""
+    out = {}
+    for k, (ms, n) in prof.items():
+        if not n:
+            continue
+        us = 1e3 * ms / n
+        m = kernel_model(k, precision, s, powers)
+        gbs = m["bytes"] * sites / (us * 1e-6) / 1e9
+        e = {"us_per_launch": us, "launches": n, "ms_total": ms, "bytes_per_site": m["bytes"],
+             "gb_s": gbs, "hbm_frac": gbs / hbm_gbs}
+        if m["fp64"] and m["fp64_ops"]:
+            tf = m["flops"] * sites / (us * 1e-6)
+            e["fp64_tflops"] = tf / 1e12
+            e["fp64_frac"] = tf / fp64_flops
+        out[k] = e
+    return out
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_grid512.txt")
@@ -236,6 +262,8 @@ def run_ours(args):
         barrier(world)
         wall = time.perf_counter() - t0
         if precision == "fp64_alg1":
+            # the FP64 ceiling of the FP64-bound kernels, measured at the clocks of this run
+            fp64_rate, fp64_probe_s = mb4.fp64_fma_rate(0.3)
             clocks = sampler.stop()
         o1 = it.observables()
         drift = max([abs(h - o0["H"]) / abs(o0["H"]) for h in Hs + [o1["H"]]])
@@ -297,18 +325,22 @@ def run_ours(args):
     it.close()
 
     fp = results["fp64"]
-    # Roofline of the dominant kernel of the FP64 path.
+    # Roofline of the dominant kernel of the FP64 path: by the bench's own event times
+    # (the host-driven copy of the timed steps), against the FP64 rate measured above.
     dom = max(fp["kernels"].items(), key=lambda kv: kv[1]["ms_total"])[0]
     model = kernel_model(dom, "fp64", fp["krylov_s"])
     us = fp["kernels"][dom]["us_per_launch"]
     flops_per_launch = model["flops"] * S
     bytes_per_launch = model["bytes"] * S
-    t_alu = flops_per_launch / FP64_PEAK_DERIVED
+    t_alu = flops_per_launch / fp64_rate
     t_hbm = bytes_per_launch / (peaks["hbm_gbs"] * 1e9)
+    probe_src = (f"measured in this run: mb4_fp64_fma_rate (DFMA chains over the whole device, "
+                 f"{fp64_probe_s:.2f} s launch); nominal {FP64_PEAK_DERIVED / 1e12:.4f} TFLOP/s = "
+                 f"152 SMs x 2070 MHz x 2 DFMA/clk/SM")
     if model["fp64"] and t_alu >= t_hbm:
         roof = {"bound": "alu", "kernel": dom, "achieved": flops_per_launch / (us * 1e-6) / 1e12,
-                "peak": FP64_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM (FP64)"}
+                "peak": fp64_rate / 1e12, "unit": "TFLOP/s", "peak_source": probe_src,
+                "frac_of_nominal": flops_per_launch / (us * 1e-6) / FP64_PEAK_DERIVED}
     else:
         roof = {"bound": "hbm", "kernel": dom, "achieved": bytes_per_launch / (us * 1e-6) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs"}
@@ -317,10 +349,15 @@ def run_ours(args):
         # the same launch against the FP64 pipe's instruction rate (an add or a
         # multiply takes a DFMA's slot, so the flop fraction understates pipe use)
         ops = model["fp64_ops"] * S / (us * 1e-6)
+        issue_peak = fp64_rate / 2.0
         roof["fp64_issue"] = {"ops_per_site": model["fp64_ops"], "achieved_gops": ops / 1e9,
-                              "peak_gops": FP64_ISSUE_PEAK / 1e9, "frac": ops / FP64_ISSUE_PEAK}
+                              "peak_gops": issue_peak / 1e9, "frac": ops / issue_peak}
     roof["traffic"] = measured_traffic(dom, "fp64")
     roof["algorithmic_per_site"] = {"flops": model["flops"], "bytes": model["bytes"]}
+    roof["all_kernels"] = kernel_rooflines({k: (v["ms_total"], v["launches"]) for k, v in fp["kernels"].items()},
+                                           "fp64", fp["krylov_s"], S, peaks["hbm_gbs"], fp64_rate)
+    global HBM_GBS, FP64_RATE
+    HBM_GBS, FP64_RATE = peaks["hbm_gbs"], fp64_rate
 
     line = {
         "metric": METRIC, "value": fp["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -405,8 +442,14 @@ def bench_ensemble(args, flush, K=20):
             ms, newton = _timed_batch_steps(bt, K, flush)
             H1 = bt.observables()[:, 0]
             shape = list(bt.launch_shape())
+            # per-kernel device times: the host-driven copy of 5 more steps, events around launches
+            flush()
+            _, codes, prof = bt.step_profiled(5)
+            if any(codes):
+                raise RuntimeError(f"profiled ensemble step failed: {sorted(set(codes))}")
         out[precision] = {"value": B * n * n * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
                           "launch_shape": shape,
+                          "kernels": kernel_rooflines(prof, precision, 4, B * n * n, HBM_GBS, FP64_RATE),
                           "newton_per_member_step": newton / (B * K),
                           "energy_drift_max": float(np.max(np.abs(H1 - H0) / np.abs(H0)))}
     return out
@@ -437,7 +480,12 @@ def bench_grid2048(args, flush, K=20):
             ms = sum(a.elapsed_time(b) for a, b in evs)
             finals[precision] = it.get_state()
             H1 = it.energy()[0]
+            # per-kernel device times: the host-driven copy of 5 more steps (the states above
+            # are taken first, so the comparison covers the timed steps only)
+            flush()
+            _, prof = it.step_profiled(5)
         out[precision] = {"value": w.S * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+                          "kernels": kernel_rooflines(prof, precision, 4, w.S, HBM_GBS, FP64_RATE),
                           "newton_per_step": newton / K, "energy_drift": abs(H1 - H0) / abs(H0)}
     a, b = finals["mixed"], finals["fp64"]
     out["mixed_vs_fp64_rel_linf"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
@@ -519,9 +567,26 @@ def _oracle_sample(n=64):
     return orc, prob, w.psi0(), w.h, n * n
 
 
+ONE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                  "BLIS_NUM_THREADS": "1", "VECLIB_MAXIMUM_THREADS": "1", "NUMEXPR_NUM_THREADS": "1"}
+
+
 def cpu_baseline(seconds=15.0, n=64):
+    """The oracle, as it stands, on one host thread (its BLAS pinned to one thread in a
+    fresh interpreter, so that ``cores`` is the number of threads actually used).  Its
+    sparse LU and GMRES barely use more than one core anyway."""
+    env = dict(os.environ, **ONE_THREAD_ENV)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
+                        "--cpu-seconds", str(seconds)], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu baseline failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_baseline_here(seconds=15.0, n=64):
     """The oracle, as it stands, on a bounded sample of the workload: an n x n
-    instance with the 512x512 physics, stepped for about ``seconds``."""
+    instance with the 512x512 physics, stepped for about ``seconds`` (run by
+    cpu_baseline in a one-thread interpreter)."""
     orc, prob, u, h, S = _oracle_sample(n)
     u = orc.step(prob, u, h)   # warm-up (imports, caches)
     t0 = time.perf_counter()
@@ -532,9 +597,10 @@ def cpu_baseline(seconds=15.0, n=64):
         steps += 1
     wall = time.perf_counter() - t0
     cpu = time.process_time() - c0
-    return {"value": S * steps / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+    return {"value": S * steps / wall, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n}x{n} instance with the 512x512 workload's physics, {steps} MB4 steps, "
-                      f"{wall:.1f} s wall", "host_threads_available": os.cpu_count()}
+                      f"{wall:.1f} s wall", "threads": "1 (BLAS and OpenMP pinned to one thread)",
+            "cpu_busy_over_wall": cpu / wall, "host_threads_available": os.cpu_count()}
 
 
 def run_reference(args):
@@ -542,6 +608,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    os.environ.update(ONE_THREAD_ENV)      # before numpy loads: the oracle runs on one thread
     n = 64
     orc, prob, u, h, S = _oracle_sample(n)
     for _ in range(args.warmup):
@@ -558,21 +625,24 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "grid512_fp64", "sample": f"{n}x{n} instance with the same physics"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "cpu_busy_over_wall": cpu / wall,
                              "sample": f"{n}x{n} instance with the 512x512 workload's physics, "
                                        f"{args.steps} MB4 steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def profile_case(precision):
-    """A few steps of the 512x512 workload with the host-driven Newton loop, so
-    that every kernel is its own launch (the form ncu captures kernel by kernel);
-    one step and one observables call sit in a profiler start/stop range, the range
-    ncu --profile-from-start off records."""
+def profile_case(case):
+    """A few steps of the 512x512 workload (``fp64``, ``mixed``) or of the 2048x2048
+    one (``fp64_2048``, ``mixed_2048``) with the host-driven Newton loop, so that every
+    kernel is its own launch (the form ncu captures kernel by kernel); one step and
+    one observables call sit in a profiler start/stop range, the range ncu
+    --profile-from-start off records."""
     import torch
     from paper_2003_04345_gb300 import inputs, mb4
-    w = inputs.grid512_fp64()
+    precision, _, size = case.partition("_")
+    w = inputs.grid2048_mixed() if size == "2048" else inputs.grid512_fp64()
     with mb4.from_workload(w, precision=precision, use_graph=False) as it:
         it.step(5)
         torch.cuda.synchronize()
@@ -581,7 +651,7 @@ def profile_case(precision):
         it.observables()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-    print(json.dumps({"profile_case": precision, "newton_iters_last": st["newton_iters_last"]}))
+    print(json.dumps({"profile_case": case, "newton_iters_last": st["newton_iters_last"]}))
 
 
 def full_runs():
@@ -646,14 +716,18 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed"],
-                    help="run 6 host-driven steps of the 512x512 workload for ncu and exit")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "fp64_2048", "mixed_2048"],
+                    help="run 6 host-driven steps of the 512x512 (or 2048x2048) workload for ncu and exit")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the ensemble, 2048^2 and served-stream lines")
     ap.add_argument("--full-runs", action="store_true",
                     help="run the 2048^2 and ensemble configurations over their whole step counts "
                          "(energy drift, Newton counts) and exit")
     args = ap.parse_args()
+    if args.cpu_baseline_only:
+        print(json.dumps(_cpu_baseline_here(seconds=args.cpu_seconds)))
+        return
     if args.profile_case:
         profile_case(args.profile_case)
         return

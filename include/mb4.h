@@ -232,7 +232,9 @@ int mb4_wait(mb4_ctx* ctx, mb4_stats* stats);
 /* Kernel classes reported by mb4_step_profiled. */
 #define MB4_K_SETUP        0   /* u0, (K+V)u0, J coefficients, first right-hand side          */
 #define MB4_K_RESIDUAL     1   /* stage residual Phi (FP64)                                    */
-#define MB4_K_MATVEC       2   /* Krylov basis v_{a+1} = (J/theta) v_a, three systems         */
+#define MB4_K_MATVEC       2   /* Krylov basis v_{a+1} = (J/theta) v_a, three systems (one
+                                  launch per level; the FP32 grid basis is one matrix-powers
+                                  launch for all s levels)                                      */
 #define MB4_K_GRAM         3   /* Gram matrix, its fixed-order reduction and least squares     */
 #define MB4_K_UPDATE       4   /* Newton update Ubar += rbar, ||r||_inf, Newton loop test      */
 #define MB4_K_ACCEPT       5   /* u1 = U_c3                                                    */
@@ -342,6 +344,13 @@ int mb4_batch_set_chi_field(mb4_batch* b, int instance, const double* chi, int o
 /* As mb4_get_launch_shape, for a batch. */
 int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);
 
+/* As mb4_step_profiled, for a batch: nsteps steps of every enabled instance with a
+ * host-driven Newton loop and an event pair around every launch; adds the summed
+ * device time of each kernel class to ms[MB4_K_COUNT] and its launch count to
+ * launches[MB4_K_COUNT] (both nullable); stats and status as mb4_batch_wait. */
+int mb4_batch_step_profiled(mb4_batch* b, int nsteps, mb4_stats* stats, int* status, double* ms,
+                            long long* launches);
+
 /* Device bytes a batch of this shape and options would allocate (for admission). */
 long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt);
 
@@ -428,14 +437,29 @@ int mb4_constants(double alpha1, double c1, double c2, double* E34, double* lam3
  * which every GPU that loads the library holds until the process exits.  The
  * first call on a device looks up that array's device address (once per device,
  * with the device current), so make the first call before any stream capture.
- * All calls share the array: calls that overlap on the GPU (different streams,
+ * That address is kept for the life of the process: after a cudaDeviceReset of
+ * the device (which unloads the library image from it) this entry point must not
+ * be called again.  All calls share the array: calls that overlap on the GPU (different streams,
  * other host threads) race and give wrong results; serialise them.  Every call
  * overwrites the whole part of the array it reads, so no clearing is needed.
  * Returns MB4_ERR_INVALID_ARG for nx or ny < 3, nx*ny > MB4_NOALLOC_MAX_SITES
- * or a NULL pointer, MB4_ERR_CUDA if the set-up or a launch fails. */
+ * or a NULL pointer, MB4_ERR_CUDA if the set-up or a launch fails (judged by the
+ * launches' own return codes: an error left pending by earlier work of the caller
+ * is neither reported nor cleared). */
 int mb4_observables_noalloc(int nx, int ny, double tx, double ty, double onsite, double chi,
                             const double* re, const double* im, const double* v, double* out6,
                             void* stream);
+
+/* The FP64 FMA throughput of the current device, measured: independent chains of
+ * dependent FP64 FMAs in every thread of a grid that fills the device, with no memory
+ * traffic, timed with CUDA events; the launch is lengthened until it runs for about
+ * `seconds` (0 < seconds <= 10).  *flops_per_s receives 2 x FMAs per second;
+ * *elapsed_s (nullable) the duration of the timed launch.  It is the ceiling of the
+ * step's FP64-bound kernels at the clock the device runs at.  Runs on the legacy
+ * default stream and synchronises it.  The paper has no counterpart: a measurement
+ * service of the library.  MB4_ERR_INVALID_ARG for a NULL output or seconds out of
+ * range, MB4_ERR_CUDA on a launch or event failure. */
+int mb4_fp64_fma_rate(double seconds, double* flops_per_s, double* elapsed_s);
 
 const char* mb4_status_string(int status);
 

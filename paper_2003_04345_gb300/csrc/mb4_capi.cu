@@ -1202,7 +1202,9 @@ int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
     P.run(MB4_K_SETUP, 1, [&] { launch_setup<TK>(c->p, c->b, s); });
     for (;;) {
       P.run(MB4_K_RESIDUAL, 1, [&] { launch_residual<TK>(c->p, c->b, true, s); });
-      P.run(MB4_K_MATVEC, c->p.s, [&] {
+      // the FP32 grid basis is one matrix-powers launch for all s levels
+      const bool powers = sizeof(TK) == sizeof(float) && c->p.use_powers && !c->p.precond;
+      P.run(MB4_K_MATVEC, powers ? 1 : c->p.s, [&] {
         if (c->p.precond) launch_precond_basis<TK>(c->p, c->b, s);
         else launch_matvecs<TK>(c->p, c->b, s);
       });
@@ -1222,12 +1224,7 @@ int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
   return MB4_OK;
 }
 
-}  // namespace
-
-extern "C" int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches) {
-  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
-  if (stats) std::memset(stats, 0, sizeof(*stats));
-  MB4_CHECK(clear_errors(c));
+int profiled(mb4_batch* c, int nsteps, double* ms, long long* launches) {
   Prof P;
   P.s = c->stream;
   MB4_CHECK((c->precision == MB4_MIXED) ? profiled_steps<float>(c, nsteps, P) : profiled_steps<double>(c, nsteps, P));
@@ -1235,5 +1232,22 @@ extern "C" int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, doubl
     if (ms) ms[k] += P.ms[k];
     if (launches) launches[k] += P.n[k];
   }
+  return MB4_OK;
+}
+
+}  // namespace
+
+extern "C" int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  MB4_CHECK(clear_errors(c));
+  MB4_CHECK(profiled(c, nsteps, ms, launches));
   return wait_batch(c, stats, nullptr);
+}
+
+extern "C" int mb4_batch_step_profiled(mb4_batch* c, int nsteps, mb4_stats* stats, int* status, double* ms,
+                                       long long* launches) {
+  if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
+  MB4_CHECK(profiled(c, nsteps, ms, launches));
+  return wait_batch(c, stats, status);
 }

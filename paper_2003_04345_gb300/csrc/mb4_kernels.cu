@@ -992,6 +992,15 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_accept(StepParams p, double
       H[(size_t)2 * S + k] = c;
     }
   }
+  // Block 0 rewrites in_step and active below while other blocks of this grid may still
+  // read in_step as took_part.  That is safe only because of an invariant: the host
+  // changes `enabled` only between calls, and an error is only ever set during a call,
+  // so when block 0 sets go = 1 the old in_step was already 1 with no error (k_arm or
+  // the previous k_accept armed it), and when it sets go = 0 after a step it took part
+  // in, the instance has an error and the branch above is skipped with either value.
+  // A block that reads the new in_step therefore does what one that reads the old does.
+  // A change to how instances are armed must keep that, or move this bookkeeping into
+  // a kernel of its own.
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (took_part && !failed) {
       I.steps_done += 1;

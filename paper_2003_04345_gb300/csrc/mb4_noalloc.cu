@@ -30,7 +30,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 void* g_na_ptr[kMaxDevices] = {};
 
-// Device address of g_na_scratch on the current device (looked up once per device).
+// Device address of g_na_scratch on the current device (looked up once per device and
+// kept: a cudaDeviceReset, which unloads the library image from the device, makes the
+// kept address stale, so the entry point may not be used after one).
 int scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MB4_ERR_CUDA;
@@ -139,8 +141,16 @@ extern "C" int mb4_observables_noalloc(int nx, int ny, double tx, double ty, dou
   double* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc != MB4_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_obs_planar<<<kNaBlocks, kNaThreads, 0, s>>>(nx, ny, tx, ty, onsite, chi, re, im, v, scratch);
-  k_obs_planar_final<<<1, 32, 0, s>>>(scratch, out6);
-  return (cudaGetLastError() == cudaSuccess) ? MB4_OK : MB4_ERR_CUDA;
+  // Each launch is checked through its own return code, so an error the caller left
+  // pending is neither reported as this call's nor cleared.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kNaBlocks);
+  cfg.blockDim = dim3(kNaThreads);
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  if (cudaLaunchKernelEx(&cfg, k_obs_planar, nx, ny, tx, ty, onsite, chi, re, im, v, scratch) != cudaSuccess)
+    return MB4_ERR_CUDA;
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(32);
+  if (cudaLaunchKernelEx(&cfg, k_obs_planar_final, (const double*)scratch, out6) != cudaSuccess) return MB4_ERR_CUDA;
+  return MB4_OK;
 }

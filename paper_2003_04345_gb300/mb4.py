@@ -40,7 +40,8 @@ EXPORTS = ("mb4_default_options", "mb4_create", "mb4_create_sparse", "mb4_destro
            "mb4_set_chi_field", "mb4_constants", "mb4_status_string", "mb4_version", "mb4_observables_noalloc",
            "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
            "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
-           "mb4_batch_clear_errors", "mb4_batch_get_launch_shape", "mb4_batch_set_chi_field", "mb4_batch_bytes", "mb4_server_create",
+           "mb4_batch_clear_errors", "mb4_batch_get_launch_shape", "mb4_batch_set_chi_field", "mb4_batch_bytes",
+           "mb4_batch_step_profiled", "mb4_fp64_fma_rate", "mb4_server_create",
            "mb4_server_destroy", "mb4_server_submit", "mb4_server_run", "mb4_server_result", "mb4_server_clock")
 
 
@@ -155,6 +156,9 @@ def lib():
         L.mb4_batch_wait.argtypes = [_P, C.POINTER(Stats), C.POINTER(C.c_int)]
         L.mb4_batch_step.argtypes = [_P, C.c_int, C.POINTER(Stats), C.POINTER(C.c_int)]
         L.mb4_batch_observables.argtypes = [_P, _D]
+        L.mb4_batch_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), C.POINTER(C.c_int), _D,
+                                              C.POINTER(C.c_longlong)]
+        L.mb4_fp64_fma_rate.argtypes = [C.c_double, _D, _D]
         L.mb4_batch_clear_errors.argtypes = [_P]
         L.mb4_batch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(Options)]
         L.mb4_batch_bytes.restype = C.c_longlong
@@ -416,6 +420,15 @@ class Integrator:
         return (re + 1j * im).reshape(3, self.S)
 
 
+def fp64_fma_rate(seconds=0.2):
+    """Measured FP64 FMA throughput of the current device (flop/s, FMA = 2) and the
+    duration of the timed launch (mb4_fp64_fma_rate)."""
+    f = C.c_double()
+    t = C.c_double()
+    _check(lib().mb4_fp64_fma_rate(float(seconds), C.byref(f), C.byref(t)), "mb4_fp64_fma_rate")
+    return f.value, t.value
+
+
 def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.0, stream=None):
     """mb4_observables_noalloc on torch CUDA tensors (float64; re, im, V of nx*ny
     elements, out6 of 6): enqueues the reduction on ``stream`` without allocating."""
@@ -539,6 +552,19 @@ class Batch:
     def step(self, nsteps=1):
         self.step_async(nsteps)
         return self.wait()
+
+    def step_profiled(self, nsteps=1):
+        """Host-driven steps with CUDA events around every launch: returns
+        (per-instance stats, status codes, {kernel class: (total ms, launches)})."""
+        st = (Stats * self.B)()
+        codes = (C.c_int * self.B)()
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = (C.c_longlong * len(KERNEL_CLASSES))()
+        rc = lib().mb4_batch_step_profiled(self._ctx, int(nsteps), st, codes, ms.ctypes.data_as(_D), n)
+        if rc not in (MB4_OK, MB4_ERR_NEWTON_NOT_CONVERGED, MB4_ERR_KRYLOV_BREAKDOWN, MB4_ERR_NONFINITE):
+            _check(rc, "mb4_batch_step_profiled")
+        return ([s.as_dict() for s in st], list(codes),
+                {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)})
 
     def observables(self):
         out = np.zeros(self.B * 6)

@@ -63,6 +63,40 @@ def test_noalloc_matches_context_observables_twice(env, nx, ny):
         assert _close(got, want), (got, want)
 
 
+def test_noalloc_allocates_nothing(env):
+    """Repeated calls leave the device's free memory and torch's allocator untouched: the
+    entry point uses only its fixed array, never cudaMalloc.  Measured after a first call,
+    so that the one-time loading of the library's kernels onto the device is not counted."""
+    torch, mb4 = env
+    nx, ny = 96, 80
+    S = nx * ny
+    psi = inputs.wavepacket(nx, ny, 4.0, np.pi / 4, 0.0)
+    V = torch.tensor(inputs.potential(nx, ny, 1.0, S // 100, 20.0, 9), dtype=torch.float64, device="cuda")
+    re = torch.tensor(psi.real.copy(), dtype=torch.float64, device="cuda")
+    im = torch.tensor(psi.imag.copy(), dtype=torch.float64, device="cuda")
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    L = mb4.lib()
+
+    def call():
+        rc = L.mb4_observables_noalloc(nx, ny, 1.0, 1.0, 0.0, 1.0, re.data_ptr(), im.data_ptr(), V.data_ptr(),
+                                       out.data_ptr(), stream.cuda_stream)
+        assert rc == mb4.MB4_OK, mb4.status_string(rc)
+
+    call()
+    stream.synchronize()
+    first = out.cpu().numpy().copy()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(5):
+        call()
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0, (free0, free1)
+    assert np.array_equal(out.cpu().numpy(), first)      # same inputs, same fixed-order sums
+
+
 def test_noalloc_rejects_out_of_range_sizes(env):
     torch, mb4 = env
     x = torch.zeros(16, dtype=torch.float64, device="cuda")
