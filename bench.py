@@ -49,7 +49,7 @@ def _peaks():
 
 
 # Algorithmic work per kernel launch, per site (flops: FMA = 2), and bytes per site.
-def kernel_model(kclass, precision, s, powers=True):
+def kernel_model(kclass, precision, s, powers=True, pred_order=2):
     """Algorithmic work of one launch per site: flops (FMA = 2), FP64 instructions
     (DFMA, DADD and DMUL one each: what occupies the FP64 pipe) and bytes (each array
     read or written once; neighbours counted once).  ``powers``: the FP32 basis is the
@@ -72,28 +72,31 @@ def kernel_model(kclass, precision, s, powers=True):
                 "bytes": s * 6 * tk + 48 + 48, "fp64": f64}
     if kclass == "setup":      # u, D in; (K+V)u0, J coefficients, level 0 out
         return {"flops": 40, "fp64_ops": 0, "bytes": 16 + 8 + 16 + 4 * tk + 6 * tk, "fp64": True}
-    if kclass == "accept":     # u, dU in; u out (history shifts not counted)
-        return {"flops": 12, "fp64_ops": 0, "bytes": 48 + 16 + 16, "fp64": True}
+    if kclass == "accept":     # u, dU in; u out; the Newton-start history shifted by one step
+        hist = 48 + (pred_order - 1) * 96 if pred_order > 0 else 0
+        return {"flops": 12, "fp64_ops": 0, "bytes": 48 + 16 + 16 + hist, "fp64": True}
     return {"flops": 0, "fp64_ops": 0, "bytes": 0, "fp64": False}
 
 
-def kernel_rooflines(prof, precision, s, sites, hbm_gbs, fp64_flops, powers=True):
-    """Per kernel class: microseconds per launch, algorithmic GB/s and its fraction of the
-    measured HBM copy bandwidth, and for FP64 kernels the FP64 flop rate and its fraction
-    of the measured FP64 FMA rate.  ``sites`` = sites one launch covers."""
+def kernel_rooflines(prof, precision, s, hbm_gbs, fp64_flops, powers=True, pred_order=2):
+    """Per kernel class, from (total ms, launches, sites computed): microseconds per
+    launch, algorithmic GB/s (bytes per site x sites computed / time) and its fraction of
+    the measured HBM copy bandwidth, and for FP64 kernels the FP64 flop rate and its
+    fraction of the measured FP64 FMA rate.  Launches that skip their instance (the
+    first residual of a step from U^0 = e3 (x) u0) add time but no sites."""
     out = {}
-    for k, (ms, n) in prof.items():
-        if not n:
+    for k, (ms, n, sites) in prof.items():
+        if not n or not sites:
             continue
-        us = 1e3 * ms / n
-        m = kernel_model(k, precision, s, powers)
-        gbs = m["bytes"] * sites / (us * 1e-6) / 1e9
-        e = {"us_per_launch": us, "launches": n, "ms_total": ms, "bytes_per_site": m["bytes"],
-             "gb_s": gbs, "hbm_frac": gbs / hbm_gbs}
+        m = kernel_model(k, precision, s, powers, pred_order)
+        gbs = m["bytes"] * sites / (ms * 1e-3) / 1e9
+        e = {"us_per_launch": 1e3 * ms / n, "launches": n, "ms_total": ms, "sites": sites,
+             "bytes_per_site": m["bytes"], "gb_s": gbs, "hbm_frac": gbs / hbm_gbs}
         if m["fp64"] and m["fp64_ops"]:
-            tf = m["flops"] * sites / (us * 1e-6)
+            tf = m["flops"] * sites / (ms * 1e-3)
             e["fp64_tflops"] = tf / 1e12
             e["fp64_frac"] = tf / fp64_flops
+            e["fp64_issue_frac"] = m["fp64_ops"] * sites / (ms * 1e-3) / (fp64_flops / 2.0)
         out[k] = e
     return out
 
@@ -293,7 +296,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         results[precision]["kernels"] = {
-            k: {"ms_total": v[0], "launches": v[1], "us_per_launch": (1e3 * v[0] / v[1]) if v[1] else 0.0}
+            k: {"ms_total": v[0], "launches": v[1], "sites": v[2],
+                "us_per_launch": (1e3 * v[0] / v[1]) if v[1] else 0.0}
             for k, v in prof.items() if v[1]}
         results[precision]["profiled_steps"] = kp
         if precision == "fp64":
@@ -329,7 +333,10 @@ def run_ours(args):
     # (the host-driven copy of the timed steps), against the FP64 rate measured above.
     dom = max(fp["kernels"].items(), key=lambda kv: kv[1]["ms_total"])[0]
     model = kernel_model(dom, "fp64", fp["krylov_s"])
-    us = fp["kernels"][dom]["us_per_launch"]
+    kd = fp["kernels"][dom]
+    # one launch's work is S sites; its duration is the time per site computed x S (a
+    # launch that skips its instance adds time but no work, and is not counted)
+    us = 1e3 * kd["ms_total"] / (kd["sites"] / S)
     flops_per_launch = model["flops"] * S
     bytes_per_launch = model["bytes"] * S
     t_alu = flops_per_launch / fp64_rate
@@ -354,8 +361,9 @@ def run_ours(args):
                               "peak_gops": issue_peak / 1e9, "frac": ops / issue_peak}
     roof["traffic"] = measured_traffic(dom, "fp64")
     roof["algorithmic_per_site"] = {"flops": model["flops"], "bytes": model["bytes"]}
-    roof["all_kernels"] = kernel_rooflines({k: (v["ms_total"], v["launches"]) for k, v in fp["kernels"].items()},
-                                           "fp64", fp["krylov_s"], S, peaks["hbm_gbs"], fp64_rate)
+    roof["all_kernels"] = kernel_rooflines({k: (v["ms_total"], v["launches"], v["sites"])
+                                            for k, v in fp["kernels"].items()},
+                                           "fp64", fp["krylov_s"], peaks["hbm_gbs"], fp64_rate)
     global HBM_GBS, FP64_RATE
     HBM_GBS, FP64_RATE = peaks["hbm_gbs"], fp64_rate
 
@@ -449,7 +457,7 @@ def bench_ensemble(args, flush, K=20):
                 raise RuntimeError(f"profiled ensemble step failed: {sorted(set(codes))}")
         out[precision] = {"value": B * n * n * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
                           "launch_shape": shape,
-                          "kernels": kernel_rooflines(prof, precision, 4, B * n * n, HBM_GBS, FP64_RATE),
+                          "kernels": kernel_rooflines(prof, precision, 4, HBM_GBS, FP64_RATE),
                           "newton_per_member_step": newton / (B * K),
                           "energy_drift_max": float(np.max(np.abs(H1 - H0) / np.abs(H0)))}
     return out
@@ -485,7 +493,7 @@ def bench_grid2048(args, flush, K=20):
             flush()
             _, prof = it.step_profiled(5)
         out[precision] = {"value": w.S * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
-                          "kernels": kernel_rooflines(prof, precision, 4, w.S, HBM_GBS, FP64_RATE),
+                          "kernels": kernel_rooflines(prof, precision, 4, HBM_GBS, FP64_RATE),
                           "newton_per_step": newton / K, "energy_drift": abs(H1 - H0) / abs(H0)}
     a, b = finals["mixed"], finals["fp64"]
     out["mixed_vs_fp64_rel_linf"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))

@@ -243,8 +243,14 @@ int mb4_wait(mb4_ctx* ctx, mb4_stats* stats);
 /* mb4_step with a host-driven Newton loop and a CUDA event pair around every
  * kernel launch, for profiling.  Same arithmetic and results as mb4_step (bit
  * for bit).  Adds to ms[MB4_K_COUNT] the summed device time of each kernel
- * class and to launches[MB4_K_COUNT] its launch count (both nullable). */
-int mb4_step_profiled(mb4_ctx* ctx, int nsteps, mb4_stats* stats, double* ms, long long* launches);
+ * class, to launches[MB4_K_COUNT] its launch count and to sites[MB4_K_COUNT] the
+ * sites its launches computed (all three nullable): an instance that has
+ * converged, or the first residual of a step that starts at U^0 = e3 (x) u0
+ * (whose right-hand side the set-up wrote), is skipped by a launch and not
+ * counted, so sites / time is the rate of the work actually done.  The status
+ * is read back between launches. */
+int mb4_step_profiled(mb4_ctx* ctx, int nsteps, mb4_stats* stats, double* ms, long long* launches,
+                      double* sites);
 
 /* Per-site nonlinearity chi_k = -gamma_k (S doubles, finite), for a context created
  * with site_chi = 1 (else MB4_ERR_INVALID_ARG).  The energy becomes
@@ -346,10 +352,11 @@ int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);
 
 /* As mb4_step_profiled, for a batch: nsteps steps of every enabled instance with a
  * host-driven Newton loop and an event pair around every launch; adds the summed
- * device time of each kernel class to ms[MB4_K_COUNT] and its launch count to
- * launches[MB4_K_COUNT] (both nullable); stats and status as mb4_batch_wait. */
+ * device time of each kernel class to ms[MB4_K_COUNT], its launch count to
+ * launches[MB4_K_COUNT] and the sites computed to sites[MB4_K_COUNT] (all
+ * nullable); stats and status as mb4_batch_wait. */
 int mb4_batch_step_profiled(mb4_batch* b, int nsteps, mb4_stats* stats, int* status, double* ms,
-                            long long* launches);
+                            long long* launches, double* sites);
 
 /* Device bytes a batch of this shape and options would allocate (for admission). */
 long long mb4_batch_bytes(int nx, int ny, int batch, const mb4_options* opt);

@@ -1164,6 +1164,7 @@ struct Prof {
   size_t used = 0;
   double ms[MB4_K_COUNT] = {0};
   long long n[MB4_K_COUNT] = {0};
+  double sites[MB4_K_COUNT] = {0};
   cudaEvent_t ev() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -1172,13 +1173,15 @@ struct Prof {
     }
     return pool[used++];
   }
-  template <typename F> void run(int cls, int count, F f) {
+  // work: sites the launch(es) compute (instances that take part x sites per instance)
+  template <typename F> void run(int cls, int count, double work, F f) {
     cudaEvent_t a = ev(), b = ev();
     cudaEventRecord(a, s);
     f();
     cudaEventRecord(b, s);
     open.push_back({cls, {a, b}});
     n[cls] += count;
+    sites[cls] += work;
   }
   void harvest() {  // stream must be synchronised
     for (auto& o : open) {
@@ -1194,22 +1197,45 @@ struct Prof {
   }
 };
 
+// Instances that a launch works on, read from the device status (the stream is idle).
+struct Work {
+  double active = 0, residual = 0, accept = 0;
+};
+
+int count_work(mb4_batch* c, bool first_iteration, Work* w) {
+  MB4_CHECK(read_status(c));
+  *w = Work{};
+  const double S = (double)c->p.S;
+  for (const InstStatus& I : c->host_status) {
+    if (I.active) {
+      w->active += S;
+      // the first residual of a step from U^0 = e3 (x) u0 returns at once: k_setup wrote b^0
+      if (!first_iteration || I.predicted) w->residual += S;
+    }
+    if (I.in_step && !I.error) w->accept += S;
+  }
+  return MB4_OK;
+}
+
 template <typename TK>
 int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
   cudaStream_t s = c->stream;
   launch_arm(c->p, c->b, s);
+  // the FP32 grid basis is one matrix-powers launch for all s levels
+  const bool powers = sizeof(TK) == sizeof(float) && c->p.use_powers && !c->p.precond;
+  Work w;
   for (int n = 0; n < nsteps; ++n) {
-    P.run(MB4_K_SETUP, 1, [&] { launch_setup<TK>(c->p, c->b, s); });
-    for (;;) {
-      P.run(MB4_K_RESIDUAL, 1, [&] { launch_residual<TK>(c->p, c->b, true, s); });
-      // the FP32 grid basis is one matrix-powers launch for all s levels
-      const bool powers = sizeof(TK) == sizeof(float) && c->p.use_powers && !c->p.precond;
-      P.run(MB4_K_MATVEC, powers ? 1 : c->p.s, [&] {
+    MB4_CHECK(count_work(c, true, &w));
+    P.run(MB4_K_SETUP, 1, w.active, [&] { launch_setup<TK>(c->p, c->b, s); });
+    for (int it = 0;; ++it) {
+      if (it > 0) MB4_CHECK(count_work(c, false, &w));
+      P.run(MB4_K_RESIDUAL, 1, w.residual, [&] { launch_residual<TK>(c->p, c->b, true, s); });
+      P.run(MB4_K_MATVEC, powers ? 1 : c->p.s, w.active * (powers ? 1 : c->p.s), [&] {
         if (c->p.precond) launch_precond_basis<TK>(c->p, c->b, s);
         else launch_matvecs<TK>(c->p, c->b, s);
       });
-      P.run(MB4_K_GRAM, 1, [&] { launch_gram<TK>(c->p, c->b, s); });
-      P.run(MB4_K_UPDATE, 1, [&] { launch_update<TK>(c->p, c->b, 0ull, 0, s); });
+      P.run(MB4_K_GRAM, 1, w.active, [&] { launch_gram<TK>(c->p, c->b, s); });
+      P.run(MB4_K_UPDATE, 1, w.active, [&] { launch_update<TK>(c->p, c->b, 0ull, 0, s); });
       MB4_TRY(cudaGetLastError());
       BatchCtl bc;
       MB4_TRY(cudaMemcpyAsync(&bc, c->b.bc, sizeof(bc), cudaMemcpyDeviceToHost, s));
@@ -1217,37 +1243,40 @@ int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
       P.harvest();
       if (!bc.any_cont) break;
     }
-    P.run(MB4_K_ACCEPT, 1, [&] { launch_accept(c->p, c->b, s); });
+    MB4_CHECK(count_work(c, false, &w));
+    P.run(MB4_K_ACCEPT, 1, w.accept, [&] { launch_accept(c->p, c->b, s); });
   }
   MB4_TRY(cudaStreamSynchronize(s));
   P.harvest();
   return MB4_OK;
 }
 
-int profiled(mb4_batch* c, int nsteps, double* ms, long long* launches) {
+int profiled(mb4_batch* c, int nsteps, double* ms, long long* launches, double* sites) {
   Prof P;
   P.s = c->stream;
   MB4_CHECK((c->precision == MB4_MIXED) ? profiled_steps<float>(c, nsteps, P) : profiled_steps<double>(c, nsteps, P));
   for (int k = 0; k < MB4_K_COUNT; ++k) {
     if (ms) ms[k] += P.ms[k];
     if (launches) launches[k] += P.n[k];
+    if (sites) sites[k] += P.sites[k];
   }
   return MB4_OK;
 }
 
 }  // namespace
 
-extern "C" int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches) {
+extern "C" int mb4_step_profiled(mb4_ctx* c, int nsteps, mb4_stats* stats, double* ms, long long* launches,
+                                 double* sites) {
   if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   MB4_CHECK(clear_errors(c));
-  MB4_CHECK(profiled(c, nsteps, ms, launches));
+  MB4_CHECK(profiled(c, nsteps, ms, launches, sites));
   return wait_batch(c, stats, nullptr);
 }
 
 extern "C" int mb4_batch_step_profiled(mb4_batch* c, int nsteps, mb4_stats* stats, int* status, double* ms,
-                                       long long* launches) {
+                                       long long* launches, double* sites) {
   if (!c || nsteps < 0) return MB4_ERR_INVALID_ARG;
-  MB4_CHECK(profiled(c, nsteps, ms, launches));
+  MB4_CHECK(profiled(c, nsteps, ms, launches, sites));
   return wait_batch(c, stats, status);
 }

@@ -132,7 +132,7 @@ def lib():
         L.mb4_batch_set_chi_field.argtypes = [_P, C.c_int, C.c_void_p, C.c_int]
         L.mb4_batch_get_launch_shape.argtypes = [_P, C.POINTER(C.c_int)]
         L.mb4_wait.argtypes = [_P, C.POINTER(Stats)]
-        L.mb4_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), _D, C.POINTER(C.c_longlong)]
+        L.mb4_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), _D, C.POINTER(C.c_longlong), _D]
         L.mb4_energy.argtypes = [_P, _D, _D]
         L.mb4_norm.argtypes = [_P, _D]
         L.mb4_observables.argtypes = [_P, _D]
@@ -157,7 +157,7 @@ def lib():
         L.mb4_batch_step.argtypes = [_P, C.c_int, C.POINTER(Stats), C.POINTER(C.c_int)]
         L.mb4_batch_observables.argtypes = [_P, _D]
         L.mb4_batch_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), C.POINTER(C.c_int), _D,
-                                              C.POINTER(C.c_longlong)]
+                                              C.POINTER(C.c_longlong), _D]
         L.mb4_fp64_fma_rate.argtypes = [C.c_double, _D, _D]
         L.mb4_batch_clear_errors.argtypes = [_P]
         L.mb4_batch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(Options)]
@@ -367,13 +367,14 @@ class Integrator:
 
     def step_profiled(self, nsteps=1):
         """Host-driven steps with CUDA events around every kernel: returns
-        (stats, {kernel class: (total ms, launches)})."""
+        (stats, {kernel class: (total ms, launches, sites computed)})."""
         st = Stats()
         ms = np.zeros(len(KERNEL_CLASSES))
+        sites = np.zeros(len(KERNEL_CLASSES))
         n = (C.c_longlong * len(KERNEL_CLASSES))()
-        _check(lib().mb4_step_profiled(self._ctx, int(nsteps), C.byref(st), ms.ctypes.data_as(_D), n),
-               "mb4_step_profiled")
-        return st.as_dict(), {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+        _check(lib().mb4_step_profiled(self._ctx, int(nsteps), C.byref(st), ms.ctypes.data_as(_D), n,
+                                       sites.ctypes.data_as(_D)), "mb4_step_profiled")
+        return st.as_dict(), {k: (float(ms[i]), int(n[i]), float(sites[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def set_state_ptr(self, re_ptr, im_ptr, on_device):
         """Set the state from raw pointers (host pinned or device), S doubles each."""
@@ -559,12 +560,14 @@ class Batch:
         st = (Stats * self.B)()
         codes = (C.c_int * self.B)()
         ms = np.zeros(len(KERNEL_CLASSES))
+        sites = np.zeros(len(KERNEL_CLASSES))
         n = (C.c_longlong * len(KERNEL_CLASSES))()
-        rc = lib().mb4_batch_step_profiled(self._ctx, int(nsteps), st, codes, ms.ctypes.data_as(_D), n)
+        rc = lib().mb4_batch_step_profiled(self._ctx, int(nsteps), st, codes, ms.ctypes.data_as(_D), n,
+                                           sites.ctypes.data_as(_D))
         if rc not in (MB4_OK, MB4_ERR_NEWTON_NOT_CONVERGED, MB4_ERR_KRYLOV_BREAKDOWN, MB4_ERR_NONFINITE):
             _check(rc, "mb4_batch_step_profiled")
         return ([s.as_dict() for s in st], list(codes),
-                {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)})
+                {k: (float(ms[i]), int(n[i]), float(sites[i])) for i, k in enumerate(KERNEL_CLASSES)})
 
     def observables(self):
         out = np.zeros(self.B * 6)
