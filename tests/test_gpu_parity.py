@@ -555,17 +555,32 @@ def test_grid2048_mixed_matches_fp64(mb4):
     assert _rel(finals["mixed"], finals["fp64"]) <= 1e-11
 
 
+@pytest.mark.oracle_long("c3_crop")
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_grid128_with_2048_physics_matches_oracle(mb4, precision):
-    """The 128x128 instance with the 2048x2048 physics, 10 steps, against the oracle."""
+    """The 128x128 instance with the 2048x2048 physics over its whole 500 steps against
+    the oracle (the error of the 2048x2048 configuration stated at the size the oracle can
+    follow): 1e-11 relative in l-inf and l2 after 10, 100, 250 and 500 steps, and the
+    GPU's energy within 1e-13 of the oracle's start every 10 steps."""
+    import oracle_jobs
     w = inputs.grid128_crop_of_2048()
-    prob = orc.Problem(w.nx, w.ny, w.potential(), w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
-    u, _ = orc.run(prob, w.psi0(), w.h, 10)
+    want = oracle_jobs.result("c3_crop")
+    errs = {}
     with mb4.from_workload(w, precision=precision) as it:
-        it.step(10)
-        got = it.get_state()
-    assert _rel(got, u) <= 1e-11
-    assert _rel2(got, u) <= 1e-11
+        H0 = it.energy()[0]
+        assert abs(H0 - want["H"][0]) <= 1e-14 * abs(want["H"][0])
+        for n in range(1, w.steps // 10 + 1):
+            it.step(10)
+            H = it.energy()[0]
+            assert abs(H - want["H"][0]) <= 1e-13 * abs(want["H"][0]), (10 * n, H)
+            if 10 * n in want:
+                got = it.get_state()
+                errs[10 * n] = (_rel(got, want[10 * n]), _rel2(got, want[10 * n]))
+    assert sorted(errs) == [10, 100, 250, 500]
+    print(f"\n[{precision}] 128x128 with the 2048x2048 physics vs the oracle, step: (rel l-inf, rel l2) "
+          + ", ".join(f"{n}: ({a:.2e}, {b:.2e})" for n, (a, b) in sorted(errs.items())))
+    for n, (einf, e2) in errs.items():
+        assert einf <= 1e-11 and e2 <= 1e-11, (n, einf, e2)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)

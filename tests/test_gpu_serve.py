@@ -48,9 +48,20 @@ def _solo(mb4, q, **opts):
         return it.get_state()
 
 
+def _oracle(q):
+    from oracle import mb4_oracle as orc
+    prob = orc.Problem(q["nx"], q["ny"], q["V"], q["chi"])
+    u = q["psi"].copy()
+    for _ in range(q["nsteps"]):
+        u = orc.step(prob, u, q["h"])
+    return u
+
+
 def test_served_results_equal_solo_runs(mb4):
     """A burst of 14 requests over 6 shape classes with 2 slots per batch: the
-    classes run concurrently and every result equals its solo run."""
+    classes run concurrently, every result equals its solo run, and every result
+    matches the FP64 oracle's run of the same request to 1e-11 (so the served path is
+    pinned to the oracle directly, not only through the solo path)."""
     reqs = _trace(14, span=0.0)
     with mb4.Server(2 << 30, max_slots=2, keep_states=True, precision="mixed") as srv:
         ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], q["arrival"])
@@ -65,6 +76,7 @@ def test_served_results_equal_solo_runs(mb4):
         assert res["admitted"] >= res["arrival"] - 1e-9 and res["completed"] >= res["admitted"]
         assert abs(res["energy_end"] - res["energy_start"]) <= 1e-13 * abs(res["energy_start"])
         assert _rel(u, _solo(mb4, q, precision="mixed")) <= 1e-12
+        assert _rel(u, _oracle(q)) <= 1e-11
         spans.append((res["admitted"], res["completed"], (q["nx"], q["ny"], q["h"])))
     # different requests were on the GPU at the same time
     overlaps = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
@@ -90,6 +102,7 @@ def test_waiting_requests_take_freed_slots(mb4):
     for q, (res, u) in zip(reqs, results):
         assert res["status"] == 0 and res["steps_done"] == q["nsteps"]
         assert _rel(u, _solo(mb4, q, precision="mixed")) <= 1e-12
+        assert _rel(u, _oracle(q)) <= 1e-11
         spans.append((res["admitted"], res["completed"]))
     assert any(a[0] < b[1] and b[0] < a[1] for a in spans for b in spans if a is not b)   # ran together
     assert sum(1 for b in spans if any(b[0] >= a[1] for a in spans if a is not b)) >= 3  # waited for a slot
