@@ -16,7 +16,9 @@ quantum-mechanical wavepacket dynamics", arXiv:2003.04345):
   K is eq. (Kdefinition), generalised to a hopping tx, ty and an on-site shift
   eps0:  K = -tx (I_Ny (x) C_Nx) - ty (C_Ny (x) I_Nx) + eps0 I,  with C_N the
   periodic adjacency (zero diagonal, ones at +-1).  The paper's Laplacian is
-  tx = 1/hx^2, ty = 1/hy^2, eps0 = 2 tx + 2 ty.
+  tx = 1/hx^2, ty = 1/hy^2, eps0 = 2 tx + 2 ty.  Problem.general takes any Hermitian
+  K instead (the appendix's m-site model; complex transfer integrals such as Peierls
+  phases included): the paper needs only that K be Hermitian (Sec. 2.1).
 * The MB4 coefficients are eq. (Adefinition); the stage polynomial is written
   in Lagrange form on c0 = 0, c1, c2, c3 (eq. Lagrange), and the stage
   equations are Phi(U) = 0 (eq. MB4_3, eq. Phidefinition).  With c3 = 1 the
@@ -191,13 +193,18 @@ class Problem:
 
     @classmethod
     def general(cls, K, V, chi):
-        """A site model with a given kinetic matrix K (S x S, real symmetric, sparse or
-        dense) instead of the grid stencil: the appendix's m-site model, in which K_kj
-        is the transfer between neighbouring sites.  nx = S, ny = 1 label the sites."""
-        K = sp.csr_matrix(K, dtype=np.float64)
+        """A site model with a given kinetic matrix K (S x S, Hermitian, sparse or dense)
+        instead of the grid stencil: the appendix's m-site model, in which K_kj is the
+        transfer between neighbouring sites (complex, e.g. with Peierls phases; the
+        paper asks only that K be Hermitian, Sec. 2.1 and the appendix).  A K with no
+        imaginary part is kept real.  nx = S, ny = 1 label the sites."""
+        K = sp.csr_matrix(K)
+        if np.iscomplexobj(K.data) and not np.any(K.data.imag):
+            K = sp.csr_matrix(K.real)
+        K = sp.csr_matrix(K, dtype=np.complex128 if np.iscomplexobj(K.data) else np.float64)
         S = K.shape[0]
-        if K.shape != (S, S) or abs(K - K.T).max() > 0:
-            raise ValueError("K must be square and symmetric")
+        if K.shape != (S, S) or (S and abs(K - K.conj().T).max() > 0):
+            raise ValueError("K must be square and Hermitian")
         self = cls.__new__(cls)
         self.nx, self.ny, self.S = S, 1, S
         self.tx = self.ty = float("nan")
@@ -280,12 +287,19 @@ def to_complex(r, S):
 def jacobian_real(prob: Problem, u0):
     """J = J_K + J_E + J_I at u0 in the real [p; q] form: eq. (JL) + eq. (JR)
     with gamma = -chi (per site when chi is):
-      J_K + J_E = [[0, A], [-A, 0]],
+      J_K + J_E = [[0, A], [-A, 0]]                 (A = K + V real),
+      J_K + J_E = [[Im A, Re A], [-Re A, Im A]]     (A = K + V complex Hermitian: the
+                  real form of -i A, whose real part acts as Re A q + Im A p and whose
+                  imaginary part as -(Re A p - Im A q)),
       J_I = [[diag(-2 g p q), diag(-g (p^2 + 3 q^2))], [diag(g (3 p^2 + q^2)), diag(2 g p q)]]."""
     p0, q0 = np.real(u0), np.imag(u0)
     g = -prob.chi * np.ones_like(p0)
     A = prob.A
-    JL = sp.bmat([[None, A], [-A, None]])
+    if np.iscomplexobj(A.data):
+        Ar, Ai = sp.csr_matrix(A.real), sp.csr_matrix(A.imag)
+        JL = sp.bmat([[Ai, Ar], [-Ar, Ai]])
+    else:
+        JL = sp.bmat([[None, A], [-A, None]])
     JI = sp.bmat([[sp.diags(-2 * g * p0 * q0), sp.diags(-g * (p0 ** 2 + 3 * q0 ** 2))],
                   [sp.diags(g * (3 * p0 ** 2 + q0 ** 2)), sp.diags(2 * g * p0 * q0)]])
     return sp.csr_matrix(JL + JI)
@@ -367,7 +381,7 @@ def run(prob: Problem, u0, h, nsteps, **kw):
 # Observables (Sec. 2.1 energy terms; Sec. 3.2 participation ratio).
 # ---------------------------------------------------------------------------
 def energy(prob: Problem, u):
-    """(H, U_K, U_E, U_nl) with U_K = u^H K u, U_E = u^H V u,
+    """(H, U_K, U_E, U_nl) with U_K = u^H K u (real for Hermitian K), U_E = u^H V u,
     U_nl = (chi/2) sum |u|^4 = -(gamma/2) ||n||^2; correctly rounded sums."""
     u = np.asarray(u, dtype=np.complex128)
     Ku = prob.K @ u

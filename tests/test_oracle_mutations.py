@@ -182,6 +182,33 @@ def test_factor_moved_between_energy_parts(monkeypatch):
     assert _fails(pins.test_observables_of_a_site_state)
 
 
+def test_complex_jacobian_with_the_imaginary_blocks_flipped(monkeypatch):
+    """The real form of J for a complex A = K + V with the sign of its Im A blocks flipped
+    ([[-Im A, Re A], [-Re A, -Im A]]): the finite-difference pin with a complex K fails."""
+    good = orc.jacobian_real
+
+    def bad(prob, u0):
+        J = good(prob, u0)
+        if not np.iscomplexobj(prob.A.data):
+            return J
+        Ai = sp.csr_matrix(prob.A.imag)
+        return sp.csr_matrix(J - 2 * sp.bmat([[Ai, None], [None, Ai]]))
+    monkeypatch.setattr(orc, "jacobian_real", bad)
+    assert _fails(pins.test_complex_hermitian_jacobian_matches_finite_difference)
+
+
+def test_kinetic_matrix_taken_transposed(monkeypatch):
+    """Problem.general storing K^T (= conj K for a Hermitian K) instead of K: the phases
+    act backwards, the gauge pin and the brute-force residual with a complex K fail."""
+    good = orc.Problem.general.__func__
+
+    def bad(cls, K, V, chi):
+        return good(cls, sp.csr_matrix(K).T, V, chi)
+    monkeypatch.setattr(orc.Problem, "general", classmethod(bad))
+    assert _fails(pins.test_gauge_transformed_kinetic_matrix_gives_the_gauge_transformed_step)
+    assert _fails(pins.test_complex_hermitian_site_model_residual_and_energy)
+
+
 def test_unmutated_oracle_passes_the_same_pins():
     """The control: with the oracle as it stands, every pin used above passes."""
     pins.test_E_row_sums_are_the_nodes()
@@ -196,4 +223,7 @@ def test_unmutated_oracle_passes_the_same_pins():
     pins.test_observables_of_a_plane_wave(True)
     pins.test_observables_of_a_site_state()
     pins.test_participation_ratio_of_spread_states()
+    pins.test_complex_hermitian_jacobian_matches_finite_difference()
+    pins.test_gauge_transformed_kinetic_matrix_gives_the_gauge_transformed_step()
+    pins.test_complex_hermitian_site_model_residual_and_energy()
     assert Fraction(orc.C_PAPER[2]) == 1

@@ -668,3 +668,122 @@ def test_participation_ratio_of_spread_states():
         u[sites] = phase[sites] / math.sqrt(M)
         assert abs(orc.norm2(u) - 1.0) <= 1e-15
         assert abs(orc.participation(u) - 1.0 / M) <= 1e-15 / M
+
+
+# ---------------------------------------------------------------------------
+# Complex Hermitian K (the appendix's m-site model with complex transfer integrals;
+# Sec. 2.1 asks only that K be Hermitian).
+# ---------------------------------------------------------------------------
+def _random_hermitian_K(S, deg, seed, onsite=0.3):
+    """A random sparse Hermitian site model: links t e^{i phi} (Peierls-like phases)."""
+    rng = np.random.default_rng(seed)
+    K = np.zeros((S, S), dtype=np.complex128)
+    for k in range(S):
+        for j in rng.choice(S, size=deg // 2, replace=False):
+            if j != k:
+                w = rng.uniform(-1.5, 1.5) * np.exp(1j * rng.uniform(-math.pi, math.pi))
+                K[k, j] = w
+                K[j, k] = np.conj(w)
+    return K + onsite * np.eye(S)
+
+
+def _f_dense(K, V, chi, u):
+    return -1j * (K @ u + V * u + chi * np.abs(u) ** 2 * u)
+
+
+def test_complex_hermitian_site_model_residual_and_energy():
+    """With a complex Hermitian K the oracle's residual equals the brute-force
+    quadrature of eq. (MB4_3), and MB4 keeps H = u^H (K+V) u + (1/2) sum chi |u|^4 (real
+    for Hermitian K) to rounding over 30 steps."""
+    rng = np.random.default_rng(81)
+    S = 28
+    K = _random_hermitian_K(S, 6, 82)
+    V = rng.uniform(-1, 1, S)
+    chi = _chi_field(S, 83)
+    prob = orc.Problem.general(K, V, chi)
+    assert np.iscomplexobj(prob.A.data)
+    u0 = _rand_state(rng, S, 0.5)
+    U = u0[None, :] + 0.1 * np.vstack([_rand_state(rng, S) for _ in range(3)])
+    got = orc.residual(prob, u0, U, 0.03)
+    want = _brute_phi_dense(K, V, chi, u0, U, 0.03)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(U))
+    u, H0, drift = u0, orc.energy(prob, u0)[0], 0.0
+    want_H = float(np.real(np.vdot(u0, (K + np.diag(V)) @ u0))) + 0.5 * float(np.sum(chi * np.abs(u0) ** 4))
+    assert abs(H0 - want_H) <= 1e-13 * abs(H0)
+    for _ in range(30):
+        u = orc.step(prob, u, 0.02)
+        drift = max(drift, abs(orc.energy(prob, u)[0] - H0) / abs(H0))
+    assert drift <= 1e-13, drift
+
+
+def test_complex_hermitian_jacobian_matches_finite_difference():
+    """The real form of J with a complex A = K + V ([[Im A, Re A], [-Re A, Im A]] plus
+    eq. (JR)) against central differences of f(u) = -i[(K+V)u + chi|u|^2 u]."""
+    rng = np.random.default_rng(84)
+    S = 10
+    K = _random_hermitian_K(S, 4, 85)
+    V = rng.uniform(-1, 1, S)
+    chi = 1.3
+    prob = orc.Problem.general(K, V, chi)
+    u0 = _rand_state(rng, S)
+    J = orc.jacobian_real(prob, u0).toarray()
+
+    def freal(x):
+        f = _f_dense(K, V, chi, x[:S] + 1j * x[S:])
+        return np.concatenate([f.real, f.imag])
+
+    x0 = np.concatenate([u0.real, u0.imag])
+    d = 1e-6
+    Jfd = np.zeros((2 * S, 2 * S))
+    for k in range(2 * S):
+        e = np.zeros(2 * S)
+        e[k] = d
+        Jfd[:, k] = (freal(x0 + e) - freal(x0 - e)) / (2 * d)
+    assert np.max(np.abs(J - Jfd)) < 1e-7 * max(1.0, np.max(np.abs(J)))
+
+
+def test_gauge_transformed_kinetic_matrix_gives_the_gauge_transformed_step():
+    """A site-dependent phase G = diag(e^{i theta_k}) is a symmetry of the equation:
+    |G u|^2 = |u|^2 and V is diagonal, so with K' = G K G^H the flow maps G u0 to
+    G u(t), and MB4 (affine-covariant, like every Runge-Kutta method) maps G u0 to
+    G u1.  K' is complex although K -- here the grid stencil -- is real, so this ties
+    the complex-K route to the real one."""
+    rng = np.random.default_rng(86)
+    nx, ny = 5, 4
+    S = nx * ny
+    V = rng.uniform(-1, 1, S)
+    grid = orc.Problem(nx, ny, V, 1.2, tx=1.1, ty=0.7, eps0=0.3)
+    theta = rng.uniform(-math.pi, math.pi, S)
+    G = np.exp(1j * theta)
+    Kc = (G[:, None] * grid.K.toarray()) * np.conj(G)[None, :]
+    Kc = 0.5 * (Kc + Kc.conj().T)          # Hermitian to the last bit (the products round)
+    gauge = orc.Problem.general(Kc, V, 1.2)
+    u0 = _rand_state(rng, S, 0.5)
+    u1 = orc.step(grid, u0, 0.02)
+    u1g = orc.step(gauge, G * u0, 0.02)
+    assert np.max(np.abs(u1g - G * u1)) <= 1e-14 * np.max(np.abs(u0))
+
+
+def test_linear_complex_K_step_equals_stability_function():
+    """chi = 0 with a complex Hermitian K: n steps equal Q R(-i h Lambda)^n Q^H u0 with
+    K + V = Q Lambda Q^H, and the norm is kept (|R(iy)| = 1)."""
+    sympy, z, R = _stability_function()
+    Rf = sympy.lambdify(z, R, "numpy")
+    rng = np.random.default_rng(87)
+    S = 24
+    K = _random_hermitian_K(S, 6, 88)
+    V = rng.uniform(-1, 1, S)
+    lam, Q = np.linalg.eigh(K + np.diag(V))
+    h, n = 0.02, 8
+    u0 = _rand_state(rng, S)
+    want = Q @ (Rf(-1j * h * lam) ** n * (Q.conj().T @ u0))
+    got, _ = orc.run(orc.Problem.general(K, V, 0.0), u0, h, n)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(u0))
+    assert abs(orc.norm2(got) - orc.norm2(u0)) <= 1e-13 * orc.norm2(u0)
+
+
+def test_general_rejects_a_non_hermitian_K():
+    K = _random_hermitian_K(8, 4, 89)
+    K[0, 1] += 0.1j
+    with pytest.raises(ValueError):
+        orc.Problem.general(K, np.zeros(8), 1.0)
