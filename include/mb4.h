@@ -179,21 +179,29 @@ int mb4_create(const mb4_grid* grid, const mb4_potential* pot, const mb4_nonline
 
 /* A general kinetic matrix in place of the grid stencil: the m-site model of the
  * paper's appendix, where K_kj is the transfer between neighbouring sites (molecules).
- * K = onsite * I + T with T real symmetric, at most max_degree nonzeros per row, given
- * row-major: nbr[k * max_degree + e] is a neighbour of site k (or -1 for an unused slot),
- * t[k * max_degree + e] the matching K_kj.  Both arrays are host memory, copied. */
+ * K = onsite * I + T with T Hermitian (Sec. 2.1 asks only that K be Hermitian), at most
+ * max_degree nonzeros per row, given row-major: nbr[k * max_degree + e] is a neighbour of
+ * site k (or -1 for an unused slot), t[k * max_degree + e] the real part of the matching
+ * K_kj and t_im[k * max_degree + e] its imaginary part (complex transfer integrals, e.g.
+ * Peierls phases; t_im = NULL for a real symmetric T).  All arrays are host memory,
+ * copied. */
 #define MB4_MAX_DEGREE 16
 typedef struct {
     int S;                /* sites, >= 1                                              */
     int max_degree;       /* 1..MB4_MAX_DEGREE                                        */
     const int* nbr;       /* S * max_degree, values in -1..S-1, no self links          */
-    const double* t;      /* S * max_degree, finite; t(k,j) = t(j,k) (symmetric)       */
+    const double* t;      /* S * max_degree, finite; t(k,j) = t(j,k)                   */
     double onsite;        /* diagonal of K (V adds to it)                             */
+    const double* t_im;   /* NULL, or S * max_degree, finite; t_im(k,j) = -t_im(j,k),
+                             so that K_jk = conj(K_kj) (Hermitian)                    */
 } mb4_sparse_kinetic;
 
-/* mb4_create for a general kinetic matrix (one instance).  Rejects a non-symmetric T,
- * out-of-range or self-linked neighbours, and precondition = 1 (the spectral
- * preconditioner needs the grid).  The FP32 path builds its Krylov basis one level per
+/* mb4_create for a general kinetic matrix (one instance).  Rejects a T that is not
+ * Hermitian (bit for bit: t(j,k) == t(k,j) and t_im(j,k) == -t_im(k,j)), out-of-range or
+ * self-linked neighbours, and precondition = 1 (the spectral preconditioner needs the
+ * grid).  With a complex T the state, stages and Krylov vectors are unchanged in form;
+ * the kinetic term is a complex sparse product, and J's kinetic block is the real form
+ * of -i K (eq. JL with K complex).  The FP32 path builds its Krylov basis one level per
  * launch (no matrix-powers tiles).  Every other entry point of a context applies. */
 int mb4_create_sparse(const mb4_sparse_kinetic* K, const mb4_potential* pot, const mb4_nonlinearity* nl,
                       double h, const mb4_options* opt, mb4_ctx** out);

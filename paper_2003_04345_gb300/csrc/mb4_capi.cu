@@ -42,7 +42,7 @@ struct mb4_batch {
   std::vector<long long> base_steps, base_newton;
   std::vector<double> ebar;       // per instance: mean of onsite + V (spectral preconditioner)
   int* ell_nbr = nullptr;         // general kinetic matrix (mb4_create_sparse), device
-  double* ell_w = nullptr;
+  void* ell_w = nullptr;          // double, or double2 for a complex K
   void* ell_wt = nullptr;
 };
 
@@ -528,8 +528,10 @@ double mean_of(const double* x, size_t n) {
 // A general kinetic matrix for make_batch: its off-diagonal in slot-major ELL form.
 struct EllHost {
   int deg = 0;
+  bool cplx = false;         // complex Hermitian K
   std::vector<int> nbr;      // deg * S, nbr[e * S + k] = j or -1
-  std::vector<double> w;     // deg * S, K_kj
+  std::vector<double> w;     // deg * S, Re K_kj
+  std::vector<double> wi;    // deg * S, Im K_kj (cplx only)
 };
 
 int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const double* chi, double h,
@@ -555,6 +557,7 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
     if (B != 1 || p.precond) return MB4_ERR_INVALID_ARG;   // one instance; no spectral preconditioner
     p.ell = 1;
     p.ell_deg = ell->deg;
+    p.ell_cplx = ell->cplx ? 1 : 0;
   }
   p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B)
                                               : gram_blocks_per_system<double>(p.s, B);
@@ -610,7 +613,9 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
       for (size_t k = 0; k < S; ++k) {
         double r = std::fabs(D[k]);
         for (int e = 0; e < ell->deg; ++e)
-          if (ell->nbr[(size_t)e * S + k] >= 0) r += std::fabs(ell->w[(size_t)e * S + k]);
+          if (ell->nbr[(size_t)e * S + k] >= 0)
+            r += ell->cplx ? std::hypot(ell->w[(size_t)e * S + k], ell->wi[(size_t)e * S + k])
+                           : std::fabs(ell->w[(size_t)e * S + k]);
         theta = std::fmax(theta, r);
       }
       if (!(theta > 0.0)) theta = 1.0;
@@ -619,19 +624,25 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   }
   if (ell) {                                    // off-diagonal in FP64 and, scaled by 1/theta, in TK
     const size_t n = (size_t)ell->deg * S;
+    const int nc = ell->cplx ? 2 : 1;            // (re, im) pairs for a complex K
     MB4_CHECK(dalloc(c, (void**)&c->ell_nbr, n * sizeof(int)));
-    MB4_CHECK(dalloc(c, (void**)&c->ell_w, n * sizeof(double)));
-    MB4_CHECK(dalloc(c, &c->ell_wt, n * tk));
+    MB4_CHECK(dalloc(c, &c->ell_w, n * nc * sizeof(double)));
+    MB4_CHECK(dalloc(c, &c->ell_wt, n * nc * tk));
     MB4_TRY(cudaMemcpy(c->ell_nbr, ell->nbr.data(), n * sizeof(int), cudaMemcpyHostToDevice));
-    MB4_TRY(cudaMemcpy(c->ell_w, ell->w.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<double> w(n * nc);
+    for (size_t q = 0; q < n; ++q) {
+      w[q * nc] = ell->w[q];
+      if (ell->cplx) w[q * nc + 1] = ell->wi[q];
+    }
+    MB4_TRY(cudaMemcpy(c->ell_w, w.data(), n * nc * sizeof(double), cudaMemcpyHostToDevice));
     if (tk == sizeof(float)) {
-      std::vector<float> wt(n);
-      for (size_t q = 0; q < n; ++q) wt[q] = (float)(ell->w[q] * ic[0].inv_theta);
-      MB4_TRY(cudaMemcpy(c->ell_wt, wt.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+      std::vector<float> wt(n * nc);
+      for (size_t q = 0; q < n * nc; ++q) wt[q] = (float)(w[q] * ic[0].inv_theta);
+      MB4_TRY(cudaMemcpy(c->ell_wt, wt.data(), n * nc * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-      std::vector<double> wt(n);
-      for (size_t q = 0; q < n; ++q) wt[q] = ell->w[q] * ic[0].inv_theta;
-      MB4_TRY(cudaMemcpy(c->ell_wt, wt.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+      std::vector<double> wt(n * nc);
+      for (size_t q = 0; q < n * nc; ++q) wt[q] = w[q] * ic[0].inv_theta;
+      MB4_TRY(cudaMemcpy(c->ell_wt, wt.data(), n * nc * sizeof(double), cudaMemcpyHostToDevice));
     }
     p.ell_nbr = c->ell_nbr;
     p.ell_w = c->ell_w;
@@ -1000,24 +1011,30 @@ int mb4_create_sparse(const mb4_sparse_kinetic* K, const mb4_potential* pot, con
   if (o.precondition) return MB4_ERR_INVALID_ARG;
   const size_t S = (size_t)K->S;
   const int deg = K->max_degree;
-  // row-major input -> slot-major ELL; entries in range, no self links, finite, symmetric
+  // row-major input -> slot-major ELL; entries in range, no self links, finite, Hermitian
   EllHost ell;
   ell.deg = deg;
+  ell.cplx = (K->t_im != nullptr);
   ell.nbr.assign((size_t)deg * S, -1);
   ell.w.assign((size_t)deg * S, 0.0);
+  if (ell.cplx) ell.wi.assign((size_t)deg * S, 0.0);
   for (size_t k = 0; k < S; ++k)
     for (int e = 0; e < deg; ++e) {
       const int j = K->nbr[k * deg + e];
       if (j < -1 || j >= K->S || j == (int)k) return MB4_ERR_INVALID_ARG;
       if (j < 0) continue;
       const double w = K->t[k * deg + e];
-      if (!std::isfinite(w)) return MB4_ERR_INVALID_ARG;
-      int found = 0;
+      const double wi = ell.cplx ? K->t_im[k * deg + e] : 0.0;
+      if (!std::isfinite(w) || !std::isfinite(wi)) return MB4_ERR_INVALID_ARG;
+      int found = 0;                             // K_jk = conj(K_kj)
       for (int f = 0; f < deg; ++f)
-        if (K->nbr[(size_t)j * deg + f] == (int)k && K->t[(size_t)j * deg + f] == w) found = 1;
-      if (!found) return MB4_ERR_INVALID_ARG;   // K must be symmetric
+        if (K->nbr[(size_t)j * deg + f] == (int)k && K->t[(size_t)j * deg + f] == w &&
+            (!ell.cplx || K->t_im[(size_t)j * deg + f] == -wi))
+          found = 1;
+      if (!found) return MB4_ERR_INVALID_ARG;   // K must be Hermitian
       ell.nbr[(size_t)e * S + k] = j;
       ell.w[(size_t)e * S + k] = w;
+      if (ell.cplx) ell.wi[(size_t)e * S + k] = wi;
     }
   std::vector<double> V;
   MB4_CHECK(potential_to_host(pot, S, &V));

@@ -149,6 +149,26 @@ __device__ __forceinline__ T2 ell_offdiag(const int* __restrict__ nbr, const T* 
   return s;
 }
 
+// The same for a complex Hermitian K: w[e * S + k] = K_kj as (re, im), and the sum is
+// the complex product sum_j K_kj x_j.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 ell_offdiag_c(const int* __restrict__ nbr, const T2* __restrict__ w, int deg, int S,
+                                            int k, const T2* __restrict__ x) {
+  T2 s;
+  s.x = 0;
+  s.y = 0;
+  for (int e = 0; e < deg; ++e) {
+    const int j = nbr[(size_t)e * S + k];
+    if (j >= 0) {
+      const T2 wv = w[(size_t)e * S + k];
+      const T2 xv = x[j];
+      s.x += wv.x * xv.x - wv.y * xv.y;
+      s.y += wv.x * xv.y + wv.y * xv.x;
+    }
+  }
+  return s;
+}
+
 // Offsets of instance b's data.
 __device__ __forceinline__ size_t plane(int b, int S) { return (size_t)b * S; }
 __device__ __forceinline__ size_t stage(int b, int m, int S) { return ((size_t)b * 3 + m) * S; }

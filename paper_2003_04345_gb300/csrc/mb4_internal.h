@@ -52,6 +52,7 @@ struct StepParams {
   // T's off-diagonal in slot-major ELL form, nbr[e * S + k] = j or -1, w = K_kj (FP64) and
   // wt = K_kj / theta in the Krylov precision, e < ell_deg
   int ell, ell_deg;
+  int ell_cplx;            // complex Hermitian K: ell_w holds double2 (re, im), ell_wt Vec2<TK>
   // grid stencil with the x hopping factored out (tx != 0): the residual reads D / tx
   // (DevBuffers::dtx) and forms h lam_i tx (D/tx x - (x_x- + x_x+) - (ty/tx)(x_y- + x_y+)),
   // one FP64 instruction less per component than h lam_i (D x - tx (..) - ty (..))
@@ -60,7 +61,7 @@ struct StepParams {
   // and the matvec spends 5 FP64 instructions per component instead of 6
   int mv_unit;
   const int* ell_nbr;
-  const double* ell_w;
+  const void* ell_w;       // double (real K) or double2 (complex K)
   const void* ell_wt;
   int bs_site, bs_residual, bs_matvec, bs_update;   // threads per block of the per-site kernels
                                                     // (bs_site: k_setup, k_accept)

@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const d
     double d = D[plane(b, S) + k];
     double2 s0;
     if constexpr (ELL) {
-      const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, ub);
+      const double2 o = p.ell_cplx
+                            ? ell_offdiag_c<double, double2>(p.ell_nbr, (const double2*)p.ell_w, p.ell_deg, S, k, ub)
+                            : ell_offdiag<double, double2>(p.ell_nbr, (const double*)p.ell_w, p.ell_deg, S, k, ub);
       s0.x = fma(d, c.x, o.x);
       s0.y = fma(d, c.y, o.y);
     } else {
@@ -145,7 +147,7 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 // exact for the degree-11 integrand).  (The u0 terms: T^-1 E T = Lambda and
 // T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
 // KM selects the kinetic term: 0 the grid stencil, 1 the grid stencil with tx factored
-// out (StepParams::kin_unit), 2 the general sparse K (ELL).
+// out (StepParams::kin_unit), 2 the general sparse K (ELL), 3 a complex Hermitian one.
 // ---------------------------------------------------------------------------
 template <typename TO, bool CHIF, int KM>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, const double2* __restrict__ u,
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
   if (k >= S) return;
   const InstConst& C = ic[b];
   Nbr n;
-  if constexpr (KM != 2) n = neighbours(k, p.nx, p.ny, S);
+  if constexpr (KM < 2) n = neighbours(k, p.nx, p.ny, S);
   const double2 u0 = u[plane(b, S) + k];
   const double2 s0 = S0[plane(b, S) + k];
   const double d = D[plane(b, S) + k];           // D / tx when KM == 1
@@ -181,8 +183,10 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
     const double2 c = P[k];
     dU[m] = c;
     double sx, sy, hl;
-    if constexpr (KM == 2) {
-      const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, P);
+    if constexpr (KM >= 2) {
+      const double2 o =
+          (KM == 3) ? ell_offdiag_c<double, double2>(p.ell_nbr, (const double2*)p.ell_w, p.ell_deg, S, k, P)
+                    : ell_offdiag<double, double2>(p.ell_nbr, (const double*)p.ell_w, p.ell_deg, S, k, P);
       sx = fma(d, c.x, o.x);
       sy = fma(d, c.y, o.y);
       hl = p.hlam[m];
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
 }
 
 // Kinetic mode of the residual and the FP64 basis (template argument KM).
-inline int kin_mode(const StepParams& p) { return p.ell ? 2 : (p.kin_unit ? 1 : 0); }
+inline int kin_mode(const StepParams& p) { return p.ell ? (p.ell_cplx ? 3 : 2) : (p.kin_unit ? 1 : 0); }
 
 template <typename TK>
 void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, cudaStream_t s) {
@@ -243,6 +247,7 @@ void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first, 
            (const double2*)b.S0, (const double2*)b.Ubar, (TK2*)b.v, os, sf, (const double*)b.chi,               \
            (const InstConst*)b.ic, (const InstStatus*)b.is)
   switch (kin_mode(p)) {
+    case 3: if (p.chi_field) MB4_RES(true, 3); else MB4_RES(false, 3); break;
     case 2: if (p.chi_field) MB4_RES(true, 2); else MB4_RES(false, 2); break;
     case 1: if (p.chi_field) MB4_RES(true, 1); else MB4_RES(false, 1); break;
     default: if (p.chi_field) MB4_RES(true, 0); else MB4_RES(false, 0); break;
@@ -258,6 +263,7 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
   k_residual<double, CF, KM><<<grid, p.bs_residual, 0, s>>>(p, b.u, D, b.S0, b.Ubar, phibar3, 3LL * p.S, 0, b.chi, \
                                                             b.ic, b.is)
   switch (kin_mode(p)) {
+    case 3: if (p.chi_field) MB4_RES(true, 3); else MB4_RES(false, 3); break;
     case 2: if (p.chi_field) MB4_RES(true, 2); else MB4_RES(false, 2); break;
     case 1: if (p.chi_field) MB4_RES(true, 1); else MB4_RES(false, 1); break;
     default: if (p.chi_field) MB4_RES(true, 0); else MB4_RES(false, 0); break;
@@ -285,13 +291,16 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S) return;
   const JCoef<TK> j = jc[plane(b, S) + k];
-  if constexpr (KM == 2) {
-    // (J x)_re = a xp + e1 xq + sum_j (K_kj / theta) xq_j, (J x)_im = -e2 xp - a xq - sum_j (K_kj / theta) xp_j
+  if constexpr (KM >= 2) {
+    // (J x)_re = a xp + e1 xq + Im(sum_j (K_kj / theta) x_j), (J x)_im = -e2 xp - a xq - Re(sum_j ..):
+    // with s = sum_j K_kj x_j / theta (a complex product when K is complex), the kinetic
+    // part of J x is the real form of -i s (eq. JL)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const TK2* P = v + level(b, a_in, i, p.s, S);
       const TK2 c = P[k];
-      const TK2 s = ell_offdiag<TK, TK2>(p.ell_nbr, (const TK*)p.ell_wt, p.ell_deg, S, k, P);
+      const TK2 s = (KM == 3) ? ell_offdiag_c<TK, TK2>(p.ell_nbr, (const TK2*)p.ell_wt, p.ell_deg, S, k, P)
+                              : ell_offdiag<TK, TK2>(p.ell_nbr, (const TK*)p.ell_wt, p.ell_deg, S, k, P);
       TK2 o;
       o.x = j.a * c.x + j.e1 * c.y + s.y;
       o.y = -j.e2 * c.x - j.a * c.y - s.x;
@@ -717,7 +726,8 @@ void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
     return;
   }
   dim3 grid((p.S + p.bs_matvec - 1) / p.bs_matvec, p.B);
-  auto kern = p.ell ? k_matvec<TK, 2> : (sizeof(TK) == sizeof(double) && p.mv_unit) ? k_matvec<TK, 1> : k_matvec<TK, 0>;
+  auto kern = p.ell ? (p.ell_cplx ? k_matvec<TK, 3> : k_matvec<TK, 2>)
+                    : (sizeof(TK) == sizeof(double) && p.mv_unit) ? k_matvec<TK, 1> : k_matvec<TK, 0>;
   for (int a = 0; a < p.s; ++a)
     launch_k(p.pdl != 0, kern, grid, dim3(p.bs_matvec), 0, s, p, (const JCoef<TK>*)b.jc, (TK2*)b.v, a,
              (const InstConst*)b.ic, (const InstStatus*)b.is);
@@ -1154,7 +1164,9 @@ __global__ void __launch_bounds__(256) k_observables(StepParams p, const double2
     const double2 c = ub[k];
     double Kx, Ky;
     if constexpr (ELL) {
-      const double2 o = ell_offdiag<double, double2>(p.ell_nbr, p.ell_w, p.ell_deg, S, k, ub);
+      const double2 o = p.ell_cplx
+                            ? ell_offdiag_c<double, double2>(p.ell_nbr, (const double2*)p.ell_w, p.ell_deg, S, k, ub)
+                            : ell_offdiag<double, double2>(p.ell_nbr, (const double*)p.ell_w, p.ell_deg, S, k, ub);
       Kx = fma(p.eps0, c.x, o.x);
       Ky = fma(p.eps0, c.y, o.y);
     } else {

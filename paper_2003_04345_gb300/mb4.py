@@ -60,7 +60,7 @@ class Nonlinearity(C.Structure):
 
 class SparseKinetic(C.Structure):
     _fields_ = [("S", C.c_int), ("max_degree", C.c_int), ("nbr", C.c_void_p), ("t", C.c_void_p),
-                ("onsite", C.c_double)]
+                ("onsite", C.c_double), ("t_im", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -268,24 +268,29 @@ class Integrator:
 
     @classmethod
     def sparse(cls, K, V, chi, h, precision="fp64", **opts):
-        """A context for a general kinetic matrix (mb4_create_sparse): K is S x S, real
-        symmetric (dense or scipy sparse).  Its diagonal is folded into V."""
-        Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K, dtype=np.float64)
+        """A context for a general kinetic matrix (mb4_create_sparse): K is S x S,
+        Hermitian, real or complex (dense or scipy sparse).  Its (real) diagonal is folded
+        into V."""
+        Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K)
+        cplx = np.iscomplexobj(Kd) and bool(np.any(Kd.imag))
+        Kd = Kd.astype(np.complex128 if cplx else np.float64)
         S = Kd.shape[0]
         off = Kd - np.diag(np.diag(Kd))
         deg = max(1, int((off != 0).sum(axis=1).max()))
         nbr = -np.ones((S, deg), dtype=np.int32)
         t = np.zeros((S, deg))
+        ti = np.zeros((S, deg))
         for k in range(S):
             js = np.nonzero(off[k])[0]
             nbr[k, :len(js)] = js
-            t[k, :len(js)] = off[k, js]
-        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(S) + np.diag(Kd))
+            t[k, :len(js)] = off[k, js].real
+            ti[k, :len(js)] = off[k, js].imag
+        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(S) + np.diag(Kd).real)
         self = cls.__new__(cls)
         self.nx, self.ny, self.S, self.h = S, 1, S, float(h)
         self.precision = precision
         self._ctx = _P()
-        spk = SparseKinetic(S, deg, nbr.ctypes.data, t.ctypes.data, 0.0)
+        spk = SparseKinetic(S, deg, nbr.ctypes.data, t.ctypes.data, 0.0, ti.ctypes.data if cplx else None)
         _check(lib().mb4_create_sparse(C.byref(spk), C.byref(Potential(Vh.ctypes.data, 0)),
                                        C.byref(Nonlinearity(float(chi))), self.h,
                                        C.byref(_options(precision=precision, **opts)), C.byref(self._ctx)),

@@ -634,6 +634,92 @@ def test_general_kinetic_matrix_matches_oracle(mb4, precision):
         assert abs(it.energy()[0] - H0) <= 1e-13 * abs(H0)
 
 
+def _random_hermitian_graph(S, deg, seed, onsite=0.3):
+    """Random sparse Hermitian K: links t e^{i phi} (Peierls-like phases)."""
+    rng = np.random.default_rng(seed)
+    K = np.zeros((S, S), dtype=np.complex128)
+    for k in range(S):
+        for j in rng.choice(S, size=deg // 2, replace=False):
+            if j != k:
+                w = rng.uniform(-1.5, 1.5) * np.exp(1j * rng.uniform(-math.pi, math.pi))
+                K[k, j] = w
+                K[j, k] = np.conj(w)
+    return K + onsite * np.eye(S)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_complex_hermitian_kinetic_matrix_matches_oracle(mb4, precision):
+    """A complex Hermitian K (the m-site model with Peierls-like phases on a random graph,
+    per-site chi): trajectory to 1e-11 and energy to 1e-13 against the oracle."""
+    S, h, steps = 300, 0.01, 10
+    K = _random_hermitian_graph(S, 6, 61)
+    rng = np.random.default_rng(62)
+    V = rng.uniform(-1, 1, S)
+    chi = rng.uniform(-2, 2, S)
+    psi = (rng.normal(size=S) + 1j * rng.normal(size=S)) / np.sqrt(2 * S)
+    prob = orc.Problem.general(K, V, chi)
+    u = psi.copy()
+    for _ in range(steps):
+        u = orc.step(prob, u, h)
+    with mb4.Integrator.sparse(K, V, 0.0, h, precision=precision, site_chi=True) as it:
+        it.set_chi_field(chi)
+        it.set_state(psi)
+        H0 = it.energy()[0]
+        assert abs(H0 - orc.energy(prob, psi)[0]) <= 1e-14 * abs(H0)
+        o = it.observables()
+        _, UK, UE, UI = orc.energy(prob, psi)
+        for got, want in ((o["U_K"], UK), (o["U_E"], UE), (o["U_nl"], UI)):
+            assert abs(got - want) <= 1e-14 * (abs(UK) + abs(UE) + abs(UI))
+        it.step(steps)
+        got = it.get_state()
+        assert _rel(got, u) <= 1e-11, _rel(got, u)
+        assert _rel2(got, u) <= 1e-11
+        assert abs(it.energy()[0] - H0) <= 1e-13 * abs(H0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_gauge_transformed_grid_equals_the_grid(mb4, precision):
+    """K' = G K G^H with G = diag(e^{i theta}) and K the 5-point stencil: the complex
+    sparse path started from G u0 gives G times the grid path's result (a symmetry of
+    the equation that MB4 keeps), to 1e-13 after 10 steps."""
+    w = inputs.grid16_fp64()
+    prob = orc.Problem(w.nx, w.ny, w.potential(), w.chi, tx=w.tx, ty=w.ty, eps0=w.eps0)
+    theta = np.random.default_rng(63).uniform(-math.pi, math.pi, w.S)
+    G = np.exp(1j * theta)
+    Kc = (G[:, None] * prob.K.toarray()) * np.conj(G)[None, :]
+    Kc = 0.5 * (Kc + Kc.conj().T)
+    with mb4.from_workload(w, precision=precision) as a, \
+            mb4.Integrator.sparse(Kc, w.potential(), w.chi, w.h, precision=precision) as b:
+        b.set_state(G * w.psi0())
+        a.step(10)
+        b.step(10)
+        assert _rel(b.get_state(), G * a.get_state()) <= 1e-13
+
+
+def test_complex_kinetic_matrix_rejects_a_non_hermitian_one(mb4):
+    from paper_2003_04345_gb300.mb4 import C, Nonlinearity, Potential, SparseKinetic, _P, _options, lib
+    S = 4
+    V = np.zeros(S)
+    nb = np.ascontiguousarray(np.array([[1], [0], [3], [2]], dtype=np.int32))
+    tt = np.ascontiguousarray(np.ones((4, 1)))
+    for ti in ([[0.5], [0.5], [0.2], [-0.2]],      # Im K_01 = Im K_10: symmetric, not Hermitian
+               [[0.5], [-0.4], [0.0], [0.0]]):     # not the conjugate
+        tim = np.ascontiguousarray(np.array(ti, dtype=np.float64))
+        ctx = _P()
+        rc = lib().mb4_create_sparse(C.byref(SparseKinetic(S, 1, nb.ctypes.data, tt.ctypes.data, 0.0,
+                                                           tim.ctypes.data)),
+                                     C.byref(Potential(V.ctypes.data, 0)), C.byref(Nonlinearity(1.0)), 0.01,
+                                     C.byref(_options()), C.byref(ctx))
+        assert rc == mb4.MB4_ERR_INVALID_ARG
+    tim = np.ascontiguousarray(np.array([[0.5], [-0.5], [0.2], [-0.2]], dtype=np.float64))
+    ctx = _P()
+    rc = lib().mb4_create_sparse(C.byref(SparseKinetic(S, 1, nb.ctypes.data, tt.ctypes.data, 0.0, tim.ctypes.data)),
+                                 C.byref(Potential(V.ctypes.data, 0)), C.byref(Nonlinearity(1.0)), 0.01,
+                                 C.byref(_options()), C.byref(ctx))
+    assert rc == mb4.MB4_OK
+    lib().mb4_destroy(ctx)
+
+
 def test_general_kinetic_matrix_of_the_grid_equals_the_grid(mb4):
     """The 5-point stencil handed over as a matrix gives the grid context's step."""
     w = inputs.grid16_fp64()
