@@ -269,8 +269,9 @@ class Integrator:
     @classmethod
     def sparse(cls, K, V, chi, h, precision="fp64", **opts):
         """A context for a general kinetic matrix (mb4_create_sparse): K is S x S,
-        Hermitian, real or complex (dense or scipy sparse).  Its (real) diagonal is folded
-        into V."""
+        Hermitian, real or complex (dense or scipy sparse).  A constant diagonal is passed
+        as K's on-site term (so U_K and U_E split as for K and V); a diagonal that varies
+        from site to site is folded into V (U_E then carries it)."""
         Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K)
         cplx = np.iscomplexobj(Kd) and bool(np.any(Kd.imag))
         Kd = Kd.astype(np.complex128 if cplx else np.float64)
@@ -285,12 +286,14 @@ class Integrator:
             nbr[k, :len(js)] = js
             t[k, :len(js)] = off[k, js].real
             ti[k, :len(js)] = off[k, js].imag
-        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(S) + np.diag(Kd).real)
+        dg = np.diag(Kd).real
+        onsite = float(dg[0]) if S and np.all(dg == dg[0]) else 0.0
+        Vh = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(S) + (dg - onsite))
         self = cls.__new__(cls)
         self.nx, self.ny, self.S, self.h = S, 1, S, float(h)
         self.precision = precision
         self._ctx = _P()
-        spk = SparseKinetic(S, deg, nbr.ctypes.data, t.ctypes.data, 0.0, ti.ctypes.data if cplx else None)
+        spk = SparseKinetic(S, deg, nbr.ctypes.data, t.ctypes.data, onsite, ti.ctypes.data if cplx else None)
         _check(lib().mb4_create_sparse(C.byref(spk), C.byref(Potential(Vh.ctypes.data, 0)),
                                        C.byref(Nonlinearity(float(chi))), self.h,
                                        C.byref(_options(precision=precision, **opts)), C.byref(self._ctx)),
