@@ -103,6 +103,7 @@ def kernel_rooflines(prof, precision, s, hbm_gbs, fp64_flops, powers=True, pred_
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_grid512.txt")
 KERNEL_SOURCES = ("paper_2003_04345_gb300/csrc/mb4_kernels.cu", "paper_2003_04345_gb300/csrc/mb4_device.cuh",
+                  "paper_2003_04345_gb300/csrc/mb4_phases.cuh", "paper_2003_04345_gb300/csrc/mb4_persist.cu",
                   "paper_2003_04345_gb300/csrc/mb4_precond.cu", "paper_2003_04345_gb300/csrc/mb4_internal.h")
 
 
@@ -246,11 +247,14 @@ def run_ours(args):
     flush = lambda: flush_buf.zero_()
 
     results = {}
-    for precision in ("fp64", "mixed", "fp64_alg1"):
+    for precision in ("fp64", "mixed", "fp64_alg1", "fp64_persistent", "mixed_persistent"):
         # fp64_alg1: the FP64 path with Algorithm 1's Newton start U^0 = e3 (x) u0 instead
-        # of the default extrapolated start (same equations, same tolerance)
+        # of the default extrapolated start (same equations, same tolerance);
+        # *_persistent: each step one persistent cooperative kernel (same results bit for bit)
         start = 0 if precision == "fp64_alg1" else None
-        it = mb4.from_workload(w, precision=precision.split("_")[0], stream=stream, newton_start=start)
+        pers = 1 if precision.endswith("_persistent") else 0
+        it = mb4.from_workload(w, precision=precision.split("_")[0], stream=stream, newton_start=start,
+                               persistent=pers)
         o0 = it.observables()
         it.step(W)
         torch.cuda.synchronize()
@@ -284,7 +288,7 @@ def run_ours(args):
             "launches": K * 3 + newton * ((s_dim if precision.startswith("fp64") else 1) + 4) + 2 * obs_calls,
             "obs_calls": obs_calls,
         }
-        if precision == "fp64_alg1":
+        if precision == "fp64_alg1" or pers:
             it.close()
             continue
         # per-kernel device times from the event-instrumented run of the same steps;
@@ -385,6 +389,12 @@ def run_ours(args):
                              "newton_per_step": results["fp64_alg1"]["newton_per_step"],
                              "energy_drift": results["fp64_alg1"]["energy_drift"],
                              "note": "FP64 path with U^0 = e3 (x) u0 (newton_start = 0)"},
+        "persistent": {pr: {"value": results[pr + "_persistent"]["value"],
+                            "ms_per_step": results[pr + "_persistent"]["ms_per_step"],
+                            "newton_per_step": results[pr + "_persistent"]["newton_per_step"],
+                            "energy_drift": results[pr + "_persistent"]["energy_drift"],
+                            "launches_per_step": 2}
+                       for pr in ("fp64", "mixed")},
         "mixed": {"value": results["mixed"]["value"], "ms_per_step": results["mixed"]["ms_per_step"],
                   "energy_drift": results["mixed"]["energy_drift"],
                   "newton_per_step": results["mixed"]["newton_per_step"],

@@ -54,8 +54,8 @@ extern "C" {
 #define MB4_ERR_KRYLOV_BREAKDOWN     -5  /* reserved: not returned by this build (the least squares
                                             truncates a numerically dependent Krylov basis)      */
 #define MB4_ERR_NONFINITE            -6  /* NaN or Inf met in a Newton update                     */
-#define MB4_ERR_TIMEOUT              -7  /* reserved: not returned by this build (no kernel waits
-                                            on a device flag)                                    */
+#define MB4_ERR_TIMEOUT              -7  /* a bounded device-side wait ran out (the persistent
+                                            step's grid barriers, option wait_limit)            */
 #define MB4_ERR_ADMISSION_REJECTED   -8  /* a batch slot or memory budget is exhausted            */
 
 /* ---- precision modes --------------------------------------------------- */
@@ -148,6 +148,19 @@ typedef struct {
                             appendix, U_I = -(1/2) sum_i gamma_i n_i^2), set with
                             mb4_set_chi_field / mb4_batch_set_chi_field and initialised to
                             the scalar chi; costs S more doubles per instance.                */
+    int    persistent;   /* 0 (default): each step is the CUDA graph described under use_graph
+                            (one launch per phase of the Newton loop).  1: each step is ONE
+                            persistent cooperative kernel -- set-up and the whole Newton loop,
+                            its phases separated by grid barriers -- followed by the accept
+                            launch: no kernel boundary inside a step.  Same arithmetic, same
+                            results bit for bit.  Grid problems (mb4_create, mb4_batch_create)
+                            without the preconditioner, krylov_s 4 or 5; else
+                            MB4_ERR_INVALID_ARG at create.                                     */
+    long long wait_limit; /* persistent = 1: polls (each followed by a short sleep) that a
+                            grid-barrier wait makes before it gives up; the step then fails
+                            with MB4_ERR_TIMEOUT and the state stays at the last accepted step.
+                            Default 1 << 22 (a fraction of a second; a healthy wait takes
+                            microseconds).  0 gives up at the first poll (for tests).         */
 } mb4_options;
 
 #define MB4_MAX_PRECOND_SIDE 1024

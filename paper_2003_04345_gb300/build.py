@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmb4.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mb4_consts.cpp", "mb4_kernels.cu", "mb4_precond.cu", "mb4_capi.cu", "mb4_server.cu", "mb4_noalloc.cu", "mb4_probe.cu"]
+SOURCES = ["mb4_consts.cpp", "mb4_kernels.cu", "mb4_precond.cu", "mb4_capi.cu", "mb4_server.cu", "mb4_noalloc.cu", "mb4_probe.cu", "mb4_persist.cu"]
 
 
 def nvcc():

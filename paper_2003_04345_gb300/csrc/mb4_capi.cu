@@ -100,6 +100,8 @@ int validate_options(const mb4_options* in, mb4_options* o) {
     return MB4_ERR_INVALID_ARG;
   if (o->precondition != 0 && o->precondition != 1) return MB4_ERR_INVALID_ARG;
   if (o->site_chi != 0 && o->site_chi != 1) return MB4_ERR_INVALID_ARG;
+  if (o->persistent != 0 && o->persistent != 1) return MB4_ERR_INVALID_ARG;
+  if (o->wait_limit < 0) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -178,6 +180,8 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.chi_field = o.site_chi;
   p.bs_site = p.bs_residual = p.bs_matvec = p.bs_update = o.site_threads > 0 ? o.site_threads : 128;
   p.pred_order = o.newton_start;
+  p.persistent = o.persistent;
+  p.wait_limit = o.wait_limit;
   p.pred_adaptive = o.newton_start_adaptive;
   // Cost of the extra residual of an extrapolated start, in Newton iterations (1/1000):
   // measured at 512x512, s = 4: residual 78 us of a 239 us FP64 iteration, of a 134 us
@@ -672,7 +676,13 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_TRY(cudaMemsetAsync(d.bc, 0, sizeof(BatchCtl), c->stream));
   MB4_CHECK(write_status(c));
   if (o.autotune && o.site_threads == 0) MB4_CHECK(autotune_launch_shapes(c, grid));
-  if (c->use_graph) MB4_CHECK(build_graph(c));
+  if (p.persistent) {
+    if (!persistent_supported(p, c->precision == MB4_MIXED)) return MB4_ERR_INVALID_ARG;
+    p.pers_blocks = persistent_blocks(p, c->precision == MB4_MIXED);
+    if (p.pers_blocks < 1) return MB4_ERR_CUDA;
+  } else if (c->use_graph) {
+    MB4_CHECK(build_graph(c));
+  }
   return MB4_OK;
 }
 
@@ -689,7 +699,14 @@ int potential_to_host(const mb4_potential* pot, size_t n, std::vector<double>* V
 
 int step_async(mb4_batch* c, int nsteps) {
   launch_arm(c->p, c->b, c->stream);
-  if (c->use_graph) {
+  if (c->p.persistent) {
+    // one cooperative launch per step, then the accept (kept outside, so that a step whose
+    // barrier gave up is never half accepted)
+    for (int n = 0; n < nsteps; ++n) {
+      MB4_TRY(launch_step_persistent(c->p, c->b, c->precision == MB4_MIXED, c->stream));
+      launch_accept(c->p, c->b, c->stream);
+    }
+  } else if (c->use_graph) {
     for (int n = 0; n < nsteps; ++n) MB4_TRY(cudaGraphLaunch(c->exec, c->stream));
   } else {
     for (int n = 0; n < nsteps; ++n) {
@@ -767,6 +784,8 @@ int mb4_default_options(mb4_options* o) {
   o->newton_start = 2;
   o->newton_start_adaptive = 1;
   o->autotune = 1;
+  o->persistent = 0;
+  o->wait_limit = 1LL << 22;
   return MB4_OK;
 }
 

@@ -63,6 +63,9 @@ struct StepParams {
   const int* ell_nbr;
   const void* ell_w;       // double (real K) or double2 (complex K)
   const void* ell_wt;
+  int persistent;          // the step as one persistent kernel with grid barriers (mb4_persist.cu)
+  int pers_blocks;         // its grid: co-resident blocks of kPersistThreads
+  long long wait_limit;    // polls of a grid-barrier wait before it gives up (MB4_ERR_TIMEOUT)
   int bs_site, bs_residual, bs_matvec, bs_update;   // threads per block of the per-site kernels
                                                     // (bs_site: k_setup, k_accept)
   int pred_order;          // Newton start: 0 = e3 (x) u0; m = extrapolate the last m increments
@@ -129,7 +132,12 @@ struct InstStatus {
 // Batch-wide loop control.
 struct BatchCtl {
   int any_cont;                      // some instance continues its Newton loop (k_newton_test)
-  int pad[3];
+  // grid barrier of the persistent step kernel (mb4_persist.cu): arrivals of the current
+  // barrier, its generation (bumped by the last arrival), and an abort flag that a block
+  // whose bounded wait ran out sets (then every instance carries MB4_ERR_TIMEOUT)
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int abort;
 };
 
 // Device buffers of one batch.
@@ -177,6 +185,14 @@ template <typename TK> void launch_update(const StepParams& p, const DevBuffers&
                                           int use_cond, cudaStream_t st);
 void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 void launch_arm(const StepParams& p, const DevBuffers& b, cudaStream_t st);
+// Persistent step (mb4_persist.cu): set-up and the whole Newton loop of one step of every
+// instance in one cooperative launch; launch_accept follows it.  persistent_supported tells
+// whether this (precision, s, kinetic form, chi field) has a persistent kernel;
+// persistent_blocks returns its co-resident grid (0 on error) and sets its attributes.
+constexpr int kPersistThreads = 256;
+bool persistent_supported(const StepParams& p, bool mixed);
+int persistent_blocks(const StepParams& p, bool mixed);
+cudaError_t launch_step_persistent(const StepParams& p, const DevBuffers& b, bool mixed, cudaStream_t st);
 // Write n = ninst * S sites of state from re/im into u starting at instance first; an
 // instance whose state changes (any bit) forgets its Newton-start history.
 void launch_set_state(const StepParams& p, const DevBuffers& b, const double* re, const double* im, int first,

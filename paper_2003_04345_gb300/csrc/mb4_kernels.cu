@@ -21,24 +21,12 @@
 
 #include "mb4_device.cuh"
 #include "mb4_internal.h"
+#include "mb4_phases.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace mb4 {
 
-// ---------------------------------------------------------------------------
-// Step set-up (Algorithm 1, start of a step, and the first residual): u0 = u(t); J at u0
-// as per-site coefficients; (K+V) u0; ||u0||_inf.  At U^0 = e3 (x) u0 every stage
-// polynomial value equals u0, so Phi_i(U^0) = -h c_i f(u0) and the first
-// right-hand side is b = -Phibar^0 = -i h (T^-1 c)_i [(K+V) u0 + chi |u0|^2 u0].
-// J and b^0 only feed the Krylov solve, so they are formed in its precision TK;
-// (K+V) u0 is reused by every residual and stays FP64.  The increments start at
-// dU^0 = 0 (the first update writes them), or, for an instance whose step starts
-// from an extrapolation (option newton_start), at the polynomial extrapolation of
-// the last m converged increments (m = 1: the last; 2: 2 H0 - H1; 3: 3 H0 - 3 H1 + H2,
-// H0 the newest), whose residual the first k_residual then evaluates.
-// Grid: (sites / bs_site, B).
-// ---------------------------------------------------------------------------
 template <typename TK, bool ELL>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const double2* __restrict__ u,
                                                const double* __restrict__ D, double2* __restrict__ S0,
@@ -48,83 +36,9 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_setup(StepParams p, const d
                                                const InstConst* __restrict__ ic, InstStatus* is) {
   const int b = blockIdx.y;
   if (!is[b].active) return;
-  typedef typename Vec2<TK>::type TK2;
-  const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const InstConst& C = ic[b];
-  float m = 0.f;
-  if (k < S) {
-    const double2* ub = u + plane(b, S);
-    double2 c = ub[k];
-    double d = D[plane(b, S) + k];
-    double2 s0;
-    if constexpr (ELL) {
-      const double2 o = p.ell_cplx
-                            ? ell_offdiag_c<double, double2>(p.ell_nbr, (const double2*)p.ell_w, p.ell_deg, S, k, ub)
-                            : ell_offdiag<double, double2>(p.ell_nbr, (const double*)p.ell_w, p.ell_deg, S, k, ub);
-      s0.x = fma(d, c.x, o.x);
-      s0.y = fma(d, c.y, o.y);
-    } else {
-      Nbr n = neighbours(k, p.nx, p.ny, S);
-      double2 a = ub[n.xm], bb = ub[n.xp], e = ub[n.ym], f = ub[n.yp];
-      s0.x = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
-      s0.y = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
-    }
-    S0[plane(b, S) + k] = s0;
-    const TK pk = from_double<TK>(c.x), qk = from_double<TK>(c.y);
-    const TK pp = pk * pk, qq = qk * qk, nn = pp + qq;
-    const TK dt = from_double<TK>(d) * kval<TK>(C.inv_theta, C.f_inv_theta);
-    const double chik = p.chi_field ? p_chi[plane(b, S) + k] : 1.0;   // per-site chi (InstConst chi = 1)
-    TK ct = kval<TK>(C.chi_theta, C.f_chi_theta);
-    if (p.chi_field) ct *= from_double<TK>(chik);
-    JCoef<TK> j;
-    j.e1 = dt + ct * (pp + (TK)3 * qq);
-    j.e2 = dt + ct * ((TK)3 * pp + qq);
-    j.a = (TK)2 * ct * pk * qk;
-    j.pad = (TK)0;
-    jc[plane(b, S) + k] = j;
-    if (is[b].predicted) {
-      const int mo = min(is[b].pred_count, p.pred_order);
-      const double w0 = (mo == 1) ? 1.0 : (mo == 2) ? 2.0 : 3.0;
-      const double w1 = (mo == 2) ? -1.0 : -3.0;
-      const double2* H = dUh + (size_t)b * p.pred_order * 3 * S;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        double2 x = H[(size_t)i * S + k];
-        if (mo >= 2) {
-          const double2 y = H[(size_t)(3 + i) * S + k];
-          double2 z = make_double2(0.0, 0.0);
-          if (mo >= 3) z = H[(size_t)(6 + i) * S + k];
-          x.x = fma(w0, x.x, fma(w1, y.x, z.x));
-          x.y = fma(w0, x.y, fma(w1, y.y, z.y));
-        }
-        dUb[stage(b, i, S) + k] = x;
-      }
-    } else {
-      TK cn = kval<TK>(C.chi, C.f_chi) * nn;
-      if (p.chi_field) cn *= from_double<TK>(chik);
-      const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        TK2 bi;
-        const TK hc = kval<TK>(p.hTc[i], p.f_hTc[i]);
-        bi.x = hc * Fy;
-        bi.y = -hc * Fx;
-        v[level(b, 0, i, p.s, S) + k] = bi;
-      }
-    }
-    m = fmaxf(absf_of(c.x), absf_of(c.y));
-  }
-  // one atomic per block: same-address atomics queue at one L2 slice
-  m = warp_max(m);
-  __shared__ float wm[kSiteThreadsMax / 32];
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float bm = wm[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) bm = fmaxf(bm, wm[w]);
-    if (bm > 0.f) atomicMax(&is[b].u0max_bits, __float_as_uint(bm));
-  }
+  const float m = (k < p.S) ? setup_site<TK, ELL>(p, u, D, S0, jc, v, dUh, dUb, p_chi, ic[b], is[b], b, k) : 0.f;
+  block_max_into(m, &is[b].u0max_bits);
 }
 
 template <typename TK>
@@ -138,17 +52,6 @@ void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
                                                   b.dU_hist, b.Ubar, b.chi, b.ic, b.is);
 }
 
-// ---------------------------------------------------------------------------
-// Residual (Algorithm 1; eq. Phidefinition, eq. fKu2, eq. fIu2) in
-// the eigenbasis, on the increments dU: b = -Phibar with
-//   Phibar_i = dU_i + i [ h lam_i (K+V) dU_i + h (T^-1 c)_i (K+V) u0
-//                         + sum_q h chi W~_iq |X_q|^2 X_q ],
-//   X_q = u0 + sum_n (L T)_qn dU_n   (the stage polynomial at the 6 Gauss nodes;
-// exact for the degree-11 integrand).  (The u0 terms: T^-1 E T = Lambda and
-// T^-1 (E_{.0} + E 1) = T^-1 c, since the rows of E sum to c.)  All FP64.
-// KM selects the kinetic term: 0 the grid stencil, 1 the grid stencil with tx factored
-// out (StepParams::kin_unit), 2 the general sparse K (ELL), 3 a complex Hermitian one.
-// ---------------------------------------------------------------------------
 template <typename TO, bool CHIF, int KM>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, const double2* __restrict__ u,
                                                   const double* __restrict__ D, const double2* __restrict__ S0,
@@ -161,74 +64,9 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_residual(StepParams p, cons
   const int b = blockIdx.y;
   if (!is[b].active) return;
   if (skip_first && is[b].newton_iter == 0 && !is[b].predicted) return;   // b^0 was written by k_setup
-  typedef typename Vec2<TO>::type TO2;
-  const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= S) return;
-  const InstConst& C = ic[b];
-  Nbr n;
-  if constexpr (KM < 2) n = neighbours(k, p.nx, p.ny, S);
-  const double2 u0 = u[plane(b, S) + k];
-  const double2 s0 = S0[plane(b, S) + k];
-  const double d = D[plane(b, S) + k];           // D / tx when KM == 1
-  const double chik = CHIF ? p_chi[plane(b, S) + k] : 1.0;   // per-site chi (InstConst chi = 1)
-  // b = -Phibar is accumulated directly.  With Phibar = dU + i Q,
-  //   Q = h lam (K+V) dU + hTc (K+V) u0 + sum_q h chi W~_q |X_q|^2 X_q,
-  // b.x = -dU.x + Q.y and b.y = -dU.y - Q.x: the dU terms ride on the first FMAs and
-  // every sign is an operand modifier.
-  double2 dU[3], bo[3];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const double2* P = dUb + stage(b, m, S);
-    const double2 c = P[k];
-    dU[m] = c;
-    double sx, sy, hl;
-    if constexpr (KM >= 2) {
-      const double2 o =
-          (KM == 3) ? ell_offdiag_c<double, double2>(p.ell_nbr, (const double2*)p.ell_w, p.ell_deg, S, k, P)
-                    : ell_offdiag<double, double2>(p.ell_nbr, (const double*)p.ell_w, p.ell_deg, S, k, P);
-      sx = fma(d, c.x, o.x);
-      sy = fma(d, c.y, o.y);
-      hl = p.hlam[m];
-    } else if constexpr (KM == 1) {
-      // (K+V) x / tx = D/tx x - (x_x- + x_x+) - (ty/tx) (x_y- + x_y+)
-      const double2 a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-      sx = fma(d, c.x, -fma(p.rty, e.x + f.x, a.x + bb.x));
-      sy = fma(d, c.y, -fma(p.rty, e.y + f.y, a.y + bb.y));
-      hl = p.hltx[m];
-    } else {
-      const double2 a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-      sx = fma(-p.ty, e.x + f.x, fma(-p.tx, a.x + bb.x, d * c.x));
-      sy = fma(-p.ty, e.y + f.y, fma(-p.tx, a.y + bb.y, d * c.y));
-      hl = p.hlam[m];
-    }
-    bo[m].x = fma(hl, sy, fma(p.hTc[m], s0.y, -c.x));
-    bo[m].y = fma(-hl, sx, fma(-p.hTc[m], s0.x, -c.y));
-  }
-#pragma unroll
-  for (int q = 0; q < kGauss; ++q) {
-    double Xx = fma(p.LT[q][0], dU[0].x, u0.x), Xy = fma(p.LT[q][0], dU[0].y, u0.y);
-    Xx = fma(p.LT[q][1], dU[1].x, Xx);
-    Xy = fma(p.LT[q][1], dU[1].y, Xy);
-    Xx = fma(p.LT[q][2], dU[2].x, Xx);
-    Xy = fma(p.LT[q][2], dU[2].y, Xy);
-    double nn = fma(Xx, Xx, Xy * Xy);
-    if (CHIF) nn *= chik;
-    const double gx = nn * Xx, gy = nn * Xy;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      bo[i].x = fma(C.hchiW[i][q], gy, bo[i].x);
-      bo[i].y = fma(-C.hchiW[i][q], gx, bo[i].y);
-    }
-  }
-  TO2* ob = out + (size_t)b * (size_t)out_stride;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    TO2 o;
-    o.x = from_double<TO>(bo[i].x);
-    o.y = from_double<TO>(bo[i].y);
-    ob[(size_t)i * S + k] = o;
-  }
+  if (k >= p.S) return;
+  residual_site<TO, CHIF, KM>(p, u, D, S0, dUb, out, out_stride, p_chi, ic[b], b, k);
 }
 
 // Kinetic mode of the residual and the FP64 basis (template argument KM).
@@ -271,13 +109,6 @@ void launch_residual_out(const StepParams& p, const DevBuffers& b, double2* phib
 #undef MB4_RES
 }
 
-// ---------------------------------------------------------------------------
-// Shifted solves (Algorithm 1; eq. MB4_5): one s-step GMRES cycle per
-// system.  The Krylov space K_s(I - h lam_i J, b_i) = span{b_i, Jb_i, .., J^{s-1} b_i}
-// is the same monomial space for all three shifts, so the basis
-// v_{a+1} = (J/theta) v_a is built for the three right-hand sides together, and
-// (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
-// ---------------------------------------------------------------------------
 template <typename TK, int KM>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
@@ -286,71 +117,9 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
   pdl_launch_dependents();
   const int b = blockIdx.y;
   if (!is[b].active) return;
-  typedef typename Vec2<TK>::type TK2;
-  const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= S) return;
-  const JCoef<TK> j = jc[plane(b, S) + k];
-  if constexpr (KM >= 2) {
-    // (J x)_re = a xp + e1 xq + Im(sum_j (K_kj / theta) x_j), (J x)_im = -e2 xp - a xq - Re(sum_j ..):
-    // with s = sum_j K_kj x_j / theta (a complex product when K is complex), the kinetic
-    // part of J x is the real form of -i s (eq. JL)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const TK2* P = v + level(b, a_in, i, p.s, S);
-      const TK2 c = P[k];
-      const TK2 s = (KM == 3) ? ell_offdiag_c<TK, TK2>(p.ell_nbr, (const TK2*)p.ell_wt, p.ell_deg, S, k, P)
-                              : ell_offdiag<TK, TK2>(p.ell_nbr, (const TK*)p.ell_wt, p.ell_deg, S, k, P);
-      TK2 o;
-      o.x = j.a * c.x + j.e1 * c.y + s.y;
-      o.y = -j.e2 * c.x - j.a * c.y - s.x;
-      v[level(b, a_in + 1, i, p.s, S) + k] = o;
-    }
-  } else {
-    Nbr n = neighbours(k, p.nx, p.ny, S);
-    const TK tx = kval<TK>(ic[b].txt, ic[b].f_txt), ty = kval<TK>(ic[b].tyt, ic[b].f_tyt);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const TK2* P = v + level(b, a_in, i, p.s, S);
-      TK2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-      TK2 o;
-      // (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
-      // (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
-      if constexpr (KM == 1) {                 // theta = tx: tx / theta = 1
-        o.x = fma(j.a, c.x, fma(j.e1, c.y, -fma(ty, e.y + f.y, a.y + bb.y)));
-        o.y = fma(-j.e2, c.x, fma(-j.a, c.y, fma(ty, e.x + f.x, a.x + bb.x)));
-      } else {
-        o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
-        o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
-      }
-      v[level(b, a_in + 1, i, p.s, S) + k] = o;
-    }
-  }
-}
-
-// Matrix powers on a tile (FP32 Krylov basis): one block builds v_1..v_SK on a
-// TX x TY tile from v_0 and the J coefficients loaded once, with an SK-wide
-// periodic halo in shared memory; level a is valid on the tile grown by SK - a,
-// so no block needs another block's result.  Replaces SK stencil launches by
-// one at the price of recomputing the shrinking halo (cheap in FP32).  Each
-// thread owns fixed positions of the extended tile (columns tx0 + 32 ix, rows
-// ty0 + 8 iy) at every level, so their J coefficients stay in registers and
-// shared memory holds only the two level buffers: 4 blocks per SM at SK = 4,
-// which puts a 512 x 512 grid's 512 tiles in one wave.
-constexpr int kPowTX = 32, kPowTY = 16, kPowThreads = 256;
-
-template <int SK>
-__host__ __device__ constexpr int pow_ext_x() { return kPowTX + 2 * SK; }
-template <int SK>
-__host__ __device__ constexpr int pow_ext_y() { return kPowTY + 2 * SK; }
-template <int SK>
-constexpr size_t pow_smem_bytes() {
-  return (size_t)pow_ext_x<SK>() * pow_ext_y<SK>() * (2 * 3 * sizeof(float2));
-}
-
-__device__ __forceinline__ int wrap(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
+  if (k >= p.S) return;
+  matvec_site<TK, KM>(p, jc, v, a_in, ic[b], b, k);
 }
 
 template <int SK>
@@ -361,161 +130,10 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   pdl_launch_dependents();
   const int b = blockIdx.y;
   if (!is[b].active) return;
-  constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
-  constexpr int NCX = (EX + 31) / 32, NCY = (EY + 7) / 8;      // positions per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* buf0 = reinterpret_cast<float2*>(smem_raw);     // [3][EA]
-  float2* buf1 = buf0 + 3 * EA;                           // [3][EA]
-  const int S = p.S, nx = p.nx, ny = p.ny;
-  const int tiles_x = (nx + kPowTX - 1) / kPowTX;
-  const int tyi = blockIdx.x / tiles_x, txi = blockIdx.x - tyi * tiles_x;
-  const int x0 = txi * kPowTX - SK, y0 = tyi * kPowTY - SK;
-  const float4* jb = jc + plane(b, S);
-  const int tx0 = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // 32 x 8 thread layout
-  float4 jr[NCY][NCX];
-#pragma unroll
-  for (int iy = 0; iy < NCY; ++iy) {
-    const int ly = ty0 + 8 * iy;
-#pragma unroll
-    for (int ix = 0; ix < NCX; ++ix) {
-      const int lx = tx0 + 32 * ix;
-      if (ly < EY && lx < EX) {
-        const int t = ly * EX + lx;
-        const int g = wrap(y0 + ly, ny) * nx + wrap(x0 + lx, nx);
-        jr[iy][ix] = jb[g];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) buf0[i * EA + t] = v[level(b, 0, i, SK, S) + g];
-      }
-    }
-  }
-  __syncthreads();
-  const float tx = ic[b].f_txt, ty = ic[b].f_tyt;
-  float2* src = buf0;
-  float2* dst = buf1;
-#pragma unroll 1
-  for (int a = 1; a <= SK; ++a) {
-#pragma unroll
-    for (int iy = 0; iy < NCY; ++iy) {
-      const int ly = ty0 + 8 * iy;
-#pragma unroll
-      for (int ix = 0; ix < NCX; ++ix) {
-        const int lx = tx0 + 32 * ix;
-        if (ly < a || ly >= EY - a || lx < a || lx >= EX - a) continue;   // level a lives on the tile grown by SK - a
-        const int c = ly * EX + lx;
-        const float4 j = jr[iy][ix];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float2* P = src + i * EA;
-          const float2 cc = P[c], xa = P[c - 1], xb = P[c + 1], ya = P[c - EX], yb = P[c + EX];
-          float2 o;
-          o.x = j.z * cc.x + j.x * cc.y - tx * (xa.y + xb.y) - ty * (ya.y + yb.y);
-          o.y = -j.y * cc.x - j.z * cc.y + tx * (xa.x + xb.x) + ty * (ya.x + yb.x);
-          dst[i * EA + c] = o;
-        }
-      }
-    }
-    __syncthreads();
-    // interior of level a to global
-    for (int ly = ty0; ly < kPowTY; ly += kPowThreads / 32) {
-      const int lx = tx0;
-      const int gx = txi * kPowTX + lx, gy = tyi * kPowTY + ly;
-      if (gx < nx && gy < ny) {
-        const int c = (ly + SK) * EX + (lx + SK);
-        const size_t g = (size_t)gy * nx + gx;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) v[level(b, a, i, SK, S) + g] = dst[i * EA + c];
-      }
-    }
-    float2* tmp = src;
-    src = dst;
-    dst = tmp;
-  }
+  powers_tile<SK>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
 }
 
-// Gram accumulators.  FP32 mode: products and per-thread sums in FP32, a
-// pairwise (shuffle-tree) warp sum per entry, then FP64 across warps and blocks.
-// For the monomial bases met here (s <= 10, ||J/theta|| <= 1) the normal
-// equations are well enough conditioned that this gives the same least-squares
-// residual as exact sums of the FP32 products; the FP32 basis vectors themselves
-// set the accuracy of the inner solve.  FP64 mode: see warp_sum_f64.
-template <typename TK> struct GramAcc;
-template <> struct GramAcc<float> {
-  float v;
-  __device__ void zero() { v = 0.f; }
-  __device__ void add(float2 a, float2 b) { v = fmaf(a.x, b.x, v); v = fmaf(a.y, b.y, v); }
-};
-template <> struct GramAcc<double> {
-  double v;
-  __device__ void zero() { v = 0.0; }
-  __device__ void add(double2 a, double2 b) { v = fma(a.x, b.x, v); v = fma(a.y, b.y, v); }
-};
-
-// Warp sums of NE per-lane FP64 values, written to out[0..NE).  A butterfly per
-// entry would cost 5 NE adds per lane on the FP64 pipe -- the pipe that bounds
-// the Gram kernel.  Recursive halving instead: at offset o = 16, 8, 4, 2 each lane
-// keeps the half of its live values picked by lane bit o and adds the partner's
-// copy of that half; after four steps a lane holds P/16 entries (P = NE padded
-// to a multiple of 16), which the o = 1 partner holds too.  About P adds per lane.
-template <int NE>
-__device__ __forceinline__ void warp_sum_f64(const GramAcc<double> (&acc)[NE], double* out, int lane) {
-  constexpr int P = ((NE + 15) / 16) * 16;
-  double x[P];
-#pragma unroll
-  for (int j = 0; j < P; ++j) x[j] = (j < NE) ? acc[j].v : 0.0;
-  int base = 0;
-#pragma unroll
-  for (int st = 0; st < 4; ++st) {
-    const int o = 16 >> st;
-    const int h = P >> (st + 1);
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int j = 0; j < (P >> (st + 1)); ++j) {
-      const double send = up ? x[j] : x[j + h];
-      const double keep = up ? x[j + h] : x[j];
-      x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-    if (up) base += h;
-  }
-#pragma unroll
-  for (int j = 0; j < P / 16; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], 1);
-  if ((lane & 1) == 0) {
-#pragma unroll
-    for (int j = 0; j < P / 16; ++j)
-      if (base + j < NE) out[base + j] = x[j];
-  }
-}
-
-template <int NE>
-__device__ __forceinline__ void warp_sums(const GramAcc<float> (&acc)[NE], double* out, int lane) {
-#pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    float r = acc[e].v;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (lane == 0) out[e] = f2d_bits(r);
-  }
-}
-template <int NE>
-__device__ __forceinline__ void warp_sums(const GramAcc<double> (&acc)[NE], double* out, int lane) {
-  warp_sum_f64<NE>(acc, out, lane);
-}
-
-// Gram matrices G_ab = <v_a, v_b> (real inner product of the [p; q] form),
-// a <= b <= s, of system i = blockIdx.y of instance blockIdx.z.  With CL > 1 the
-// blocks form clusters of CL along x: each cluster's rank-0 block adds its
-// members' block sums from their shared memory (distributed shared memory, in
-// rank order) and writes one partial per cluster to
-// part[((inst * 3 + i) * (gridDim.x / CL) + cluster) * NE + e].  The last
-// cluster of system i to finish then
-//  1. reduces that system's partials in a fixed order (so results do not depend
-//     on which block finishes last),
-//  2. forms the normal equations of the least-squares problem
-//     min_c || b - (I - h lam_i J) sum_a c_a v_a ||:
-//       (B^T G B) c = B^T G e_0,  B = [I; 0] - sig_i [0; I]  (s x s),
-//  3. factors them with one warp (right-looking Cholesky; the basis is truncated
-//     at the first pivot below trunc_rel times the larger of the leading one and
-//     its own diagonal entry before elimination, a numerically exhausted Krylov
-//     space whatever the scale of the levels; b = 0 gives c = 0) and solves.
-// The three systems finish on three different blocks, in parallel.
 template <typename TK, int SK, int CL>
 __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                   double* __restrict__ part, double* __restrict__ coef,
@@ -524,55 +142,12 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   pdl_launch_dependents();
   const int inst = blockIdx.z;
   if (!is[inst].active) return;
-  typedef typename Vec2<TK>::type TK2;
   constexpr int NV = SK + 1;
   constexpr int NE = NV * (NV + 1) / 2;
-  constexpr int U = 4;                          // sites whose loads are in flight together
-  const int S = p.S;
   const int i = blockIdx.y;
-  GramAcc<TK> acc[NE];
-#pragma unroll
-  for (int e = 0; e < NE; ++e) acc[e].zero();
-  const int stride = gridDim.x * blockDim.x;
-  const TK2* vi = v + level(inst, 0, i, SK, S);
-  const size_t lstride = (size_t)3 * S;         // from level a to level a+1 of the same system
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; k + (U - 1) * stride < S; k += U * stride) {
-    TK2 x[U][NV];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int a = 0; a < NV; ++a) x[u][a] = vi[(size_t)a * lstride + k + u * stride];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int e = 0;
-#pragma unroll
-      for (int a = 0; a < NV; ++a)
-#pragma unroll
-        for (int c = a; c < NV; ++c) acc[e++].add(x[u][a], x[u][c]);
-    }
-  }
-  for (; k < S; k += stride) {
-    TK2 x[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) x[a] = vi[(size_t)a * lstride + k];
-    int e = 0;
-#pragma unroll
-    for (int a = 0; a < NV; ++a)
-#pragma unroll
-      for (int c = a; c < NV; ++c) acc[e++].add(x[a], x[c]);
-  }
-  __shared__ double red[8][NE];
   __shared__ double blk[NE];
   __shared__ bool is_last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  warp_sums<NE>(acc, red[warp], lane);
-  __syncthreads();
-  for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][e];
-    blk[e] = t;
-  }
+  gram_accumulate<TK, SK>(p, v, inst, i, blockIdx.x, gridDim.x, blk);
   const int nb = gridDim.x / CL;                 // partials of system i
   double* pi = part + ((size_t)inst * 3 + i) * nb * NE;
   bool leader = true;
@@ -589,7 +164,6 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
     }
     cluster.sync();                              // members stay resident until read
   } else {
-    __syncthreads();
     for (int e = threadIdx.x; e < NE; e += blockDim.x) pi[(size_t)blockIdx.x * NE + e] = blk[e];
   }
   if (!leader) return;
@@ -602,85 +176,7 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  // 1. fixed-order reduction: thread t takes entry t % NE and partial slice t / NE.
-  constexpr int SLICES = (256 / NE) > 0 ? (256 / NE) : 1;
-  __shared__ double slice[SLICES][NE];
-  __shared__ double G[NE];
-  __shared__ double Nm[SK][SK + 1];             // [.., SK] holds the right-hand side
-  __shared__ double rinv[SK];
-  __shared__ double Ndiag[SK];                  // diagonal of the normal matrix before elimination
-  for (int t = threadIdx.x; t < SLICES * NE; t += blockDim.x) {
-    const int sl = t / NE, e = t - sl * NE;
-    const int b0 = sl * nb / SLICES, b1 = (sl + 1) * nb / SLICES;
-    const double* pp = pi + e;
-    double q[4] = {0, 0, 0, 0};
-    int bb = b0;
-    for (; bb + 4 <= b1; bb += 4) {
-      double w[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = __ldcg(pp + (size_t)(bb + j) * NE);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) q[j] += w[j];
-    }
-    for (int j = 0; bb < b1; ++bb, ++j) q[j] += __ldcg(pp + (size_t)bb * NE);
-    slice[sl][e] = (q[0] + q[1]) + (q[2] + q[3]);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-    double sum = 0.0;
-    for (int sl = 0; sl < SLICES; ++sl) sum += slice[sl][e];
-    G[e] = sum;
-  }
-  __syncthreads();
-  // 2. normal equations, all entries in parallel
-  auto g = [&](int a, int c) -> double {
-    if (a > c) { int t = a; a = c; c = t; }
-    return G[a * NV - a * (a - 1) / 2 + (c - a)];
-  };
-  const double sg = p.precond ? -1.0 : ic[inst].sig[i];   // preconditioned: A z_a = v_a + v_{a+1}
-  for (int t = threadIdx.x; t < SK * (SK + 1); t += blockDim.x) {
-    const int a = t / (SK + 1), c = t - a * (SK + 1);
-    Nm[a][c] = (c < SK) ? g(a, c) - sg * (g(a + 1, c) + g(a, c + 1)) + sg * sg * g(a + 1, c + 1)
-                        : g(a, 0) - sg * g(a + 1, 0);
-    if (c == a) Ndiag[a] = Nm[a][c];
-  }
-  __syncthreads();
-  // 3. one warp: Cholesky in place (lower triangle), then the two triangular solves,
-  // with one reciprocal square root per pivot (kept in rinv) and no divisions.
-  if (warp == 0) {
-    int dim = (G[0] > 0.0) ? SK : 0;
-    const double lead = Nm[0][0];
-    for (int a = 0; a < dim; ++a) {
-      const double dg = Nm[a][a];
-      if (!(dg > (double)p.trunc_rel * fmax(lead, Ndiag[a]))) { dim = a; break; }
-      const double il = rsqrt(dg);
-      __syncwarp();
-      for (int b2 = a + 1 + lane; b2 < SK; b2 += 32) Nm[b2][a] *= il;
-      if (lane == 0) { Nm[a][a] = dg * il; rinv[a] = il; }
-      __syncwarp();
-      const int m = SK - a - 1;
-      for (int idx = lane; idx < m * m; idx += 32) {
-        const int b2 = a + 1 + idx / m, c = a + 1 + idx % m;
-        if (c <= b2) Nm[b2][c] -= Nm[b2][a] * Nm[c][a];
-      }
-      __syncwarp();
-    }
-    if (lane == 0) {
-      double y[SK], cc[SK];
-      for (int a = 0; a < dim; ++a) {
-        double t = Nm[a][SK];
-        for (int b2 = 0; b2 < a; ++b2) t -= Nm[a][b2] * y[b2];
-        y[a] = t * rinv[a];
-      }
-      for (int a = dim - 1; a >= 0; --a) {
-        double t = y[a];
-        for (int b2 = a + 1; b2 < dim; ++b2) t -= Nm[b2][a] * cc[b2];
-        cc[a] = t * rinv[a];
-      }
-      for (int a = 0; a < SK; ++a) coef[((size_t)inst * 3 + i) * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
-      is[inst].ticket_gram[i] = 0u;
-    }
-  }
+  gram_lsq_solve<SK>(p, part, coef, ic, is, inst, i, nb);
 }
 
 template <int SK>
@@ -802,10 +298,6 @@ void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   launch_gram<TK>(p, b, s);
 }
 
-// Newton update (Algorithm 1): rbar_i = sum_a c_ia v_a,i; dU_i += rbar_i in FP64 (from
-// dU^0 = 0 the first iteration writes rbar); ||r||_inf with r = (T (x) I) rbar, merged over
-// the blocks with an atomic max; NaN/Inf flagged.  No block waits for another: the loop
-// test runs in k_newton_test once the whole grid has finished.  Grid: (sites / bs_update, B).
 template <typename TK, int SK>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                 const double* __restrict__ coef, double2* __restrict__ Ubar,
@@ -815,116 +307,24 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_update(StepParams p, const 
   const int inst = blockIdx.y;
   InstStatus& I = is[inst];
   if (!I.active) return;
-  typedef typename Vec2<TK>::type TK2;
   __shared__ TK cs[3][SK];
-  __shared__ float wmax[8];
-  __shared__ int wbad[8];
   if (threadIdx.x < 3 * SK)
     cs[threadIdx.x / SK][threadIdx.x % SK] =
         (TK)coef[((size_t)inst * 3 + threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
   const bool first = I.newton_iter == 0 && !I.predicted;
   __syncthreads();
-  const int S = p.S;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   float m = 0.f;
   int bad = 0;
-  if (k < S) {
-    TK2 x[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      TK sx = 0, sy = 0;
-#pragma unroll
-      for (int a = 0; a < SK; ++a) {
-        const TK2 w = v[level(inst, a, i, SK, S) + k];
-        sx += cs[i][a] * w.x;
-        sy += cs[i][a] * w.y;
-      }
-      x[i].x = sx;
-      x[i].y = sy;
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      double2 U;
-      if (first) {
-        U.x = to_double(x[i].x);
-        U.y = to_double(x[i].y);
-      } else {
-        U = Ubar[stage(inst, i, S) + k];
-        U.x += to_double(x[i].x);
-        U.y += to_double(x[i].y);
-      }
-      Ubar[stage(inst, i, S) + k] = U;
-    }
-    // ||r||_inf with r = T rbar, in FP32: it only decides whether to iterate again.
-    float xf[3][2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { xf[i][0] = to_float(x[i].x); xf[i][1] = to_float(x[i].y); }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float t0 = p.fT[j][0], t1 = p.fT[j][1], t2 = p.fT[j][2];
-      const float rx = t0 * xf[0][0] + t1 * xf[1][0] + t2 * xf[2][0];
-      const float ry = t0 * xf[0][1] + t1 * xf[1][1] + t2 * xf[2][1];
-      bad |= !(isfinite(rx) && isfinite(ry));
-      m = fmaxf(m, fmaxf(fabsf(rx), fabsf(ry)));
-    }
-  }
-  m = warp_max(m);
-  bad = __any_sync(0xffffffffu, bad);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { wmax[warp] = m; wbad[warp] = bad; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float bm = wmax[0];
-    int bb = wbad[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { bm = fmaxf(bm, wmax[w]); bb |= wbad[w]; }
-    if (bm > 0.f) atomicMax(&I.rmax_bits, dbits((double)bm));
-    if (bb) atomicOr(&I.nonfinite, 1);
-  }
+  if (k < p.S) update_site<TK, SK>(p, v, cs, Ubar, first, inst, k, m, bad);
+  block_update_flags(m, bad, I);
 }
 
-// The loop test of a Newton iteration (failure rule of Sec. 2.2), one thread per instance
-// that iterated: continue while ||r^l||_inf > rtol ||u0||_inf (and, when enabled, while the
-// predicted remaining error is above newton_predict ||u0||_inf), for at most newton_max
-// iterations.  The block then sets the WHILE condition: continue while any instance
-// continues.  One block of up to 1024 threads.
 __global__ void k_newton_test(StepParams p, InstStatus* is, BatchCtl* bc, cudaGraphConditionalHandle h,
                               int use_cond) {
   pdl_wait();
-  int any = 0;
-  for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
-    InstStatus& I = is[b];
-    if (!I.active) continue;
-    int cont = 0;
-    const int it = I.newton_iter;                // iteration index l of this update
-    const double r = __longlong_as_double((long long)I.rmax_bits);
-    const double u0n = (double)__uint_as_float(I.u0max_bits);
-    if (it < 8) I.hist[it] = r;
-    I.last_rmax = r;
-    I.last_u0max = u0n;
-    I.newton_iter = it + 1;
-    if (I.nonfinite || !isfinite(r)) {
-      I.error = MB4_ERR_NONFINITE;
-    } else if (r <= p.newton_rtol * u0n) {
-      cont = 0;
-    } else if (p.newton_predict > 0.0 && it >= 1 && r < 0.5 * I.prev_rmax &&
-               (r / I.prev_rmax) / (1.0 - r / I.prev_rmax) * r <= p.newton_predict * u0n) {
-      cont = 0;
-    } else if (it + 1 >= p.newton_max) {
-      I.error = MB4_ERR_NEWTON_NOT_CONVERGED;
-    } else {
-      cont = 1;
-    }
-    I.prev_rmax = r;
-    I.last_newton_iters = it + 1;
-    I.rmax_bits = 0ull;
-    if (!cont) I.active = 0;
-    any |= cont;
-  }
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) {
-    bc->any_cont = any;
-    if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
-  }
+  const int any = newton_test_all(p, is, bc);
+  if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 template <typename TK>
@@ -1037,7 +437,11 @@ void launch_accept(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 // Arms every enabled instance without an error for the next step (start of a call).
 __global__ void k_arm(int B, int pred_order, InstStatus* is, BatchCtl* bc) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b == 0) bc->any_cont = 0;
+  if (b == 0) {
+    bc->any_cont = 0;
+    bc->bar_count = 0u;                          // a barrier a timed-out call left half full
+    bc->abort = 0;
+  }
   if (b >= B) return;
   InstStatus& I = is[b];
   I.newton_iter = 0;

@@ -69,7 +69,7 @@ class Options(C.Structure):
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
                 ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int),
                 ("autotune", C.c_int), ("site_threads", C.c_int), ("precondition", C.c_int),
-                ("site_chi", C.c_int)]
+                ("site_chi", C.c_int), ("persistent", C.c_int), ("wait_limit", C.c_longlong)]
 
 
 class Stats(C.Structure):
@@ -241,7 +241,7 @@ class Integrator:
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
         """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
         stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive,
-        autotune, site_threads, precondition, site_chi)."""
+        autotune, site_threads, precondition, site_chi, persistent, wait_limit)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -450,7 +450,7 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
              c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True,
              newton_start=None, newton_start_adaptive=None, autotune=None, site_threads=None,
-             precondition=None, site_chi=None):
+             precondition=None, site_chi=None, persistent=None, wait_limit=None):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -475,6 +475,10 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
         opt.precondition = int(precondition)
     if site_chi is not None:
         opt.site_chi = 1 if site_chi else 0
+    if persistent is not None:
+        opt.persistent = int(persistent)
+    if wait_limit is not None:
+        opt.wait_limit = int(wait_limit)
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
