@@ -123,6 +123,19 @@ template <typename T> __device__ __forceinline__ float to_float(T x);
 template <> __device__ __forceinline__ float to_float<float>(float x) { return x; }
 template <> __device__ __forceinline__ float to_float<double>(double x) { return d2f_trunc(x); }
 
+// Arithmetic that the compiler never contracts or reorders: a*b + c rounded once (fma_)
+// or twice (mul_ then add_).  The step's phases are inlined into two kernel forms (one
+// launch per phase, or one persistent kernel); with plain expressions the compiler may fuse
+// a multiply into an add in one form and not in the other, and the two would round
+// differently.  Writing every product-sum explicitly makes both forms compute bit for bit
+// the same.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+
 // Threads per block of the one-site-per-thread kernels: chosen per context (StepParams
 // bs_*; the autotuner of the C ABI or 128), at most kSiteThreadsMax.  Their results do
 // not depend on it: each site is computed alone and the only reductions are maxima.
@@ -142,8 +155,8 @@ __device__ __forceinline__ T2 ell_offdiag(const int* __restrict__ nbr, const T* 
     if (j >= 0) {
       const T wv = w[(size_t)e * S + k];
       const T2 xv = x[j];
-      s.x += wv * xv.x;
-      s.y += wv * xv.y;
+      s.x = fma_(wv, xv.x, s.x);
+      s.y = fma_(wv, xv.y, s.y);
     }
   }
   return s;
@@ -162,8 +175,8 @@ __device__ __forceinline__ T2 ell_offdiag_c(const int* __restrict__ nbr, const T
     if (j >= 0) {
       const T2 wv = w[(size_t)e * S + k];
       const T2 xv = x[j];
-      s.x += wv.x * xv.x - wv.y * xv.y;
-      s.y += wv.x * xv.y + wv.y * xv.x;
+      s.x = fma_(wv.x, xv.x, fma_(-wv.y, xv.y, s.x));
+      s.y = fma_(wv.x, xv.y, fma_(wv.y, xv.x, s.y));
     }
   }
   return s;

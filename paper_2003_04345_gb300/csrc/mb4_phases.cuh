@@ -56,15 +56,15 @@ __device__ __forceinline__ float setup_site(const StepParams& p, const double2* 
   }
   S0[plane(b, S) + k] = s0;
   const TK pk = from_double<TK>(c.x), qk = from_double<TK>(c.y);
-  const TK pp = pk * pk, qq = qk * qk, nn = pp + qq;
-  const TK dt = from_double<TK>(d) * kval<TK>(C.inv_theta, C.f_inv_theta);
+  const TK pp = mul_(pk, pk), qq = mul_(qk, qk), nn = add_(pp, qq);
+  const TK dt = mul_(from_double<TK>(d), kval<TK>(C.inv_theta, C.f_inv_theta));
   const double chik = p.chi_field ? p_chi[plane(b, S) + k] : 1.0;   // per-site chi (InstConst chi = 1)
   TK ct = kval<TK>(C.chi_theta, C.f_chi_theta);
-  if (p.chi_field) ct *= from_double<TK>(chik);
+  if (p.chi_field) ct = mul_(ct, from_double<TK>(chik));
   JCoef<TK> j;
-  j.e1 = dt + ct * (pp + (TK)3 * qq);
-  j.e2 = dt + ct * ((TK)3 * pp + qq);
-  j.a = (TK)2 * ct * pk * qk;
+  j.e1 = fma_(ct, fma_((TK)3, qq, pp), dt);
+  j.e2 = fma_(ct, fma_((TK)3, pp, qq), dt);
+  j.a = mul_(mul_(mul_((TK)2, ct), pk), qk);
   j.pad = (TK)0;
   jc[plane(b, S) + k] = j;
   if (I.predicted) {
@@ -85,15 +85,15 @@ __device__ __forceinline__ float setup_site(const StepParams& p, const double2* 
       dUb[stage(b, i, S) + k] = x;
     }
   } else {
-    TK cn = kval<TK>(C.chi, C.f_chi) * nn;
-    if (p.chi_field) cn *= from_double<TK>(chik);
-    const TK Fx = from_double<TK>(s0.x) + cn * pk, Fy = from_double<TK>(s0.y) + cn * qk;
+    TK cn = mul_(kval<TK>(C.chi, C.f_chi), nn);
+    if (p.chi_field) cn = mul_(cn, from_double<TK>(chik));
+    const TK Fx = fma_(cn, pk, from_double<TK>(s0.x)), Fy = fma_(cn, qk, from_double<TK>(s0.y));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       TK2 bi;
       const TK hc = kval<TK>(p.hTc[i], p.f_hTc[i]);
-      bi.x = hc * Fy;
-      bi.y = -hc * Fx;
+      bi.x = mul_(hc, Fy);
+      bi.y = mul_(-hc, Fx);
       v[level(b, 0, i, p.s, S) + k] = bi;
     }
   }
@@ -181,9 +181,9 @@ __device__ __forceinline__ void residual_site(const StepParams& p, const double2
     Xy = fma(p.LT[q][1], dU[1].y, Xy);
     Xx = fma(p.LT[q][2], dU[2].x, Xx);
     Xy = fma(p.LT[q][2], dU[2].y, Xy);
-    double nn = fma(Xx, Xx, Xy * Xy);
-    if (CHIF) nn *= chik;
-    const double gx = nn * Xx, gy = nn * Xy;
+    double nn = fma(Xx, Xx, mul_(Xy, Xy));
+    if (CHIF) nn = mul_(nn, chik);
+    const double gx = mul_(nn, Xx), gy = mul_(nn, Xy);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       bo[i].x = fma(C.hchiW[i][q], gy, bo[i].x);
@@ -226,8 +226,8 @@ __device__ __forceinline__ void matvec_site(const StepParams& p, const JCoef<TK>
       const TK2 s = (KM == 3) ? ell_offdiag_c<TK, TK2>(p.ell_nbr, (const TK2*)p.ell_wt, p.ell_deg, S, k, P)
                               : ell_offdiag<TK, TK2>(p.ell_nbr, (const TK*)p.ell_wt, p.ell_deg, S, k, P);
       TK2 o;
-      o.x = j.a * c.x + j.e1 * c.y + s.y;
-      o.y = -j.e2 * c.x - j.a * c.y - s.x;
+      o.x = fma_(j.a, c.x, fma_(j.e1, c.y, s.y));
+      o.y = fma_(-j.e2, c.x, fma_(-j.a, c.y, -s.x));
       v[level(b, a_in + 1, i, p.s, S) + k] = o;
     }
   } else {
@@ -244,8 +244,8 @@ __device__ __forceinline__ void matvec_site(const StepParams& p, const JCoef<TK>
         o.x = fma(j.a, c.x, fma(j.e1, c.y, -fma(ty, e.y + f.y, a.y + bb.y)));
         o.y = fma(-j.e2, c.x, fma(-j.a, c.y, fma(ty, e.x + f.x, a.x + bb.x)));
       } else {
-        o.x = j.a * c.x + j.e1 * c.y - tx * (a.y + bb.y) - ty * (e.y + f.y);
-        o.y = -j.e2 * c.x - j.a * c.y + tx * (a.x + bb.x) + ty * (e.x + f.x);
+        o.x = fma_(-ty, add_(e.y, f.y), fma_(-tx, add_(a.y, bb.y), fma_(j.e1, c.y, mul_(j.a, c.x))));
+        o.y = fma_(ty, add_(e.x, f.x), fma_(tx, add_(a.x, bb.x), fma_(-j.a, c.y, mul_(-j.e2, c.x))));
       }
       v[level(b, a_in + 1, i, p.s, S) + k] = o;
     }
@@ -328,8 +328,8 @@ __device__ __forceinline__ void powers_tile(const StepParams& p, const float4* _
           const float2* P = src + i * EA;
           const float2 cc = P[c], xa = P[c - 1], xb = P[c + 1], ya = P[c - EX], yb = P[c + EX];
           float2 o;
-          o.x = j.z * cc.x + j.x * cc.y - tx * (xa.y + xb.y) - ty * (ya.y + yb.y);
-          o.y = -j.y * cc.x - j.z * cc.y + tx * (xa.x + xb.x) + ty * (ya.x + yb.x);
+          o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(j.x, cc.y, mul_(j.z, cc.x))));
+          o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-j.z, cc.y, mul_(-j.y, cc.x))));
           dst[i * EA + c] = o;
         }
       }
@@ -540,8 +540,8 @@ __device__ void gram_lsq_solve(const StepParams& p, const double* __restrict__ p
   const double sg = p.precond ? -1.0 : ic[inst].sig[i];   // preconditioned: A z_a = v_a + v_{a+1}
   for (int t = threadIdx.x; t < SK * (SK + 1); t += blockDim.x) {
     const int a = t / (SK + 1), c = t - a * (SK + 1);
-    Nm[a][c] = (c < SK) ? g(a, c) - sg * (g(a + 1, c) + g(a, c + 1)) + sg * sg * g(a + 1, c + 1)
-                        : g(a, 0) - sg * g(a + 1, 0);
+    Nm[a][c] = (c < SK) ? fma_(mul_(sg, sg), g(a + 1, c + 1), fma_(-sg, add_(g(a + 1, c), g(a, c + 1)), g(a, c)))
+                        : fma_(-sg, g(a + 1, 0), g(a, 0));
     if (c == a) Ndiag[a] = Nm[a][c];
   }
   __syncthreads();
@@ -561,7 +561,7 @@ __device__ void gram_lsq_solve(const StepParams& p, const double* __restrict__ p
       const int m = SK - a - 1;
       for (int idx = lane; idx < m * m; idx += 32) {
         const int b2 = a + 1 + idx / m, c = a + 1 + idx % m;
-        if (c <= b2) Nm[b2][c] -= Nm[b2][a] * Nm[c][a];
+        if (c <= b2) Nm[b2][c] = fma_(-Nm[b2][a], Nm[c][a], Nm[b2][c]);
       }
       __syncwarp();
     }
@@ -569,12 +569,12 @@ __device__ void gram_lsq_solve(const StepParams& p, const double* __restrict__ p
       double y[SK], cc[SK];
       for (int a = 0; a < dim; ++a) {
         double t = Nm[a][SK];
-        for (int b2 = 0; b2 < a; ++b2) t -= Nm[a][b2] * y[b2];
+        for (int b2 = 0; b2 < a; ++b2) t = fma_(-Nm[a][b2], y[b2], t);
         y[a] = t * rinv[a];
       }
       for (int a = dim - 1; a >= 0; --a) {
         double t = y[a];
-        for (int b2 = a + 1; b2 < dim; ++b2) t -= Nm[b2][a] * cc[b2];
+        for (int b2 = a + 1; b2 < dim; ++b2) t = fma_(-Nm[b2][a], cc[b2], t);
         cc[a] = t * rinv[a];
       }
       for (int a = 0; a < SK; ++a) coef[((size_t)inst * 3 + i) * kMaxS + a] = (a < dim) ? cc[a] : 0.0;
@@ -601,8 +601,8 @@ __device__ __forceinline__ void update_site(const StepParams& p, const typename 
 #pragma unroll
     for (int a = 0; a < SK; ++a) {
       const TK2 w = v[level(inst, a, i, SK, S) + k];
-      sx += cs[i][a] * w.x;
-      sy += cs[i][a] * w.y;
+      sx = fma_(cs[i][a], w.x, sx);
+      sy = fma_(cs[i][a], w.y, sy);
     }
     x[i].x = sx;
     x[i].y = sy;
@@ -627,8 +627,8 @@ __device__ __forceinline__ void update_site(const StepParams& p, const typename 
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const float t0 = p.fT[j][0], t1 = p.fT[j][1], t2 = p.fT[j][2];
-    const float rx = t0 * xf[0][0] + t1 * xf[1][0] + t2 * xf[2][0];
-    const float ry = t0 * xf[0][1] + t1 * xf[1][1] + t2 * xf[2][1];
+    const float rx = fma_(t2, xf[2][0], fma_(t1, xf[1][0], mul_(t0, xf[0][0])));
+    const float ry = fma_(t2, xf[2][1], fma_(t1, xf[1][1], mul_(t0, xf[0][1])));
     bad |= !(isfinite(rx) && isfinite(ry));
     m = fmaxf(m, fmaxf(fabsf(rx), fabsf(ry)));
   }
