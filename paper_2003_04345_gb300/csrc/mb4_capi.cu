@@ -303,6 +303,11 @@ int build_graph(mb4_batch* c) {
   return rc;
 }
 
+// Barrier slots of the persistent step: slot 0 and one per group of kBarGroup blocks.
+size_t bar_bytes(const StepParams& p) {
+  return (size_t)(1 + (p.pers_blocks + kBarGroup - 1) / kBarGroup) * kBarSlotWords * sizeof(unsigned int);
+}
+
 int ensure_scratch(mb4_batch* c) {
   if (c->io) return MB4_OK;
   const size_t S = (size_t)c->p.S, BS = (size_t)c->B * S;
@@ -680,6 +685,8 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
     if (!persistent_supported(p, c->precision == MB4_MIXED)) return MB4_ERR_INVALID_ARG;
     p.pers_blocks = persistent_blocks(p, c->precision == MB4_MIXED);
     if (p.pers_blocks < 1) return MB4_ERR_CUDA;
+    MB4_CHECK(dalloc(c, (void**)&d.bar, bar_bytes(p)));
+    MB4_TRY(cudaMemsetAsync(d.bar, 0, bar_bytes(p), c->stream));
   } else if (c->use_graph) {
     MB4_CHECK(build_graph(c));
   }
@@ -700,6 +707,8 @@ int potential_to_host(const mb4_potential* pot, size_t n, std::vector<double>* V
 int step_async(mb4_batch* c, int nsteps) {
   launch_arm(c->p, c->b, c->stream);
   if (c->p.persistent) {
+    // arrival counts start at zero (a call whose barrier gave up may have left some)
+    MB4_TRY(cudaMemsetAsync(c->b.bar, 0, bar_bytes(c->p), c->stream));
     // one cooperative launch per step, then the accept (kept outside, so that a step whose
     // barrier gave up is never half accepted)
     for (int n = 0; n < nsteps; ++n) {

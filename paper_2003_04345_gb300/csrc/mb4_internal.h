@@ -132,13 +132,16 @@ struct InstStatus {
 // Batch-wide loop control.
 struct BatchCtl {
   int any_cont;                      // some instance continues its Newton loop (k_newton_test)
-  // grid barrier of the persistent step kernel (mb4_persist.cu): arrivals of the current
-  // barrier, its generation (bumped by the last arrival), and an abort flag that a block
-  // whose bounded wait ran out sets (then every instance carries MB4_ERR_TIMEOUT)
-  unsigned int bar_count;
-  unsigned int bar_gen;
-  int abort;
+  int abort;                         // persistent step: a block's bounded barrier wait ran out
+                                     // (every instance of the step then carries MB4_ERR_TIMEOUT)
+  int pad[2];
 };
+
+// Grid barrier of the persistent step kernel: blocks arrive in groups of kBarGroup, each
+// group with its own counter and release word in a slot of its own 128-byte line (slot 0
+// counts the groups), so no cache line sees more than kBarGroup arrivals or pollers.
+constexpr int kBarGroup = 16;
+constexpr int kBarSlotWords = 32;    // unsigned ints per slot: [0] arrivals, [1] generation
 
 // Device buffers of one batch.
 struct DevBuffers {
@@ -166,6 +169,7 @@ struct DevBuffers {
   InstConst* ic;     // B
   InstStatus* is;    // B
   BatchCtl* bc;
+  unsigned int* bar; // persistent step only: (1 + groups) x kBarSlotWords barrier slots
 };
 
 // Host launchers (mb4_kernels.cu).  TK = float (mixed) or double (fp64).

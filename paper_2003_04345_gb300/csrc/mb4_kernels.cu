@@ -439,8 +439,7 @@ __global__ void k_arm(int B, int pred_order, InstStatus* is, BatchCtl* bc) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b == 0) {
     bc->any_cont = 0;
-    bc->bar_count = 0u;                          // a barrier a timed-out call left half full
-    bc->abort = 0;
+    bc->abort = 0;                               // (the barrier slots are cleared by the host)
   }
   if (b >= B) return;
   InstStatus& I = is[b];

@@ -26,31 +26,42 @@ namespace mb4 {
 namespace {
 
 // A barrier over the whole grid, after which every block sees every other block's
-// writes from before it.  The last block to arrive runs tail() (all its threads) before
-// it releases the others.  Returns false when this block must stop: its wait ran out,
-// or another block's did (abort).  Every thread of every block calls it.
+// writes from before it.  Arrival is two-level: a block counts itself in its group's slot,
+// the group's last block counts the group in slot 0, and the last group's last block --
+// the last block to arrive -- runs tail() (all its threads) and then bumps every group's
+// release word.  Each block polls only its own group's word.  Returns false when this
+// block must stop: its wait ran out, or another block's did (abort).  Every thread of
+// every block calls it.
 template <typename Tail>
-__device__ __forceinline__ bool grid_barrier(BatchCtl* bc, InstStatus* is, int B, long long limit, Tail tail) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, BatchCtl* bc, InstStatus* is, int B, long long limit,
+                                             Tail tail) {
   __shared__ int s_state;                        // 0 stop, 1 released, 2 last to arrive
   volatile BatchCtl* vb = bc;
+  const unsigned int ng = (gridDim.x + kBarGroup - 1) / kBarGroup;
   __syncthreads();
   if (threadIdx.x == 0) {
     int state = 0;
     if (!vb->abort) {
-      // the generation cannot move before this block arrives, so this is the current one
-      const unsigned int gen = vb->bar_gen;
+      const unsigned int g = blockIdx.x / kBarGroup;
+      const unsigned int members = min((unsigned int)kBarGroup, gridDim.x - g * kBarGroup);
+      unsigned int* grp = bar + (size_t)(1 + g) * kBarSlotWords;
+      volatile unsigned int* rel = grp + 1;
+      // the release word cannot move before this block arrives, so this is the current one
+      const unsigned int gen = *rel;
       __threadfence();                           // this block's writes before the arrival
-      const unsigned int arrived = atomicAdd(&bc->bar_count, 1u);
-      if (arrived == gridDim.x - 1) {
-        state = 2;
-      } else {
+      if (atomicAdd(grp, 1u) == members - 1) {   // the group is complete: count it
+        atomicExch(grp, 0u);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == ng - 1) state = 2;
+      }
+      if (state != 2) {
         for (long long n = 0;; ++n) {
-          if (vb->bar_gen != gen) {
+          if (*rel != gen) {
             state = 1;
             break;
           }
           if (vb->abort || n >= limit) break;
-          __nanosleep(64);
+          __nanosleep(32);
         }
         if (state == 0 && !vb->abort) {          // this block's wait ran out: fail the step
           for (int b = 0; b < B; ++b)
@@ -69,9 +80,9 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* bc, InstStatus* is, int B
     tail();
     __syncthreads();
     if (threadIdx.x == 0) {
-      atomicExch(&bc->bar_count, 0u);            // before the release, so no arrival at the
+      atomicExch(bar, 0u);                       // before the release, so no arrival at the
       __threadfence();                           // next barrier counts against this one
-      atomicAdd(&bc->bar_gen, 1u);
+      for (unsigned int h = 0; h < ng; ++h) atomicAdd(bar + (size_t)(1 + h) * kBarSlotWords + 1, 1u);
     }
     __syncthreads();
     return true;
@@ -114,7 +125,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_step_persistent(StepPara
                                          is[b], b, k));
     block_max_into(m, &is[b].u0max_bits);
   }
-  if (!grid_barrier(bc, is, B, lim, NoTail())) return;
+  if (!grid_barrier(d.bar, bc, is, B, lim, NoTail())) return;
 
   for (;;) {
     // residual b = -Phibar (the first one of a step from U^0 = e3 (x) u0 was written by the set-up)
@@ -123,7 +134,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_step_persistent(StepPara
       for (int k = gtid; k < S; k += gstride)
         residual_site<TK, CHIF, KMR>(p, d.u, D, d.S0, d.Ubar, v, os, d.chi, d.ic[b], b, k);
     }
-    if (!grid_barrier(bc, is, B, lim, NoTail())) return;
+    if (!grid_barrier(d.bar, bc, is, B, lim, NoTail())) return;
 
     // Krylov basis: all s levels per tile (FP32 matrix powers) or one level per phase (FP64)
     if constexpr (MIXED) {
@@ -133,14 +144,14 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_step_persistent(StepPara
         if (!is[b].active) continue;
         powers_tile<SK>(p, (const float4*)d.jc, (float2*)d.v, d.ic[b], b, item - b * tiles, smem_raw);
       }
-      if (!grid_barrier(bc, is, B, lim, NoTail())) return;
+      if (!grid_barrier(d.bar, bc, is, B, lim, NoTail())) return;
     } else {
       for (int a = 0; a < SK; ++a) {
         for (int b = 0; b < B; ++b) {
           if (!is[b].active) continue;
           for (int k = gtid; k < S; k += gstride) matvec_site<TK, KMV>(p, (const JCoef<TK>*)d.jc, v, a, d.ic[b], b, k);
         }
-        if (!grid_barrier(bc, is, B, lim, NoTail())) return;
+        if (!grid_barrier(d.bar, bc, is, B, lim, NoTail())) return;
       }
     }
 
@@ -174,7 +185,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_step_persistent(StepPara
       }
       __syncthreads();
     }
-    if (!grid_barrier(bc, is, B, lim, NoTail())) return;
+    if (!grid_barrier(d.bar, bc, is, B, lim, NoTail())) return;
 
     // Newton update, then the loop test in the last block to arrive
     for (int b = 0; b < B; ++b) {
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_step_persistent(StepPara
       block_update_flags(m, bad, is[b]);
     }
     auto test = [&]() { newton_test_all(p, is, bc); };
-    if (!grid_barrier(bc, is, B, lim, test)) return;
+    if (!grid_barrier(d.bar, bc, is, B, lim, test)) return;
     if (!((volatile BatchCtl*)bc)->any_cont) break;
   }
 }
