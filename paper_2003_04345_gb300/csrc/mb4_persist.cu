@@ -19,6 +19,8 @@
 // is resident, so in a healthy run no wait comes near the limit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "mb4_phases.cuh"
 
 namespace mb4 {
@@ -247,7 +249,12 @@ int persistent_blocks(const StepParams& p, bool mixed) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kPersistThreads, smem) != cudaSuccess || occ < 1)
     return 0;
-  return sms * occ;
+  // no more blocks than the sites (or, in FP32, the tiles) give one thread (block) work:
+  // a small problem then needs fewer arrivals per barrier
+  const long long sites = (long long)p.B * p.S;
+  long long want = (sites + kPersistThreads - 1) / kPersistThreads;
+  if (mixed) want = std::max(want, (long long)p.B * ((p.nx + kPowTX - 1) / kPowTX) * ((p.ny + kPowTY - 1) / kPowTY));
+  return (int)std::min<long long>((long long)sms * occ, std::max<long long>(want, 1));
 }
 
 cudaError_t launch_step_persistent(const StepParams& p, const DevBuffers& b, bool mixed, cudaStream_t st) {
