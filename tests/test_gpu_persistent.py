@@ -106,8 +106,9 @@ def test_persistent_batch_equals_graph_batch(mb4, precision):
 def test_persistent_wait_limit_zero_times_out_and_keeps_the_state(mb4, precision):
     """wait_limit = 0: a grid-barrier wait gives up at its first poll.  The step returns
     MB4_ERR_TIMEOUT (no hang, no fault), the state stays at the last accepted step, and
-    the context stays usable: observables, and a following call that times out again."""
-    w = inputs.grid16_fp64()
+    the context stays usable: observables, and a following call that times out again.
+    (64 x 64, so that the step runs on several blocks: one block alone never waits.)"""
+    w = inputs.Workload("grid64", 64, 64, h=0.01, steps=10, chi=1.0, W=1.0, defect_fraction=0.01, sigma=4.0)
     with mb4.from_workload(w, precision=precision, persistent=1, wait_limit=0) as it:
         u0 = it.get_state()
         H0 = it.energy()[0]
