@@ -947,6 +947,19 @@ int mb4_batch_step(mb4_batch* c, int nsteps, mb4_stats* stats, int* status) {
   return wait_batch(c, stats, status);
 }
 
+}  // extern "C"
+
+int mb4::batch_observables_async(mb4_batch* c, double* host_out) {
+  if (!c || !host_out) return MB4_ERR_INVALID_ARG;
+  launch_observables(c->p, c->b, c->stream);
+  MB4_TRY(cudaGetLastError());
+  MB4_TRY(cudaMemcpyAsync(host_out, c->b.obs_out, (size_t)c->B * 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  return MB4_OK;
+}
+
+extern "C" {
+
 int mb4_batch_observables(const mb4_batch* cc, double* out) {
   mb4_batch* c = const_cast<mb4_batch*>(cc);
   if (!c || !out) return MB4_ERR_INVALID_ARG;

@@ -172,6 +172,12 @@ struct DevBuffers {
   unsigned int* bar; // persistent step only: (1 + groups) x kBarSlotWords barrier slots
 };
 
+// The observables of every instance of a batch, enqueued on the batch's stream and copied
+// to host_out (batch x 6 doubles; page-locked memory for the copy to be asynchronous)
+// without waiting (mb4_capi.cu).  For the serving loop, which reads them once a later
+// event on that stream has completed.
+int batch_observables_async(mb4_batch* b, double* host_out);
+
 // Host launchers (mb4_kernels.cu).  TK = float (mixed) or double (fp64).
 template <typename TK> void launch_setup(const StepParams& p, const DevBuffers& b, cudaStream_t st);
 template <typename TK> void launch_residual(const StepParams& p, const DevBuffers& b, bool skip_first,

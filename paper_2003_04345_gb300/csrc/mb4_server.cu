@@ -1,16 +1,19 @@
 // libmb4 serving loop: continuous batching of MB4 simulation requests.
 //
 // One batch per shape class (nx, ny, tx, ty, onsite, h), each on its own CUDA
-// stream, inside an HBM budget.  Every pass of the loop
-//   1. admits each request that has arrived into a free slot of its class
-//      (creating the class's batch when the budget allows, releasing idle
-//      batches when it does not),
-//   2. enqueues the next chunk of steps of every class with running requests
-//      on that class's stream (so different classes overlap on the GPU; a
-//      chunk never runs past the earliest finishing request of its class),
-//   3. waits, books the steps, and retires the requests that reached their
-//      step count, freeing their slots for the queue.
-// States stay on the GPU from admission to completion.
+// stream, inside an HBM budget.  The classes run independently in time: the loop
+// polls each class's last chunk with an event and, as soon as THAT class is idle,
+//   1. books the chunk's steps and retires the requests that reached their step
+//      count (final energy, final state), freeing their slots,
+//   2. admits every arrived request of that class into a free slot (creating the
+//      class's batch when the budget allows, releasing idle batches when it does
+//      not), queues the observables of the new requests (their start energy, read
+//      back asynchronously) and
+//   3. enqueues the class's next chunk of steps (at most 32, never past its earliest
+//      finishing request) and records its event.
+// A small class therefore keeps admitting, stepping and retiring while a large class
+// is in the middle of a long chunk; the kernels of different classes overlap on the
+// GPU.  States stay on the GPU from admission to completion.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,7 +40,6 @@ struct ServerReq {
   int cls = -1, slot = -1;
   long long remaining = 0;
   bool queued = true;
-  bool need_h0 = false;
   std::vector<double> out_re, out_im;
 };
 
@@ -46,6 +48,10 @@ struct ClassBatch {
   double h = 0;
   mb4_batch* b = nullptr;
   cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;        // recorded after the class's last enqueued chunk
+  bool in_flight = false;            // a chunk is queued or running on the class's stream
+  double* obs = nullptr;             // page-locked, slots x 6: observables read back asynchronously
+  std::vector<int> start_pending;    // slots whose start energy is in obs once the chunk is done
   int slots = 0;
   long long bytes = 0;
   std::vector<long long> slot_req;   // request in each slot, -1 = free
@@ -78,12 +84,18 @@ struct mb4_server {
 
 namespace {
 
+void free_class(ClassBatch* c) {
+  if (c->b) mb4_batch_destroy(c->b);
+  if (c->done) cudaEventDestroy(c->done);
+  if (c->obs) cudaFreeHost(c->obs);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
 void release_class(mb4_server* s, size_t idx) {
   ClassBatch* c = s->classes[idx];
-  if (c->b) mb4_batch_destroy(c->b);
-  if (c->stream) cudaStreamDestroy(c->stream);
   s->used -= c->bytes;
-  delete c;
+  free_class(c);
   s->classes.erase(s->classes.begin() + idx);
 }
 
@@ -94,7 +106,7 @@ ClassBatch* create_class(mb4_server* s, const mb4_grid& g, double h, int want) {
   if (one <= 0) return nullptr;
   if (s->used + one > s->budget) {
     for (size_t i = 0; i < s->classes.size();) {
-      if (s->classes[i]->running == 0) release_class(s, i);
+      if (s->classes[i]->running == 0 && !s->classes[i]->in_flight) release_class(s, i);
       else ++i;
       if (s->used + one <= s->budget) break;
     }
@@ -117,11 +129,11 @@ ClassBatch* create_class(mb4_server* s, const mb4_grid& g, double h, int want) {
   const size_t S = (size_t)g.nx * g.ny;
   std::vector<double> V(S * slots, 0.0), chi(slots, 0.0);
   mb4_potential pot{V.data(), 0};
-  if (mb4_batch_create(&g, slots, &pot, chi.data(), h, &o, &c->b) != MB4_OK ||
+  if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost((void**)&c->obs, (size_t)slots * 6 * sizeof(double)) != cudaSuccess ||
+      mb4_batch_create(&g, slots, &pot, chi.data(), h, &o, &c->b) != MB4_OK ||
       mb4_batch_enable(c->b, -1, 0) != MB4_OK) {
-    if (c->b) mb4_batch_destroy(c->b);
-    cudaStreamDestroy(c->stream);
-    delete c;
+    free_class(c);
     return nullptr;
   }
   c->slot_req.assign(slots, -1);
@@ -147,6 +159,41 @@ void complete(mb4_server* s, ClassBatch* c, int slot, int status, double energy_
   c->slot_req[slot] = -1;
   c->running -= 1;
   s->n_done += 1;
+}
+
+// Books the finished chunk of an idle class: steps, start energies of the requests admitted
+// before it, retirement of the requests that are done.  Returns MB4_OK or a call failure.
+int harvest_class(mb4_server* s, ClassBatch* c, std::vector<mb4_stats>& stats, std::vector<int>& codes,
+                  std::vector<double>& obs) {
+  for (int sl : c->start_pending)                // queued before the chunk, so complete now
+    if (c->slot_req[sl] >= 0) s->reqs[c->slot_req[sl]].res.energy_start = c->obs[(size_t)sl * 6];
+  c->start_pending.clear();
+  stats.resize(c->slots);
+  codes.resize(c->slots);
+  const int wrc = mb4_batch_wait(c->b, stats.data(), codes.data());   // the stream is idle
+  if (wrc != MB4_OK && wrc != MB4_ERR_NEWTON_NOT_CONVERGED && wrc != MB4_ERR_NONFINITE && wrc != MB4_ERR_TIMEOUT)
+    return wrc;                                  // the call itself failed
+  bool finished = false;
+  for (int sl = 0; sl < c->slots; ++sl) {
+    const long long id = c->slot_req[sl];
+    if (id < 0) continue;
+    ServerReq& r = s->reqs[id];
+    r.res.steps_done += stats[sl].steps_done;
+    r.res.newton_iters_total += stats[sl].newton_iters_total;
+    r.remaining -= stats[sl].steps_done;
+    if (codes[sl] != MB4_OK || r.remaining <= 0) finished = true;
+  }
+  if (!finished) return MB4_OK;
+  obs.resize((size_t)c->slots * 6);
+  const int orc = mb4_batch_observables(c->b, obs.data());   // final energies (idle stream)
+  if (orc != MB4_OK) return orc;
+  for (int sl = 0; sl < c->slots; ++sl) {
+    const long long id = c->slot_req[sl];
+    if (id < 0) continue;
+    if (codes[sl] != MB4_OK || s->reqs[id].remaining <= 0) complete(s, c, sl, codes[sl], obs[(size_t)sl * 6]);
+  }
+  if (std::any_of(codes.begin(), codes.end(), [](int x) { return x != MB4_OK; })) mb4_batch_clear_errors(c->b);
+  return MB4_OK;
 }
 
 }  // namespace
@@ -218,7 +265,20 @@ int mb4_server_run(mb4_server* s, double until, long long* n_done) {
   for (;;) {
     const double t = s->now();
     if (t >= until) break;
-    // 1. admission (first come, first served among the requests that have arrived)
+    bool progress = false;
+    // 1. classes whose chunk has finished: book it, retire finished requests
+    for (ClassBatch* c : s->classes) {
+      if (!c->in_flight) continue;
+      const cudaError_t q = cudaEventQuery(c->done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return MB4_ERR_CUDA;
+      c->in_flight = false;
+      progress = true;
+      const int rc = harvest_class(s, c, stats, codes, obs);
+      if (rc != MB4_OK) return rc;
+    }
+    // 2. admission (first come, first served among the requests that have arrived), into
+    //    classes that are idle; a request whose class is mid-chunk waits for that chunk only
     for (auto it = s->queue.begin(); it != s->queue.end();) {
       ServerReq& r = s->reqs[*it];
       if (r.arrival > t) {
@@ -226,12 +286,17 @@ int mb4_server_run(mb4_server* s, double until, long long* n_done) {
         continue;
       }
       ClassBatch* c = nullptr;
+      bool busy_class = false;                   // a batch of this class is mid-chunk with room
       for (ClassBatch* cb : s->classes)
         if (same_class(*cb, r.grid, r.h) && cb->running < cb->slots) {
+          if (cb->in_flight) {
+            busy_class = true;
+            continue;
+          }
           c = cb;
           break;
         }
-      if (!c) {
+      if (!c && !busy_class) {
         int want = 0;   // requests of this class that have arrived and wait
         for (long long q : s->queue)
           if (s->reqs[q].arrival <= t && s->reqs[q].grid.nx == r.grid.nx && s->reqs[q].grid.ny == r.grid.ny &&
@@ -266,85 +331,51 @@ int mb4_server_run(mb4_server* s, double until, long long* n_done) {
       if (rc != MB4_OK) return rc;
       c->slot_req[slot] = *it;
       c->running += 1;
+      c->start_pending.push_back(slot);
       r.cls = 0;
       r.slot = slot;
       r.remaining = r.nsteps;
       r.queued = false;
-      r.need_h0 = true;
       r.res.admitted = s->now();
       std::vector<double>().swap(r.v);
       std::vector<double>().swap(r.re);
       std::vector<double>().swap(r.im);
+      progress = true;
       it = s->queue.erase(it);
     }
-    // energy at admission
+    // 3. every idle class with running requests: the start energies of its new requests
+    //    (read back when the chunk is done), then its next chunk and its event
     for (ClassBatch* c : s->classes) {
-      bool any = false;
-      for (int k = 0; k < c->slots; ++k)
-        if (c->slot_req[k] >= 0 && s->reqs[c->slot_req[k]].need_h0) any = true;
-      if (!any) continue;
-      obs.resize((size_t)c->slots * 6);
-      int rc = mb4_batch_observables(c->b, obs.data());
-      if (rc != MB4_OK) return rc;
-      for (int k = 0; k < c->slots; ++k)
-        if (c->slot_req[k] >= 0 && s->reqs[c->slot_req[k]].need_h0) {
-          s->reqs[c->slot_req[k]].res.energy_start = obs[(size_t)k * 6];
-          s->reqs[c->slot_req[k]].need_h0 = false;
-        }
-    }
-    // 2. enqueue one chunk per class with running requests
-    bool stepped = false;
-    for (ClassBatch* c : s->classes) {
-      c->chunk = 0;
-      if (c->running == 0) continue;
+      if (c->in_flight || c->running == 0) continue;
+      if (!c->start_pending.empty()) {
+        const int rc = mb4::batch_observables_async(c->b, c->obs);
+        if (rc != MB4_OK) return rc;
+      }
       long long k = kMaxChunk;
       for (int sl = 0; sl < c->slots; ++sl)
         if (c->slot_req[sl] >= 0) k = std::min(k, s->reqs[c->slot_req[sl]].remaining);
       int rc = mb4_batch_step_async(c->b, (int)k);
       if (rc != MB4_OK) return rc;
+      if (cudaEventRecord(c->done, c->stream) != cudaSuccess) return MB4_ERR_CUDA;
       c->chunk = k;
-      stepped = true;
+      c->in_flight = true;
+      progress = true;
     }
-    if (!stepped) {
-      if (s->queue.empty()) break;
-      double next = 1e300;
-      for (long long q : s->queue) next = std::min(next, s->reqs[q].arrival);
-      if (next > s->now()) {
-        const double dt = std::min(next - s->now(), until - s->now());
-        if (dt > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(dt, 0.01)));
-      } else if (s->classes.empty()) {
-        return MB4_ERR_ADMISSION_REJECTED;   // arrived requests, nothing running, nothing creatable
+    bool any_flight = false;
+    for (ClassBatch* c : s->classes) any_flight |= c->in_flight;
+    if (!any_flight && s->queue.empty()) break;
+    if (progress) continue;
+    // 4. nothing to do until a chunk finishes or a request arrives
+    double next = 1e300;
+    for (long long q : s->queue) next = std::min(next, s->reqs[q].arrival);
+    if (!any_flight) {
+      if (next <= s->now()) {
+        if (s->classes.empty()) return MB4_ERR_ADMISSION_REJECTED;   // arrived, nothing creatable
       }
-      continue;
-    }
-    // 3. wait and retire
-    for (ClassBatch* c : s->classes) {
-      if (c->chunk == 0) continue;
-      stats.resize(c->slots);
-      codes.resize(c->slots);
-      const int wrc = mb4_batch_wait(c->b, stats.data(), codes.data());
-      if (wrc != MB4_OK && wrc != MB4_ERR_NEWTON_NOT_CONVERGED && wrc != MB4_ERR_NONFINITE) return wrc;   // the call failed
-      bool finished = false;
-      for (int sl = 0; sl < c->slots; ++sl) {
-        const long long id = c->slot_req[sl];
-        if (id < 0) continue;
-        ServerReq& r = s->reqs[id];
-        r.res.steps_done += stats[sl].steps_done;
-        r.res.newton_iters_total += stats[sl].newton_iters_total;
-        r.remaining -= stats[sl].steps_done;
-        if (codes[sl] != MB4_OK || r.remaining <= 0) finished = true;
-      }
-      if (!finished) continue;
-      obs.resize((size_t)c->slots * 6);
-      const int orc = mb4_batch_observables(c->b, obs.data());
-      if (orc != MB4_OK) return orc;
-      for (int sl = 0; sl < c->slots; ++sl) {
-        const long long id = c->slot_req[sl];
-        if (id < 0) continue;
-        if (codes[sl] != MB4_OK || s->reqs[id].remaining <= 0) complete(s, c, sl, codes[sl], obs[(size_t)sl * 6]);
-      }
-      if (codes.size() && std::any_of(codes.begin(), codes.end(), [](int x) { return x != MB4_OK; }))
-        mb4_batch_clear_errors(c->b);
+      const double dt = std::min(next - s->now(), until - s->now());
+      if (dt > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(dt, 0.01)));
+    } else {
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
   }
   if (n_done) *n_done = s->n_done;

@@ -108,6 +108,29 @@ def test_waiting_requests_take_freed_slots(mb4):
     assert sum(1 for b in spans if any(b[0] >= a[1] for a in spans if a is not b)) >= 3  # waited for a slot
 
 
+def test_small_request_finishes_while_a_large_class_is_mid_chunk(mb4):
+    """Each shape class is polled on its own: a 1024 x 1024 request of 256 steps (8 chunks
+    of 32 steps) arrives first, a 32 x 32 request of 20 steps 5 ms later.  The small one is
+    admitted, stepped and retired while the large class is inside one of its chunks: its
+    latency is well under one large chunk, instead of waiting for the large chunk to end."""
+    big = dict(nx=1024, ny=1024, h=0.002, nsteps=256, chi=1.0, arrival=0.0,
+               V=inputs.potential(1024, 1024, 1.0, 10000, 20.0, 11),
+               psi=inputs.wavepacket(1024, 1024, 16.0, math.pi / 4, 0.0))
+    small = dict(nx=32, ny=32, h=0.01, nsteps=20, chi=1.0, arrival=0.005,
+                 V=inputs.potential(32, 32, 1.0, 10, 20.0, 12),
+                 psi=inputs.wavepacket(32, 32, 3.0, math.pi / 4, 0.0))
+    with mb4.Server(8 << 30, max_slots=2, keep_states=True, precision="mixed") as srv:
+        ids = [srv.submit(q["nx"], q["ny"], q["V"], q["chi"], q["psi"], q["h"], q["nsteps"], q["arrival"])
+               for q in (big, small)]
+        assert srv.run() == 2
+        (rb, _), (rs, us) = [srv.result(i, state=True) for i in ids]
+    assert rb["status"] == 0 and rs["status"] == 0
+    chunk = (rb["completed"] - rb["admitted"]) / 8
+    assert rs["completed"] < rb["completed"]
+    assert rs["completed"] - rs["arrival"] < 0.5 * chunk, (rs["completed"] - rs["arrival"], chunk)
+    assert _rel(us, _oracle(small)) <= 1e-11
+
+
 def test_budget_limits_concurrency(mb4):
     reqs = [dict(q, nx=32, ny=20) for q in _trace(5, seed=1)]
     for q in reqs:
