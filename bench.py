@@ -726,6 +726,16 @@ def full_runs():
     print(json.dumps({"full_runs": out}))
 
 
+def served_full():
+    """The served stream at the size its p50/p99 need: the first 2000 arrivals of the
+    200 req/s trace, and a rate sweep of 100 requests per rate at 0.5, 1 and 2 req/s (the
+    first 100 requests of the same trace, arrival gaps scaled by 200/rate).  A validation
+    run of tens of minutes: prints one JSON line, not a bench line."""
+    out = {"served_poisson200_first2000": bench_served(None, n_requests=2000, rate=200.0),
+           "rate_sweep_100": [bench_served(None, n_requests=100, rate=r) for r in (0.5, 1.0, 2.0)]}
+    print(json.dumps({"served_full": out}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -739,6 +749,9 @@ def main():
                     help="run 6 host-driven steps of the 512x512 (or 2048x2048) workload for ncu and exit")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the ensemble, 2048^2 and served-stream lines")
+    ap.add_argument("--served-full", action="store_true",
+                    help="replay the first 2000 arrivals of the 200 req/s trace and a 100-request rate "
+                         "sweep through the server, and exit")
     ap.add_argument("--full-runs", action="store_true",
                     help="run the 2048^2 and ensemble configurations over their whole step counts "
                          "(energy drift, Newton counts) and exit")
@@ -751,6 +764,9 @@ def main():
         return
     if args.full_runs:
         full_runs()
+        return
+    if args.served_full:
+        served_full()
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

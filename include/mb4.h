@@ -416,7 +416,9 @@ typedef struct {
 
 /* hbm_budget_bytes: device memory the server's batches may hold together;
  * max_slots: instances per class batch, at most; keep_states: 1 to keep each
- * final state for mb4_server_result.  opt applies to every batch. */
+ * final state for mb4_server_result.  opt applies to every batch, except that the
+ * server's batches skip the launch-shape tuner (its timings would run behind the
+ * other classes' kernels and delay the admitted request). */
 int mb4_server_create(long long hbm_budget_bytes, int max_slots, int keep_states, const mb4_options* opt,
                       mb4_server** out);
 void mb4_server_destroy(mb4_server* s);

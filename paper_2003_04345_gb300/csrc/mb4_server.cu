@@ -13,7 +13,8 @@
 //      finishing request) and records its event.
 // A small class therefore keeps admitting, stepping and retiring while a large class
 // is in the middle of a long chunk; the kernels of different classes overlap on the
-// GPU.  States stay on the GPU from admission to completion.
+// GPU, and smaller classes run on higher-priority streams.  States stay on the GPU from
+// admission to completion.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -120,12 +121,23 @@ ClassBatch* create_class(mb4_server* s, const mb4_grid& g, double h, int want) {
   c->h = h;
   c->slots = slots;
   c->bytes = mb4_batch_bytes(g.nx, g.ny, slots, &s->opt);
-  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // Smaller classes get higher stream priority: when SMs free up, the block scheduler
+  // serves their short kernels before the pending blocks of a large class, so a small
+  // request is not stretched to the pace of a large class running beside it.
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const long long sites = (long long)g.nx * g.ny;
+  const int prio = (sites <= 128LL * 128) ? greatest : (sites <= 512LL * 512) ? (least + greatest) / 2 : least;
+  if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
     delete c;
     return nullptr;
   }
   mb4_options o = s->opt;
   o.stream = c->stream;
+  // no launch-shape timing at admission: its launches would queue behind the kernels of
+  // the classes already running (a delay for the new request) and time their load rather
+  // than the class's own kernels; the classes keep the default shape
+  o.autotune = 0;
   const size_t S = (size_t)g.nx * g.ny;
   std::vector<double> V(S * slots, 0.0), chi(slots, 0.0);
   mb4_potential pot{V.data(), 0};
