@@ -127,11 +127,13 @@ typedef struct {
                             bit for bit.  0 = always extrapolate once history exists.        */
     int    autotune;     /* 1 (default): at create, time the one-site-per-thread kernels
                             (residual, Krylov basis, update; set-up and accept follow the
-                            residual) with 64, 128 and 256 threads per block on the context's
-                            own buffers and keep the fastest (128 unless another is faster by
-                            more than 5%); the choice is cached per device,
-                            precision, grid, batch size and s.  Every choice gives the same
-                            results bit for bit.  0: 128 threads everywhere.                 */
+                            residual) with 64, 128 and 256 threads per block, and in mixed
+                            mode the matrix-powers kernel with tiles of 32 x 16, 32 x 32,
+                            64 x 16 and 32 x 8 sites, on the context's own buffers, and keep
+                            the fastest (the default unless another is faster by more than
+                            5%); the choice is cached per device, precision, grid, batch size
+                            and s.  Every choice gives the same results bit for bit.  0: 128
+                            threads and the 32 x 16 tile everywhere.                          */
     int    site_threads; /* 0 (default): as autotune says.  64, 128 or 256: that many threads per
                             block for every per-site kernel, no tuning.                       */
     int    precondition; /* 0 (default): the shifted solves use the monomial Krylov basis of J.
@@ -156,6 +158,10 @@ typedef struct {
                             results bit for bit.  Grid problems (mb4_create, mb4_batch_create)
                             without the preconditioner, krylov_s 4 or 5; else
                             MB4_ERR_INVALID_ARG at create.                                     */
+    int    powers_tile;  /* mixed mode, matrix-powers basis: 0 (default) = the tuner's choice
+                            (32 x 16 when autotune = 0); 1, 2, 3, 4 = a tile of 32 x 16,
+                            32 x 32, 64 x 16 or 32 x 8 sites (krylov_s <= 6 for 2..4).  Every
+                            tile gives the same basis bit for bit.                            */
     long long wait_limit; /* persistent = 1: polls (each followed by a short sleep) that a
                             grid-barrier wait makes before it gives up; the step then fails
                             with MB4_ERR_TIMEOUT and the state stays at the last accepted step.
@@ -370,6 +376,12 @@ int mb4_batch_set_chi_field(mb4_batch* b, int instance, const double* chi, int o
 
 /* As mb4_get_launch_shape, for a batch. */
 int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);
+
+/* The tile (*tx x *ty sites) of the FP32 matrix-powers Krylov basis that the tuner chose
+ * for this batch or context (cast an mb4_ctx* to mb4_batch*: a context is a batch of one),
+ * or 0 x 0 where that kernel is not used (FP64 mode, the preconditioner, a general K).
+ * Every tile gives the same basis bit for bit. */
+int mb4_batch_get_tile_shape(const mb4_batch* b, int* tx, int* ty);
 
 /* As mb4_step_profiled, for a batch: nsteps steps of every enabled instance with a
  * host-driven Newton loop and an event pair around every launch; adds the summed

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "mb4_internal.h"
+#include "mb4_phases.cuh"
 
 using namespace mb4;
 
@@ -44,6 +45,7 @@ struct mb4_batch {
   int* ell_nbr = nullptr;         // general kinetic matrix (mb4_create_sparse), device
   void* ell_w = nullptr;          // double, or double2 for a complex K
   void* ell_wt = nullptr;
+  bool forced_tile = false;       // option powers_tile set: the tuner keeps it
 };
 
 struct mb4_ctx : mb4_batch {};
@@ -102,6 +104,8 @@ int validate_options(const mb4_options* in, mb4_options* o) {
   if (o->site_chi != 0 && o->site_chi != 1) return MB4_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return MB4_ERR_INVALID_ARG;
   if (o->wait_limit < 0) return MB4_ERR_INVALID_ARG;
+  if (o->powers_tile < 0 || o->powers_tile > kPowShapes) return MB4_ERR_INVALID_ARG;
+  if (o->powers_tile > 1 && o->krylov_s > kPowShapeMaxS) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -181,6 +185,7 @@ void fill_params(mb4_batch* c, const mb4_grid* grid, double h, const mb4_options
   p.bs_site = p.bs_residual = p.bs_matvec = p.bs_update = o.site_threads > 0 ? o.site_threads : 128;
   p.pred_order = o.newton_start;
   p.persistent = o.persistent;
+  p.pow_shape = o.powers_tile > 0 ? o.powers_tile - 1 : 0;
   p.wait_limit = o.wait_limit;
   p.pred_adaptive = o.newton_start_adaptive;
   // Cost of the extra residual of an extrapolated start, in Newton iterations (1/1000):
@@ -434,14 +439,18 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
 // candidate: its loop made the default launch 5% slower, so it is not offered.)
 typedef std::tuple<int, int, int, int, int, int, int> TuneKey;   // device, precision, nx, ny, B, s, precond
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 4>> g_tune;
+std::map<TuneKey, std::array<int, 5>> g_tune;   // threads of the four per-site groups, powers tile shape
 
+// which: 0 residual, 1 FP64 stencil basis, 2 update (bs = threads per block), 3 FP32 matrix
+// powers (bs = tile shape index).
 int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
   if (which == 1 && (c->precision == MB4_MIXED || c->p.precond)) return MB4_ERR_INVALID_ARG;   // FP64 buffers only
+  if (which == 3 && !(c->precision == MB4_MIXED && c->p.use_powers)) return MB4_ERR_INVALID_ARG;
   StepParams p = c->p;
   if (which == 0) p.bs_residual = bs;
   else if (which == 1) p.bs_matvec = bs;
-  else p.bs_update = bs;
+  else if (which == 2) p.bs_update = bs;
+  else p.pow_shape = bs;
   const bool mixed = (c->precision == MB4_MIXED);
   float total = 0.f;
   for (int r = 0; r < 11; ++r) {
@@ -452,6 +461,8 @@ int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_
       else launch_residual<double>(p, c->b, false, c->stream);
     } else if (which == 1) {
       launch_matvecs<double>(p, c->b, c->stream);
+    } else if (which == 3) {
+      launch_matvecs<float>(p, c->b, c->stream);
     } else {
       if (mixed) launch_update<float>(p, c->b, 0ull, 0, c->stream);
       else launch_update<double>(p, c->b, 0ull, 0, c->stream);
@@ -466,11 +477,12 @@ int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_
   return MB4_OK;
 }
 
-void apply_shape(StepParams& p, const std::array<int, 4>& t) {
+void apply_shape(StepParams& p, const std::array<int, 5>& t) {
   p.bs_site = t[0];
   p.bs_residual = t[1];
   p.bs_matvec = t[2];
   p.bs_update = t[3];
+  p.pow_shape = t[4];
 }
 
 int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
@@ -479,7 +491,7 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) {
+    if (it != g_tune.end() && !c->forced_tile) {  // (a forced tile is neither taken from nor put in the cache)
       apply_shape(c->p, it->second);
       return MB4_OK;
     }
@@ -505,15 +517,25 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
       if (t[k] < 0.95f * t[best]) best = k;
     chosen[which] = cand[best];
   }
+  // FP32 matrix-powers tile: the default 32 x 16 unless another shape is clearly faster
+  int shape = c->p.pow_shape;                    // a forced tile (option powers_tile) stays
+  if (rc == MB4_OK && mixed && c->p.use_powers && c->p.s <= kPowShapeMaxS && !c->forced_tile) {
+    float t[kPowShapes];
+    for (int k = 0; k < kPowShapes && rc == MB4_OK; ++k) rc = time_site_kernel(c, 3, k, e0, e1, &t[k]);
+    if (rc == MB4_OK)
+      for (int k = 1; k < kPowShapes; ++k)
+        if (t[k] < 0.95f * t[shape]) shape = k;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != MB4_OK) return rc;
-  const std::array<int, 4> t = {chosen[0], chosen[0], chosen[1], chosen[2]};
+  const std::array<int, 5> t = {chosen[0], chosen[0], chosen[1], chosen[2], shape};
   apply_shape(c->p, t);
   // the timing launches wrote scratch, the increments and the status: start clean
   MB4_TRY(cudaMemsetAsync(c->b.Ubar, 0, (size_t)3 * c->B * c->p.S * sizeof(double2), c->stream));
   MB4_TRY(cudaMemsetAsync(c->b.bc, 0, sizeof(BatchCtl), c->stream));
   MB4_CHECK(write_status(c));
+  if (c->forced_tile) return MB4_OK;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = t;
   return MB4_OK;
@@ -548,6 +570,7 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
   MB4_CHECK(compute_constants(o.alpha1, o.c1, o.c2, &c->k));
   c->precision = o.precision;
   c->use_graph = o.use_graph ? 1 : 0;
+  c->forced_tile = o.powers_tile > 0;
   c->stream = (cudaStream_t)o.stream;
   c->tk = (o.precision == MB4_MIXED) ? sizeof(float) : sizeof(double);
   c->B = B;
@@ -1011,6 +1034,14 @@ int mb4_batch_get_launch_shape(const mb4_batch* c, int* shape8) {
 }
 
 int mb4_get_launch_shape(const mb4_ctx* c, int* shape8) { return mb4_batch_get_launch_shape(c, shape8); }
+
+int mb4_batch_get_tile_shape(const mb4_batch* c, int* tx, int* ty) {
+  if (!c || !tx || !ty) return MB4_ERR_INVALID_ARG;
+  const bool powers = c->precision == MB4_MIXED && c->p.use_powers;
+  *tx = powers ? kPowShapeTX[c->p.pow_shape] : 0;
+  *ty = powers ? kPowShapeTY[c->p.pow_shape] : 0;
+  return MB4_OK;
+}
 
 // ---- single contexts: a batch of one -------------------------------------
 

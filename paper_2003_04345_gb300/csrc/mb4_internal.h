@@ -42,6 +42,7 @@ struct StepParams {
   int s;                   // Krylov subspace dimension
   int gram_blocks;         // Gram blocks per (instance, system)
   int use_powers;          // FP32 basis: one tiled matrix-powers launch instead of s stencil launches
+  int pow_shape;           // its tile shape (kPowShapeTX/TY index; the tuner's choice, 0 = 32 x 16)
   int pdl;                 // programmatic dependent launch inside the Newton loop
   int precond;             // spectral preconditioning of the shifted solves (mb4_precond.cu)
   // radices of the preconditioner's FFTs along x and y (product nx, ny; none for 1)

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
   matvec_site<TK, KM>(p, jc, v, a_in, ic[b], b, k);
 }
 
-template <int SK>
+template <int SK, int TX, int TY>
 __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const float4* __restrict__ jc,
                                                         float2* __restrict__ v, const InstConst* __restrict__ ic,
                                                         const InstStatus* is) {
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   const int b = blockIdx.y;
   if (!is[b].active) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  powers_tile<SK>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
+  powers_tile<SK, TX, TY>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
 }
 
 template <typename TK, int SK, int CL>
@@ -179,23 +179,47 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   gram_lsq_solve<SK>(p, part, coef, ic, is, inst, i, nb);
 }
 
+template <int SK, int SH>
+void launch_powers_shape(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
+  constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
+  dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), p.B);
+  launch_k(p.pdl != 0, k_powers<SK, TX, TY>, grid, dim3(kPowThreads), pow_smem_bytes<SK, TX, TY>(), s, p,
+           (const float4*)b.jc, (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is);
+}
+
 template <int SK>
 void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
-  dim3 grid(((p.nx + kPowTX - 1) / kPowTX) * ((p.ny + kPowTY - 1) / kPowTY), p.B);
-  launch_k(p.pdl != 0, k_powers<SK>, grid, dim3(kPowThreads), pow_smem_bytes<SK>(), s, p, (const float4*)b.jc,
-           (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is);
+  if constexpr (SK <= kPowShapeMaxS) {
+    switch (p.pow_shape) {
+      case 1: launch_powers_shape<SK, 1>(p, b, s); return;
+      case 2: launch_powers_shape<SK, 2>(p, b, s); return;
+      case 3: launch_powers_shape<SK, 3>(p, b, s); return;
+      default: break;
+    }
+  }
+  launch_powers_shape<SK, 0>(p, b, s);
 }
 
 // Opt the matrix-powers kernels into more than 48 KB of dynamic shared memory.
+template <int SK, int SH>
+bool powers_attr() {
+  constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
+  return cudaFuncSetAttribute(k_powers<SK, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pow_smem_bytes<SK, TX, TY>()) == cudaSuccess;
+}
+template <int SK>
+bool powers_attrs() {
+  if constexpr (SK <= kPowShapeMaxS)
+    return powers_attr<SK, 0>() && powers_attr<SK, 1>() && powers_attr<SK, 2>() && powers_attr<SK, 3>();
+  else
+    return powers_attr<SK, 0>();
+}
+
 int prepare_powers() {
-#define MB4_ATTR(N)                                                                               \
-  if (cudaFuncSetAttribute(k_powers<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                           (int)pow_smem_bytes<N>()) != cudaSuccess)                              \
-    return MB4_ERR_CUDA;
-  MB4_ATTR(1) MB4_ATTR(2) MB4_ATTR(3) MB4_ATTR(4) MB4_ATTR(5) MB4_ATTR(6) MB4_ATTR(7) MB4_ATTR(8) MB4_ATTR(9)
-  MB4_ATTR(10)
-#undef MB4_ATTR
-  return MB4_OK;
+  const bool ok = powers_attrs<1>() && powers_attrs<2>() && powers_attrs<3>() && powers_attrs<4>() &&
+                  powers_attrs<5>() && powers_attrs<6>() && powers_attrs<7>() && powers_attrs<8>() &&
+                  powers_attrs<9>() && powers_attrs<10>();
+  return ok ? MB4_OK : MB4_ERR_CUDA;
 }
 
 #define MB4_SWITCH_S(CALL)        \

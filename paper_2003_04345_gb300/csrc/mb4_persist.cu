@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_step_persistent(StepPara
       for (int item = blockIdx.x; item < B * tiles; item += gridDim.x) {
         const int b = item / tiles;
         if (!is[b].active) continue;
-        powers_tile<SK>(p, (const float4*)d.jc, (float2*)d.v, d.ic[b], b, item - b * tiles, smem_raw);
+        powers_tile<SK, kPowTX, kPowTY>(p, (const float4*)d.jc, (float2*)d.v, d.ic[b], b, item - b * tiles, smem_raw);
       }
       if (!grid_barrier(d.bar, bc, is, B, lim, NoTail())) return;
     } else {

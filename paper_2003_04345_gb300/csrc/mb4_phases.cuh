@@ -262,34 +262,44 @@ __device__ __forceinline__ void matvec_site(const StepParams& p, const JCoef<TK>
 // ty0 + 8 iy) at every level, so their J coefficients stay in registers and
 // shared memory holds only the two level buffers: 4 blocks per SM at SK = 4,
 // which puts a 512 x 512 grid's 512 tiles in one wave.
-constexpr int kPowTX = 32, kPowTY = 16, kPowThreads = 256;
+constexpr int kPowTX = 32, kPowTY = 16, kPowThreads = 256;   // the default tile (shape 0)
 
-template <int SK>
-__host__ __device__ constexpr int pow_ext_x() { return kPowTX + 2 * SK; }
-template <int SK>
-__host__ __device__ constexpr int pow_ext_y() { return kPowTY + 2 * SK; }
-template <int SK>
+template <int SK, int TX = kPowTX>
+__host__ __device__ constexpr int pow_ext_x() { return TX + 2 * SK; }
+template <int SK, int TY = kPowTY>
+__host__ __device__ constexpr int pow_ext_y() { return TY + 2 * SK; }
+template <int SK, int TX = kPowTX, int TY = kPowTY>
 constexpr size_t pow_smem_bytes() {
-  return (size_t)pow_ext_x<SK>() * pow_ext_y<SK>() * (2 * 3 * sizeof(float2));
+  return (size_t)pow_ext_x<SK, TX>() * pow_ext_y<SK, TY>() * (2 * 3 * sizeof(float2));
 }
+
+// Tile shapes the launch-shape tuner chooses among (TX a multiple of 32): the results do
+// not depend on the shape -- every tile computes each level at each site it holds with
+// the same arithmetic from the same neighbours -- only the halo overhead, the shared
+// memory per block and so the blocks per SM do.
+constexpr int kPowShapes = 4;
+constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32};
+constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8};
+constexpr int kPowShapeMaxS = 6;   // larger s: the default tile only
 
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
-template <int SK>
+template <int SK, int TX = kPowTX, int TY = kPowTY>
 __device__ __forceinline__ void powers_tile(const StepParams& p, const float4* __restrict__ jc,
                                             float2* __restrict__ v, const InstConst& C, int b, int tile,
                                             unsigned char* smem_raw) {
-  constexpr int EX = pow_ext_x<SK>(), EY = pow_ext_y<SK>(), EA = EX * EY;
+  static_assert(TX % 32 == 0, "tile width is a multiple of the warp");
+  constexpr int EX = pow_ext_x<SK, TX>(), EY = pow_ext_y<SK, TY>(), EA = EX * EY;
   constexpr int NCX = (EX + 31) / 32, NCY = (EY + 7) / 8;      // positions per thread
   float2* buf0 = reinterpret_cast<float2*>(smem_raw);     // [3][EA]
   float2* buf1 = buf0 + 3 * EA;                           // [3][EA]
   const int S = p.S, nx = p.nx, ny = p.ny;
-  const int tiles_x = (nx + kPowTX - 1) / kPowTX;
+  const int tiles_x = (nx + TX - 1) / TX;
   const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
-  const int x0 = txi * kPowTX - SK, y0 = tyi * kPowTY - SK;
+  const int x0 = txi * TX - SK, y0 = tyi * TY - SK;
   const float4* jb = jc + plane(b, S);
   const int tx0 = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // 32 x 8 thread layout
   float4 jr[NCY][NCX];
@@ -336,14 +346,16 @@ __device__ __forceinline__ void powers_tile(const StepParams& p, const float4* _
     }
     __syncthreads();
     // interior of level a to global
-    for (int ly = ty0; ly < kPowTY; ly += kPowThreads / 32) {
-      const int lx = tx0;
-      const int gx = txi * kPowTX + lx, gy = tyi * kPowTY + ly;
-      if (gx < nx && gy < ny) {
-        const int c = (ly + SK) * EX + (lx + SK);
-        const size_t g = (size_t)gy * nx + gx;
+    for (int ly = ty0; ly < TY; ly += kPowThreads / 32) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) v[level(b, a, i, SK, S) + g] = dst[i * EA + c];
+      for (int lx = tx0; lx < TX; lx += 32) {
+        const int gx = txi * TX + lx, gy = tyi * TY + ly;
+        if (gx < nx && gy < ny) {
+          const int c = (ly + SK) * EX + (lx + SK);
+          const size_t g = (size_t)gy * nx + gx;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) v[level(b, a, i, SK, S) + g] = dst[i * EA + c];
+        }
       }
     }
     float2* tmp = src;

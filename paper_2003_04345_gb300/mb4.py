@@ -41,7 +41,7 @@ EXPORTS = ("mb4_default_options", "mb4_create", "mb4_create_sparse", "mb4_destro
            "mb4_batch_create", "mb4_batch_destroy", "mb4_batch_set_state", "mb4_batch_get_state", "mb4_batch_load",
            "mb4_batch_enable", "mb4_batch_step_async", "mb4_batch_wait", "mb4_batch_step", "mb4_batch_observables",
            "mb4_batch_clear_errors", "mb4_batch_get_launch_shape", "mb4_batch_set_chi_field", "mb4_batch_bytes",
-           "mb4_batch_step_profiled", "mb4_fp64_fma_rate", "mb4_server_create",
+           "mb4_batch_step_profiled", "mb4_fp64_fma_rate", "mb4_batch_get_tile_shape", "mb4_server_create",
            "mb4_server_destroy", "mb4_server_submit", "mb4_server_run", "mb4_server_result", "mb4_server_clock")
 
 
@@ -69,7 +69,8 @@ class Options(C.Structure):
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("newton_predict", C.c_double),
                 ("overlap_launches", C.c_int), ("newton_start", C.c_int), ("newton_start_adaptive", C.c_int),
                 ("autotune", C.c_int), ("site_threads", C.c_int), ("precondition", C.c_int),
-                ("site_chi", C.c_int), ("persistent", C.c_int), ("wait_limit", C.c_longlong)]
+                ("site_chi", C.c_int), ("persistent", C.c_int), ("powers_tile", C.c_int),
+                ("wait_limit", C.c_longlong)]
 
 
 class Stats(C.Structure):
@@ -159,6 +160,7 @@ def lib():
         L.mb4_batch_step_profiled.argtypes = [_P, C.c_int, C.POINTER(Stats), C.POINTER(C.c_int), _D,
                                               C.POINTER(C.c_longlong), _D]
         L.mb4_fp64_fma_rate.argtypes = [C.c_double, _D, _D]
+        L.mb4_batch_get_tile_shape.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.mb4_batch_clear_errors.argtypes = [_P]
         L.mb4_batch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(Options)]
         L.mb4_batch_bytes.restype = C.c_longlong
@@ -241,7 +243,7 @@ class Integrator:
     def __init__(self, nx, ny, V, chi, h, tx=1.0, ty=None, onsite=0.0, precision="fp64", **opts):
         """opts: the mb4_options fields (krylov_s, newton_rtol, newton_max, alpha1, c1, c2,
         stream, use_graph, newton_predict, overlap_launches, newton_start, newton_start_adaptive,
-        autotune, site_threads, precondition, site_chi, persistent, wait_limit)."""
+        autotune, site_threads, precondition, site_chi, persistent, powers_tile, wait_limit)."""
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.S = self.nx * self.ny
@@ -360,6 +362,12 @@ class Integrator:
         _check(lib().mb4_get_launch_shape(self._ctx, out), "mb4_get_launch_shape")
         return tuple(out)
 
+    def tile_shape(self):
+        """(tx, ty) of the FP32 matrix-powers tile in use, (0, 0) where it is not used."""
+        tx, ty = C.c_int(), C.c_int()
+        _check(lib().mb4_batch_get_tile_shape(self._ctx, C.byref(tx), C.byref(ty)), "mb4_batch_get_tile_shape")
+        return tx.value, ty.value
+
     def step_async(self, nsteps=1):
         """Queue nsteps steps on the stream without waiting (see wait)."""
         _check(lib().mb4_step_async(self._ctx, int(nsteps)), "mb4_step_async")
@@ -450,7 +458,7 @@ def observables_noalloc(nx, ny, re, im, V, out6, chi, tx=1.0, ty=None, onsite=0.
 def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alpha1=-712.5, c1=1.0 / 3.0,
              c2=2.0 / 3.0, stream=None, use_graph=True, newton_predict=0.0, overlap_launches=True,
              newton_start=None, newton_start_adaptive=None, autotune=None, site_threads=None,
-             precondition=None, site_chi=None, persistent=None, wait_limit=None):
+             precondition=None, site_chi=None, persistent=None, wait_limit=None, powers_tile=None):
     opt = Options()
     lib().mb4_default_options(C.byref(opt))
     opt.newton_rtol = float(newton_rtol)
@@ -479,6 +487,8 @@ def _options(precision="fp64", krylov_s=0, newton_rtol=1e-13, newton_max=30, alp
         opt.persistent = int(persistent)
     if wait_limit is not None:
         opt.wait_limit = int(wait_limit)
+    if powers_tile is not None:
+        opt.powers_tile = int(powers_tile)
     if stream is not None:
         opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return opt
@@ -599,6 +609,12 @@ class Batch:
         out = (C.c_int * 8)()
         _check(lib().mb4_batch_get_launch_shape(self._ctx, out), "mb4_batch_get_launch_shape")
         return tuple(out)
+
+    def tile_shape(self):
+        """(tx, ty) of the FP32 matrix-powers tile in use, (0, 0) where it is not used."""
+        tx, ty = C.c_int(), C.c_int()
+        _check(lib().mb4_batch_get_tile_shape(self._ctx, C.byref(tx), C.byref(ty)), "mb4_batch_get_tile_shape")
+        return tx.value, ty.value
 
 
 class Server:
