@@ -128,8 +128,8 @@ typedef struct {
     int    autotune;     /* 1 (default): at create, time the one-site-per-thread kernels
                             (residual, Krylov basis, update; set-up and accept follow the
                             residual) with 64, 128 and 256 threads per block, and in mixed
-                            mode the matrix-powers kernel with tiles of 32 x 16, 32 x 32,
-                            64 x 16 and 32 x 8 sites, on the context's own buffers, and keep
+                            mode the matrix-powers kernel with each tile of option
+                            powers_tile, on the context's own buffers, and keep
                             the fastest (the default unless another is faster by more than
                             5%); the choice is cached per device, precision, grid, batch size
                             and s.  Every choice gives the same results bit for bit.  0: 128
@@ -160,8 +160,10 @@ typedef struct {
                             MB4_ERR_INVALID_ARG at create.                                     */
     int    powers_tile;  /* mixed mode, matrix-powers basis: 0 (default) = the tuner's choice
                             (32 x 16 when autotune = 0); 1, 2, 3, 4 = a tile of 32 x 16,
-                            32 x 32, 64 x 16 or 32 x 8 sites (krylov_s <= 6 for 2..4).  Every
-                            tile gives the same basis bit for bit.                            */
+                            32 x 32, 64 x 16 or 32 x 8 sites; 5, 6 = 32 x 16 or 64 x 16 with
+                            each warp's band of rows kept in registers (fewer shared-memory
+                            reads); 2..6 need krylov_s <= 6.  Every tile gives the same basis
+                            bit for bit.                                                      */
     long long wait_limit; /* persistent = 1: polls (each followed by a short sleep) that a
                             grid-barrier wait makes before it gives up; the step then fails
                             with MB4_ERR_TIMEOUT and the state stays at the last accepted step.

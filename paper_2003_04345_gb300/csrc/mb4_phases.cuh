@@ -277,9 +277,10 @@ constexpr size_t pow_smem_bytes() {
 // not depend on the shape -- every tile computes each level at each site it holds with
 // the same arithmetic from the same neighbours -- only the halo overhead, the shared
 // memory per block and so the blocks per SM do.
-constexpr int kPowShapes = 4;
-constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32};
-constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8};
+constexpr int kPowShapes = 6;       // shapes 4 and 5 keep each warp's rows in registers
+constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64};
+constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16};
+constexpr bool kPowShapeRows[kPowShapes] = {false, false, false, false, true, true};
 constexpr int kPowShapeMaxS = 6;   // larger s: the default tile only
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -363,6 +364,102 @@ __device__ __forceinline__ void powers_tile(const StepParams& p, const float4* _
     dst = tmp;
   }
   __syncthreads();                               // the caller may reuse shared memory for the next tile
+}
+
+// The same tile with each warp owning a band of NR consecutive rows (lane = column):
+// a thread keeps its own positions' values of the previous level in registers, so the
+// centre and the y neighbours inside its band need no shared-memory read; only the x
+// neighbours (other lanes) and the rows just outside the band come from shared memory.
+// Same arithmetic on the same values as powers_tile, so the same basis bit for bit.
+template <int SK, int TX, int TY>
+__device__ __forceinline__ void powers_tile_rows(const StepParams& p, const float4* __restrict__ jc,
+                                                 float2* __restrict__ v, const InstConst& C, int b, int tile,
+                                                 unsigned char* smem_raw) {
+  static_assert(TX % 32 == 0, "tile width is a multiple of the warp");
+  constexpr int EX = pow_ext_x<SK, TX>(), EY = pow_ext_y<SK, TY>(), EA = EX * EY;
+  constexpr int NCX = (EX + 31) / 32, NR = (EY + 7) / 8;       // columns and rows per thread
+  float2* buf0 = reinterpret_cast<float2*>(smem_raw);     // [3][EA]
+  float2* buf1 = buf0 + 3 * EA;                           // [3][EA]
+  const int S = p.S, nx = p.nx, ny = p.ny;
+  const int tiles_x = (nx + TX - 1) / TX;
+  const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+  const int x0 = txi * TX - SK, y0 = tyi * TY - SK;
+  const float4* jb = jc + plane(b, S);
+  const int tx0 = threadIdx.x & 31, ly0 = (threadIdx.x >> 5) * NR;   // lane = column, warp = band of rows
+  float4 jr[NR][NCX];
+  float2 own[NR][NCX][3];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int ly = ly0 + r;
+#pragma unroll
+    for (int ix = 0; ix < NCX; ++ix) {
+      const int lx = tx0 + 32 * ix;
+      if (ly < EY && lx < EX) {
+        const int t = ly * EX + lx;
+        const int g = wrap(y0 + ly, ny) * nx + wrap(x0 + lx, nx);
+        jr[r][ix] = jb[g];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          own[r][ix][i] = v[level(b, 0, i, SK, S) + g];
+          buf0[i * EA + t] = own[r][ix][i];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const float tx = C.f_txt, ty = C.f_tyt;
+  float2* src = buf0;
+  float2* dst = buf1;
+#pragma unroll 1
+  for (int a = 1; a <= SK; ++a) {
+    float2 above[NCX][3];                        // the previous row's level a-1 values
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int ly = ly0 + r;
+#pragma unroll
+      for (int ix = 0; ix < NCX; ++ix) {
+        const int lx = tx0 + 32 * ix;
+        const bool live = !(ly < a || ly >= EY - a || lx < a || lx >= EX - a);   // the tile grown by SK - a
+        const int c = ly * EX + lx;
+        const float4 j = jr[r][ix];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float2 cc = own[r][ix][i];
+          if (live) {
+            const float2* P = src + i * EA;
+            const float2 xa = P[c - 1], xb = P[c + 1];
+            const float2 ya = (r > 0) ? above[ix][i] : P[c - EX];
+            const float2 yb = (r < NR - 1) ? own[r + 1][ix][i] : P[c + EX];
+            float2 o;
+            o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(j.x, cc.y, mul_(j.z, cc.x))));
+            o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-j.z, cc.y, mul_(-j.y, cc.x))));
+            dst[i * EA + c] = o;
+            own[r][ix][i] = o;
+          }
+          above[ix][i] = cc;
+        }
+      }
+    }
+    // interior of level a to global, from the registers
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int ly = ly0 + r - SK;
+#pragma unroll
+      for (int ix = 0; ix < NCX; ++ix) {
+        const int lx = tx0 + 32 * ix - SK;
+        const int gx = txi * TX + lx, gy = tyi * TY + ly;
+        if (ly >= 0 && ly < TY && lx >= 0 && lx < TX && gx < nx && gy < ny) {
+          const size_t g = (size_t)gy * nx + gx;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) v[level(b, a, i, SK, S) + g] = own[r][ix][i];
+        }
+      }
+    }
+    __syncthreads();
+    float2* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
 }
 
 // Gram accumulators.  FP32 mode: products and per-thread sums in FP32, a
