@@ -591,8 +591,8 @@ int make_batch(mb4_batch* c, const mb4_grid* grid, int B, const double* V, const
     p.ell_deg = ell->deg;
     p.ell_cplx = ell->cplx ? 1 : 0;
   }
-  p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B)
-                                              : gram_blocks_per_system<double>(p.s, B);
+  p.gram_blocks = (o.precision == MB4_MIXED) ? gram_blocks_per_system<float>(p.s, B, p.S)
+                                              : gram_blocks_per_system<double>(p.s, B, p.S);
   if (p.gram_blocks < 1) return MB4_ERR_CUDA;
   if (p.precond && (grid->nx > MB4_MAX_PRECOND_SIDE || grid->ny > MB4_MAX_PRECOND_SIDE)) return MB4_ERR_INVALID_ARG;
   if (p.precond) {

@@ -190,7 +190,7 @@ template <typename TK> void launch_gram(const StepParams& p, const DevBuffers& b
 // Raise the dynamic shared-memory limit of the matrix-powers kernels (once per process/device).
 int prepare_powers();
 // Blocks per (instance, system) that make the Gram kernel about one wave (0 on error).
-template <typename TK> int gram_blocks_per_system(int s_dim, int B);
+template <typename TK> int gram_blocks_per_system(int s_dim, int B, int S);
 // Newton update and loop test; cond_handle drives the graph's WHILE node when use_cond.
 template <typename TK> void launch_update(const StepParams& p, const DevBuffers& b, unsigned long long cond_handle,
                                           int use_cond, cudaStream_t st);

@@ -293,9 +293,11 @@ void launch_gram(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 #undef MB4_CALL
 }
 
-// Blocks per (instance, system) that keep the Gram kernel about one wave deep.
+// Blocks per (instance, system) that keep the Gram kernel about one wave deep, and no
+// more than one per 1024 sites: on a small grid more blocks only add partial sums for the
+// last block's fixed-order reduction to read.
 template <typename TK>
-int gram_blocks_per_system(int s_dim, int B) {
+int gram_blocks_per_system(int s_dim, int B, int S) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -313,11 +315,13 @@ int gram_blocks_per_system(int s_dim, int B) {
   if (sizeof(TK) == sizeof(double)) occ = 1;
   long long nb = (long long)sms * occ / (3LL * (B > 0 ? B : 1));
   if (nb > kGramCap) nb = kGramCap;   // more blocks only lengthen the last block's reduction
+  const long long by_sites = ((long long)S + 1023) / 1024;
+  if (nb > by_sites) nb = by_sites;
   if (sizeof(TK) == sizeof(float) && nb >= kGramCluster) nb -= nb % kGramCluster;   // whole clusters
   return nb < 1 ? 1 : (int)nb;
 }
-template int gram_blocks_per_system<float>(int, int);
-template int gram_blocks_per_system<double>(int, int);
+template int gram_blocks_per_system<float>(int, int, int);
+template int gram_blocks_per_system<double>(int, int, int);
 
 template <typename TK>
 void launch_krylov(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
