@@ -162,8 +162,9 @@ typedef struct {
                             (32 x 16 when autotune = 0); 1, 2, 3, 4 = a tile of 32 x 16,
                             32 x 32, 64 x 16 or 32 x 8 sites; 5, 6 = 32 x 16 or 64 x 16 with
                             each warp's band of rows kept in registers (fewer shared-memory
-                            reads); 2..6 need krylov_s <= 6.  Every tile gives the same basis
-                            bit for bit.                                                      */
+                            reads); 7, 8 = 32 x 16 or 64 x 16 building the three systems one
+                            after the other (a third of the shared memory per block); 2..8
+                            need krylov_s <= 6.  Every tile gives the same basis bit for bit. */
     long long wait_limit; /* persistent = 1: polls (each followed by a short sleep) that a
                             grid-barrier wait makes before it gives up; the step then fails
                             with MB4_ERR_TIMEOUT and the state stays at the last accepted step.

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const 
   matvec_site<TK, KM>(p, jc, v, a_in, ic[b], b, k);
 }
 
-template <int SK, int TX, int TY, bool ROWS>
+template <int SK, int TX, int TY, int FORM>
 __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const float4* __restrict__ jc,
                                                         float2* __restrict__ v, const InstConst* __restrict__ ic,
                                                         const InstStatus* is) {
@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   const int b = blockIdx.y;
   if (!is[b].active) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if constexpr (ROWS) powers_tile_rows<SK, TX, TY>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
+  if constexpr (FORM == 1) powers_tile_rows<SK, TX, TY>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
+  else if constexpr (FORM == 2) powers_tile_sys<SK, TX, TY>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
   else powers_tile<SK, TX, TY>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
 }
 
@@ -184,7 +185,8 @@ template <int SK, int SH>
 void launch_powers_shape(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
   dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), p.B);
-  launch_k(p.pdl != 0, k_powers<SK, TX, TY, kPowShapeRows[SH]>, grid, dim3(kPowThreads), pow_smem_bytes<SK, TX, TY>(),
+  constexpr int F = kPowShapeForm[SH];
+  launch_k(p.pdl != 0, k_powers<SK, TX, TY, F>, grid, dim3(kPowThreads), pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>(),
            s, p, (const float4*)b.jc, (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is);
 }
 
@@ -197,6 +199,8 @@ void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
       case 3: launch_powers_shape<SK, 3>(p, b, s); return;
       case 4: launch_powers_shape<SK, 4>(p, b, s); return;
       case 5: launch_powers_shape<SK, 5>(p, b, s); return;
+      case 6: launch_powers_shape<SK, 6>(p, b, s); return;
+      case 7: launch_powers_shape<SK, 7>(p, b, s); return;
       default: break;
     }
   }
@@ -207,14 +211,15 @@ void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
 template <int SK, int SH>
 bool powers_attr() {
   constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
-  return cudaFuncSetAttribute(k_powers<SK, TX, TY, kPowShapeRows[SH]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pow_smem_bytes<SK, TX, TY>()) == cudaSuccess;
+  constexpr int F = kPowShapeForm[SH];
+  return cudaFuncSetAttribute(k_powers<SK, TX, TY, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>()) == cudaSuccess;
 }
 template <int SK>
 bool powers_attrs() {
   if constexpr (SK <= kPowShapeMaxS)
     return powers_attr<SK, 0>() && powers_attr<SK, 1>() && powers_attr<SK, 2>() && powers_attr<SK, 3>() &&
-           powers_attr<SK, 4>() && powers_attr<SK, 5>();
+           powers_attr<SK, 4>() && powers_attr<SK, 5>() && powers_attr<SK, 6>() && powers_attr<SK, 7>();
   else
     return powers_attr<SK, 0>();
 }

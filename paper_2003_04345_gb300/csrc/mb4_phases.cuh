@@ -268,19 +268,19 @@ template <int SK, int TX = kPowTX>
 __host__ __device__ constexpr int pow_ext_x() { return TX + 2 * SK; }
 template <int SK, int TY = kPowTY>
 __host__ __device__ constexpr int pow_ext_y() { return TY + 2 * SK; }
-template <int SK, int TX = kPowTX, int TY = kPowTY>
+template <int SK, int TX = kPowTX, int TY = kPowTY, int NSYS = 3>
 constexpr size_t pow_smem_bytes() {
-  return (size_t)pow_ext_x<SK, TX>() * pow_ext_y<SK, TY>() * (2 * 3 * sizeof(float2));
+  return (size_t)pow_ext_x<SK, TX>() * pow_ext_y<SK, TY>() * (2 * NSYS * sizeof(float2));
 }
 
 // Tile shapes the launch-shape tuner chooses among (TX a multiple of 32): the results do
 // not depend on the shape -- every tile computes each level at each site it holds with
 // the same arithmetic from the same neighbours -- only the halo overhead, the shared
 // memory per block and so the blocks per SM do.
-constexpr int kPowShapes = 6;       // shapes 4 and 5 keep each warp's rows in registers
-constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64};
-constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16};
-constexpr bool kPowShapeRows[kPowShapes] = {false, false, false, false, true, true};
+constexpr int kPowShapes = 8;       // 4, 5: warps keep their rows in registers; 6, 7: one system at a time
+constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64, 32, 64};
+constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16, 16, 16};
+constexpr int kPowShapeForm[kPowShapes] = {0, 0, 0, 0, 1, 1, 2, 2};   // 0 tile, 1 rows, 2 by system
 constexpr int kPowShapeMaxS = 6;   // larger s: the default tile only
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -364,6 +364,80 @@ __device__ __forceinline__ void powers_tile(const StepParams& p, const float4* _
     dst = tmp;
   }
   __syncthreads();                               // the caller may reuse shared memory for the next tile
+}
+
+// The same tile with the three systems built one after the other through buffers for one
+// system: a third of the shared memory per block, so more blocks fit an SM (the kernel is
+// bound by shared-memory latency, not by its arithmetic).  Same arithmetic, same basis.
+template <int SK, int TX, int TY>
+__device__ __forceinline__ void powers_tile_sys(const StepParams& p, const float4* __restrict__ jc,
+                                                float2* __restrict__ v, const InstConst& C, int b, int tile,
+                                                unsigned char* smem_raw) {
+  static_assert(TX % 32 == 0, "tile width is a multiple of the warp");
+  constexpr int EX = pow_ext_x<SK, TX>(), EY = pow_ext_y<SK, TY>(), EA = EX * EY;
+  constexpr int NCX = (EX + 31) / 32, NCY = (EY + 7) / 8;      // positions per thread
+  float2* buf0 = reinterpret_cast<float2*>(smem_raw);     // [EA]
+  float2* buf1 = buf0 + EA;                               // [EA]
+  const int S = p.S, nx = p.nx, ny = p.ny;
+  const int tiles_x = (nx + TX - 1) / TX;
+  const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+  const int x0 = txi * TX - SK, y0 = tyi * TY - SK;
+  const float4* jb = jc + plane(b, S);
+  const int tx0 = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // 32 x 8 thread layout
+  const float tx = C.f_txt, ty = C.f_tyt;
+  float4 jr[NCY][NCX];
+#pragma unroll
+  for (int iy = 0; iy < NCY; ++iy)
+#pragma unroll
+    for (int ix = 0; ix < NCX; ++ix) {
+      const int ly = ty0 + 8 * iy, lx = tx0 + 32 * ix;
+      if (ly < EY && lx < EX) jr[iy][ix] = jb[wrap(y0 + ly, ny) * nx + wrap(x0 + lx, nx)];
+    }
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int iy = 0; iy < NCY; ++iy)
+#pragma unroll
+      for (int ix = 0; ix < NCX; ++ix) {
+        const int ly = ty0 + 8 * iy, lx = tx0 + 32 * ix;
+        if (ly < EY && lx < EX)
+          buf0[ly * EX + lx] = v[level(b, 0, i, SK, S) + wrap(y0 + ly, ny) * nx + wrap(x0 + lx, nx)];
+      }
+    __syncthreads();
+    float2* src = buf0;
+    float2* dst = buf1;
+#pragma unroll 1
+    for (int a = 1; a <= SK; ++a) {
+#pragma unroll
+      for (int iy = 0; iy < NCY; ++iy) {
+        const int ly = ty0 + 8 * iy;
+#pragma unroll
+        for (int ix = 0; ix < NCX; ++ix) {
+          const int lx = tx0 + 32 * ix;
+          if (ly < a || ly >= EY - a || lx < a || lx >= EX - a) continue;   // the tile grown by SK - a
+          const int c = ly * EX + lx;
+          const float4 j = jr[iy][ix];
+          const float2 cc = src[c], xa = src[c - 1], xb = src[c + 1], ya = src[c - EX], yb = src[c + EX];
+          float2 o;
+          o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(j.x, cc.y, mul_(j.z, cc.x))));
+          o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-j.z, cc.y, mul_(-j.y, cc.x))));
+          dst[c] = o;
+        }
+      }
+      __syncthreads();
+      for (int ly = ty0; ly < TY; ly += kPowThreads / 32) {
+#pragma unroll
+        for (int lx = tx0; lx < TX; lx += 32) {
+          const int gx = txi * TX + lx, gy = tyi * TY + ly;
+          if (gx < nx && gy < ny) v[level(b, a, i, SK, S) + (size_t)gy * nx + gx] = dst[(ly + SK) * EX + (lx + SK)];
+        }
+      }
+      float2* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    __syncthreads();                             // before the next system overwrites the buffers
+  }
 }
 
 // The same tile with each warp owning a band of NR consecutive rows (lane = column):

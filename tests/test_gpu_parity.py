@@ -747,14 +747,14 @@ def test_general_kinetic_matrix_rejects_bad_input(mb4):
         assert rc == mb4.MB4_ERR_INVALID_ARG and not ctx.value
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_matrix_powers_tiles_give_the_same_steps(mb4, tile):
     """Every matrix-powers tile shape the tuner chooses among (32x16, 32x32, 64x16, 32x8)
     builds the same FP32 Krylov basis bit for bit, so the mixed step is the same: a grid
     whose sides are not multiples of any tile (ragged tiles at both edges)."""
     w = inputs.Workload("ragged", 100, 70, h=0.005, steps=10, chi=1.0, W=1.0, defect_fraction=0.01, sigma=5.0)
     with mb4.from_workload(w, precision="mixed", powers_tile=tile) as it:
-        assert it.tile_shape() == [(32, 16), (32, 32), (64, 16), (32, 8), (32, 16), (64, 16)][tile - 1]
+        assert it.tile_shape() == [(32, 16), (32, 32), (64, 16), (32, 8), (32, 16), (64, 16), (32, 16), (64, 16)][tile - 1]
         it.step(10)
         got = it.get_state()
     with mb4.from_workload(w, precision="mixed", powers_tile=1) as it:
