@@ -113,13 +113,19 @@ template <typename TK, int KM>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_matvec(StepParams p, const JCoef<TK>* __restrict__ jc,
                                                 typename Vec2<TK>::type* __restrict__ v, int a_in,
                                                 const InstConst* __restrict__ ic, const InstStatus* is) {
+  // Before the wait for the predecessor: the status and the J coefficients, which this step's
+  // set-up wrote and no kernel after it changes (the predecessor of a basis launch is a
+  // residual or a basis launch, and both start only after the set-up and the last loop test
+  // have completed).
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool go = is[b].active && k < p.S;
+  JCoef<TK> j;
+  if (go) j = jc[plane(b, p.S) + k];
   pdl_wait();
   pdl_launch_dependents();
-  const int b = blockIdx.y;
-  if (!is[b].active) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= p.S) return;
-  matvec_site<TK, KM>(p, jc, v, a_in, ic[b], b, k);
+  if (!go) return;
+  matvec_site_j<TK, KM>(p, j, v, a_in, ic[b], b, k);
 }
 
 template <int SK, int TX, int TY, int FORM>
@@ -339,21 +345,26 @@ template <typename TK, int SK>
 __global__ void __launch_bounds__(kSiteThreadsMax) k_update(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                 const double* __restrict__ coef, double2* __restrict__ Ubar,
                                                 InstStatus* is) {
-  pdl_wait();
-  pdl_launch_dependents();
+  // Before the wait for the predecessor: the status and the increments dU, which the last
+  // update (or this step's set-up) wrote before the residual of this iteration started.
   const int inst = blockIdx.y;
   InstStatus& I = is[inst];
-  if (!I.active) return;
+  const bool active = I.active;
+  const bool first = I.newton_iter == 0 && !I.predicted;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double2 Uold[3];
+  if (active && k < p.S) load_increments(Ubar, first, inst, p.S, k, Uold);
+  pdl_wait();
+  pdl_launch_dependents();
+  if (!active) return;
   __shared__ TK cs[3][SK];
   if (threadIdx.x < 3 * SK)
     cs[threadIdx.x / SK][threadIdx.x % SK] =
         (TK)coef[((size_t)inst * 3 + threadIdx.x / SK) * kMaxS + threadIdx.x % SK];
-  const bool first = I.newton_iter == 0 && !I.predicted;
   __syncthreads();
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   float m = 0.f;
   int bad = 0;
-  if (k < p.S) update_site<TK, SK>(p, v, cs, Ubar, first, inst, k, m, bad);
+  if (k < p.S) update_site_u<TK, SK>(p, v, cs, Uold, Ubar, first, inst, k, m, bad);
   block_update_flags(m, bad, I);
 }
 

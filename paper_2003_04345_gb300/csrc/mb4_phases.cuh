@@ -209,12 +209,11 @@ __device__ __forceinline__ void residual_site(const StepParams& p, const double2
 // (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
 // ---------------------------------------------------------------------------
 template <typename TK, int KM>
-__device__ __forceinline__ void matvec_site(const StepParams& p, const JCoef<TK>* __restrict__ jc,
-                                            typename Vec2<TK>::type* __restrict__ v, int a_in, const InstConst& C,
-                                            int b, int k) {
+__device__ __forceinline__ void matvec_site_j(const StepParams& p, const JCoef<TK> j,
+                                              typename Vec2<TK>::type* __restrict__ v, int a_in, const InstConst& C,
+                                              int b, int k) {
   typedef typename Vec2<TK>::type TK2;
   const int S = p.S;
-  const JCoef<TK> j = jc[plane(b, S) + k];
   if constexpr (KM >= 2) {
     // (J x)_re = a xp + e1 xq + Im(sum_j (K_kj / theta) x_j), (J x)_im = -e2 xp - a xq - Re(sum_j ..):
     // with s = sum_j K_kj x_j / theta (a complex product when K is complex), the kinetic
@@ -252,6 +251,15 @@ __device__ __forceinline__ void matvec_site(const StepParams& p, const JCoef<TK>
   }
 }
 
+
+// The same with the J coefficients read here (the persistent step; the launch-per-phase
+// kernel reads them before it waits for its predecessor).
+template <typename TK, int KM>
+__device__ __forceinline__ void matvec_site(const StepParams& p, const JCoef<TK>* __restrict__ jc,
+                                            typename Vec2<TK>::type* __restrict__ v, int a_in, const InstConst& C,
+                                            int b, int k) {
+  matvec_site_j<TK, KM>(p, jc[plane(b, p.S) + k], v, a_in, C, b, k);
+}
 
 // Matrix powers on a tile (FP32 Krylov basis): one block builds v_1..v_SK on a
 // TX x TY tile from v_0 and the J coefficients loaded once, with an SK-wide
@@ -772,9 +780,10 @@ __device__ void gram_lsq_solve(const StepParams& p, const double* __restrict__ p
 // the blocks with an atomic max; NaN/Inf flagged.  No block waits for another: the loop
 // test runs in k_newton_test once the whole grid has finished.  Grid: (sites / bs_update, B).
 template <typename TK, int SK>
-__device__ __forceinline__ void update_site(const StepParams& p, const typename Vec2<TK>::type* __restrict__ v,
-                                            const TK (&cs)[3][SK], double2* __restrict__ Ubar, bool first,
-                                            int inst, int k, float& m, int& bad) {
+__device__ __forceinline__ void update_site_u(const StepParams& p, const typename Vec2<TK>::type* __restrict__ v,
+                                              const TK (&cs)[3][SK], const double2 (&Uold)[3],
+                                              double2* __restrict__ Ubar, bool first, int inst, int k, float& m,
+                                              int& bad) {
   typedef typename Vec2<TK>::type TK2;
   const int S = p.S;
   TK2 x[3];
@@ -797,7 +806,7 @@ __device__ __forceinline__ void update_site(const StepParams& p, const typename 
       U.x = to_double(x[i].x);
       U.y = to_double(x[i].y);
     } else {
-      U = Ubar[stage(inst, i, S) + k];
+      U = Uold[i];
       U.x += to_double(x[i].x);
       U.y += to_double(x[i].y);
     }
@@ -815,6 +824,22 @@ __device__ __forceinline__ void update_site(const StepParams& p, const typename 
     bad |= !(isfinite(rx) && isfinite(ry));
     m = fmaxf(m, fmaxf(fabsf(rx), fabsf(ry)));
   }
+}
+
+// dU of the site before the update (unread on the first iteration, which writes dU).
+__device__ __forceinline__ void load_increments(const double2* __restrict__ Ubar, bool first, int inst, int S, int k,
+                                                double2 (&Uold)[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Uold[i] = first ? make_double2(0.0, 0.0) : Ubar[stage(inst, i, S) + k];
+}
+
+template <typename TK, int SK>
+__device__ __forceinline__ void update_site(const StepParams& p, const typename Vec2<TK>::type* __restrict__ v,
+                                            const TK (&cs)[3][SK], double2* __restrict__ Ubar, bool first,
+                                            int inst, int k, float& m, int& bad) {
+  double2 Uold[3];
+  load_increments(Ubar, first, inst, p.S, k, Uold);
+  update_site_u<TK, SK>(p, v, cs, Uold, Ubar, first, inst, k, m, bad);
 }
 
 // Merges the block's largest |r| and non-finite flag into instance I (one atomic each).
