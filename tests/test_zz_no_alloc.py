@@ -5,7 +5,8 @@ or where cudaMalloc and its implicit synchronisation are not allowed).
 The entry point keeps its block partial sums in a fixed array inside the
 library instead of allocating.  Through the C ABI it must give the same six
 observables as the context-based mb4_observables, call after call, although
-every call reuses the same scratch array.  This file is collected last so that
+every call reuses the same scratch array, and match the FP64 oracle's correctly rounded
+sums.  This file is collected last so that
 a run that stops at the first failure has already run every other test.
 """
 import numpy as np
@@ -61,6 +62,13 @@ def test_noalloc_matches_context_observables_twice(env, nx, ny):
         stream.synchronize()
         got = out.cpu().numpy()
         assert _close(got, want), (got, want)
+        # and against the FP64 oracle's correctly rounded sums directly
+        from oracle import mb4_oracle as orc
+        prob = orc.Problem(nx, ny, V, chi, tx=tx, ty=ty, eps0=onsite)
+        H, UK, UE, UI = orc.energy(prob, psi)
+        ref = np.array([H, UK, UE, UI, orc.norm2(psi), orc.participation(psi)])
+        scale = np.array([abs(UK) + abs(UE) + abs(UI)] * 4 + [ref[4], ref[5]])
+        assert np.all(np.abs(got - ref) <= 1e-14 * scale), (got, ref)
 
 
 def test_noalloc_allocates_nothing(env):
