@@ -128,7 +128,7 @@ typedef struct {
     int    autotune;     /* 1 (default): at create, time the one-site-per-thread kernels
                             (residual, Krylov basis, update; set-up and accept follow the
                             residual) with 64, 128 and 256 threads per block, and in mixed
-                            mode the matrix-powers kernel with each tile of option
+                            mode the matrix-powers kernel in each form of option
                             powers_tile, on the context's own buffers, and keep
                             the fastest (the default unless another is faster by more than
                             5%); the choice is cached per device, precision, grid, batch size
@@ -163,8 +163,13 @@ typedef struct {
                             32 x 32, 64 x 16 or 32 x 8 sites; 5, 6 = 32 x 16 or 64 x 16 with
                             each warp's band of rows kept in registers (fewer shared-memory
                             reads); 7, 8 = 32 x 16 or 64 x 16 building the three systems one
-                            after the other (a third of the shared memory per block); 2..8
-                            need krylov_s <= 6.  Every tile gives the same basis bit for bit. */
+                            after the other (a third of the shared memory per block); 9, 10 =
+                            one warp per tile in registers, (32 - 2 krylov_s) x 4 or x 8
+                            sites (neighbours by shuffles, no shared memory); 11, 12 = one
+                            warp walking down a strip of (32 - 2 krylov_s) x 8 or x 16 sites,
+                            three rows per level in registers; 2..12 need krylov_s <= 6;
+                            13 = no tiles: one stencil launch per level.
+                            Every form gives the same basis bit for bit.                      */
     long long wait_limit; /* persistent = 1: polls (each followed by a short sleep) that a
                             grid-barrier wait makes before it gives up; the step then fails
                             with MB4_ERR_TIMEOUT and the state stays at the last accepted step.
@@ -382,7 +387,8 @@ int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);
 
 /* The tile (*tx x *ty sites) of the FP32 matrix-powers Krylov basis that the tuner chose
  * for this batch or context (cast an mb4_ctx* to mb4_batch*: a context is a batch of one),
- * or 0 x 0 where that kernel is not used (FP64 mode, the preconditioner, a general K).
+ * or 0 x 0 where that kernel is not used (FP64 mode, the preconditioner, a general K, or a
+ * basis built by one stencil launch per level, option powers_tile = 13 or the tuner's choice).
  * Every tile gives the same basis bit for bit. */
 int mb4_batch_get_tile_shape(const mb4_batch* b, int* tx, int* ty);
 

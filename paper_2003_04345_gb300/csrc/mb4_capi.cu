@@ -104,8 +104,8 @@ int validate_options(const mb4_options* in, mb4_options* o) {
   if (o->site_chi != 0 && o->site_chi != 1) return MB4_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return MB4_ERR_INVALID_ARG;
   if (o->wait_limit < 0) return MB4_ERR_INVALID_ARG;
-  if (o->powers_tile < 0 || o->powers_tile > kPowShapes) return MB4_ERR_INVALID_ARG;
-  if (o->powers_tile > 1 && o->krylov_s > kPowShapeMaxS) return MB4_ERR_INVALID_ARG;
+  if (o->powers_tile < 0 || o->powers_tile > kPowShapes + 1) return MB4_ERR_INVALID_ARG;
+  if (o->powers_tile > 1 && o->powers_tile <= kPowShapes && o->krylov_s > kPowShapeMaxS) return MB4_ERR_INVALID_ARG;
   return MB4_OK;
 }
 
@@ -520,10 +520,10 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
   // FP32 matrix-powers tile: the default 32 x 16 unless another shape is clearly faster
   int shape = c->p.pow_shape;                    // a forced tile (option powers_tile) stays
   if (rc == MB4_OK && mixed && c->p.use_powers && c->p.s <= kPowShapeMaxS && !c->forced_tile) {
-    float t[kPowShapes];
-    for (int k = 0; k < kPowShapes && rc == MB4_OK; ++k) rc = time_site_kernel(c, 3, k, e0, e1, &t[k]);
+    float t[kPowShapes + 1];                       // the tile forms, then one launch per level
+    for (int k = 0; k <= kPowShapes && rc == MB4_OK; ++k) rc = time_site_kernel(c, 3, k, e0, e1, &t[k]);
     if (rc == MB4_OK)
-      for (int k = 1; k < kPowShapes; ++k)
+      for (int k = 1; k <= kPowShapes; ++k)
         if (t[k] < 0.95f * t[shape]) shape = k;
   }
   cudaEventDestroy(e0);
@@ -1037,8 +1037,8 @@ int mb4_get_launch_shape(const mb4_ctx* c, int* shape8) { return mb4_batch_get_l
 
 int mb4_batch_get_tile_shape(const mb4_batch* c, int* tx, int* ty) {
   if (!c || !tx || !ty) return MB4_ERR_INVALID_ARG;
-  const bool powers = c->precision == MB4_MIXED && c->p.use_powers;
-  *tx = powers ? kPowShapeTX[c->p.pow_shape] : 0;
+  const bool powers = c->precision == MB4_MIXED && c->p.use_powers && c->p.pow_shape != kPowLevels;
+  *tx = !powers ? 0 : kPowShapeForm[c->p.pow_shape] >= 3 ? 32 - 2 * c->p.s : kPowShapeTX[c->p.pow_shape];
   *ty = powers ? kPowShapeTY[c->p.pow_shape] : 0;
   return MB4_OK;
 }
@@ -1311,7 +1311,7 @@ int profiled_steps(mb4_batch* c, int nsteps, Prof& P) {
   cudaStream_t s = c->stream;
   launch_arm(c->p, c->b, s);
   // the FP32 grid basis is one matrix-powers launch for all s levels
-  const bool powers = sizeof(TK) == sizeof(float) && c->p.use_powers && !c->p.precond;
+  const bool powers = sizeof(TK) == sizeof(float) && c->p.use_powers && !c->p.precond && c->p.pow_shape != kPowLevels;
   Work w;
   for (int n = 0; n < nsteps; ++n) {
     MB4_CHECK(count_work(c, true, &w));

@@ -142,6 +142,20 @@ __global__ void __launch_bounds__(kPowThreads) k_powers(StepParams p, const floa
   else powers_tile<SK, TX, TY>(p, jc, v, ic[b], b, blockIdx.x, smem_raw);
 }
 
+// One warp per tile (form 3): kPowWarpsPerBlock tiles per block, no shared memory.
+template <int SK, int TY>
+__global__ void __launch_bounds__(32 * kPowWarpsPerBlock, TY <= 4 ? 4 : 3)
+    k_powers_warp(StepParams p, const float4* __restrict__ jc, float2* __restrict__ v,
+                  const InstConst* __restrict__ ic, const InstStatus* is, int ntiles) {
+  pdl_wait();
+  pdl_launch_dependents();
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
+  const int tile = blockIdx.x * kPowWarpsPerBlock + (threadIdx.x >> 5);
+  if (tile >= ntiles) return;                    // whole warps leave: the shuffles see full warps
+  powers_warp<SK, TY>(p, jc, v, ic[b], b, tile);
+}
+
 template <typename TK, int SK, int CL>
 __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename Vec2<TK>::type* __restrict__ v,
                                                   double* __restrict__ part, double* __restrict__ coef,
@@ -187,13 +201,43 @@ __global__ void __launch_bounds__(256) k_gram_lsq(StepParams p, const typename V
   gram_lsq_solve<SK>(p, part, coef, ic, is, inst, i, nb);
 }
 
+// One warp per strip of H rows (form 4).
+// Two rows of loads in flight and 4 blocks (16 warps) per SM: measured at 2048^2 against
+// no prefetch (126 us per launch), and against 3 blocks per SM with 2 or 3 rows ahead
+// (128, 124 us): 117 us.
+template <int SK, int H>
+__global__ void __launch_bounds__(32 * kPowWarpsPerBlock, 4)
+    k_powers_stream(StepParams p, const float4* __restrict__ jc, float2* __restrict__ v,
+                    const InstConst* __restrict__ ic, const InstStatus* is, int nstrips) {
+  pdl_wait();
+  pdl_launch_dependents();
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
+  const int strip = blockIdx.x * kPowWarpsPerBlock + (threadIdx.x >> 5);
+  if (strip >= nstrips) return;                  // whole warps leave: the shuffles see full warps
+  powers_stream<SK, H, 2>(p, jc, v, ic[b], b, strip);
+}
+
 template <int SK, int SH>
 void launch_powers_shape(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
-  dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), p.B);
   constexpr int F = kPowShapeForm[SH];
-  launch_k(p.pdl != 0, k_powers<SK, TX, TY, F>, grid, dim3(kPowThreads), pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>(),
-           s, p, (const float4*)b.jc, (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is);
+  if constexpr (F == 3 || F == 4) {
+    constexpr int WX = 32 - 2 * SK;              // the warp's interior width
+    const int ntiles = ((p.nx + WX - 1) / WX) * ((p.ny + TY - 1) / TY);
+    dim3 grid((ntiles + kPowWarpsPerBlock - 1) / kPowWarpsPerBlock, p.B);
+    if constexpr (F == 3)
+      launch_k(p.pdl != 0, k_powers_warp<SK, TY>, grid, dim3(32 * kPowWarpsPerBlock), 0, s, p, (const float4*)b.jc,
+               (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is, ntiles);
+    else
+      launch_k(p.pdl != 0, k_powers_stream<SK, TY>, grid, dim3(32 * kPowWarpsPerBlock), 0, s, p, (const float4*)b.jc,
+               (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is, ntiles);
+  } else {
+    dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), p.B);
+    launch_k(p.pdl != 0, k_powers<SK, TX, TY, F>, grid, dim3(kPowThreads),
+             pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>(), s, p, (const float4*)b.jc, (float2*)b.v,
+             (const InstConst*)b.ic, (const InstStatus*)b.is);
+  }
 }
 
 template <int SK>
@@ -207,6 +251,10 @@ void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
       case 5: launch_powers_shape<SK, 5>(p, b, s); return;
       case 6: launch_powers_shape<SK, 6>(p, b, s); return;
       case 7: launch_powers_shape<SK, 7>(p, b, s); return;
+      case 8: launch_powers_shape<SK, 8>(p, b, s); return;
+      case 9: launch_powers_shape<SK, 9>(p, b, s); return;
+      case 10: launch_powers_shape<SK, 10>(p, b, s); return;
+      case 11: launch_powers_shape<SK, 11>(p, b, s); return;
       default: break;
     }
   }
@@ -218,14 +266,17 @@ template <int SK, int SH>
 bool powers_attr() {
   constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
   constexpr int F = kPowShapeForm[SH];
-  return cudaFuncSetAttribute(k_powers<SK, TX, TY, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>()) == cudaSuccess;
+  if constexpr (F >= 3) return true;             // no shared memory
+  else
+    return cudaFuncSetAttribute(k_powers<SK, TX, TY, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>()) == cudaSuccess;
 }
 template <int SK>
 bool powers_attrs() {
   if constexpr (SK <= kPowShapeMaxS)
     return powers_attr<SK, 0>() && powers_attr<SK, 1>() && powers_attr<SK, 2>() && powers_attr<SK, 3>() &&
-           powers_attr<SK, 4>() && powers_attr<SK, 5>() && powers_attr<SK, 6>() && powers_attr<SK, 7>();
+           powers_attr<SK, 4>() && powers_attr<SK, 5>() && powers_attr<SK, 6>() && powers_attr<SK, 7>() &&
+           powers_attr<SK, 8>() && powers_attr<SK, 9>() && powers_attr<SK, 10>() && powers_attr<SK, 11>();
   else
     return powers_attr<SK, 0>();
 }
@@ -254,7 +305,7 @@ int prepare_powers() {
 template <typename TK>
 void launch_matvecs(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   typedef typename Vec2<TK>::type TK2;
-  if (sizeof(TK) == sizeof(float) && p.use_powers) {
+  if (sizeof(TK) == sizeof(float) && p.use_powers && p.pow_shape != kPowLevels) {
 #define MB4_CALL(N) launch_powers_s<N>(p, b, s)
     MB4_SWITCH_S(MB4_CALL)
 #undef MB4_CALL

@@ -285,11 +285,17 @@ constexpr size_t pow_smem_bytes() {
 // not depend on the shape -- every tile computes each level at each site it holds with
 // the same arithmetic from the same neighbours -- only the halo overhead, the shared
 // memory per block and so the blocks per SM do.
-constexpr int kPowShapes = 8;       // 4, 5: warps keep their rows in registers; 6, 7: one system at a time
-constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64, 32, 64};
-constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16, 16, 16};
-constexpr int kPowShapeForm[kPowShapes] = {0, 0, 0, 0, 1, 1, 2, 2};   // 0 tile, 1 rows, 2 by system
+// Forms 3 and 4 (one warp per tile or per strip: powers_warp, powers_stream) list the warp's
+// extended width, 32: the interior is 32 - 2 s sites wide.
+constexpr int kPowShapes = 12;      // 4, 5: rows in registers; 6, 7: one system at a time; 8, 9: one warp
+                                    // per tile; 10, 11: one warp per strip
+constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64, 32, 64, 32, 32, 32, 32};
+constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16, 16, 16, 4, 8, 8, 16};
+constexpr int kPowShapeForm[kPowShapes] = {0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4};   // 0 tile, 1 rows, 2 by
+                                                                                 // system, 3 warp, 4 strip
+constexpr int kPowWarpsPerBlock = 4;   // form 3: warps (tiles) per block
 constexpr int kPowShapeMaxS = 6;   // larger s: the default tile only
+constexpr int kPowLevels = kPowShapes;   // pow_shape value: no tiles, one stencil launch per level
 
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
@@ -541,6 +547,165 @@ __device__ __forceinline__ void powers_tile_rows(const StepParams& p, const floa
     float2* tmp = src;
     src = dst;
     dst = tmp;
+  }
+}
+
+// A store issued where it stands: the compiler may not sink it below later arithmetic.
+// (Plain stores of each level's interior were all held back to the end of the tile,
+// which kept every level's values live and doubled the registers of powers_warp.)
+__device__ __forceinline__ void st_global_now(float2* p, float2 x) {
+  asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x.x), "f"(x.y) : "memory");
+}
+
+// The same levels built by one warp per tile, in registers: lane l holds column l of a
+// 32-wide extended tile (an interior 32 - 2 SK wide) over TY + 2 SK rows, one system at a
+// time.  The x neighbours come from the adjacent lanes by shuffles and the y neighbours
+// from the thread's own registers, so the form uses no shared memory and no block barrier;
+// warps run their tiles independently.  Level a is valid on lanes and rows a .. end - a;
+// the values outside (from the wrapped shuffles at lanes 0 and 31, or rows not updated)
+// never reach the interior.  Same arithmetic on the same values as powers_tile, so the
+// same basis bit for bit.
+template <int SK, int TY>
+__device__ __forceinline__ void powers_warp(const StepParams& p, const float4* __restrict__ jc,
+                                            float2* __restrict__ v, const InstConst& C, int b, int tile) {
+  constexpr int TX = 32 - 2 * SK, EY = TY + 2 * SK;
+  static_assert(TX >= 1, "the warp's interior is 32 - 2 SK columns");
+  const int S = p.S, nx = p.nx, ny = p.ny;
+  const int tiles_x = (nx + TX - 1) / TX;
+  const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+  const int lane = threadIdx.x & 31;
+  const int gx = txi * TX - SK + lane;           // this lane's column, before wrapping
+  const int gxw = wrap(gx, nx);
+  const int y0w = wrap(tyi * TY - SK, ny);       // the first row, wrapped
+  const bool store_lane = lane >= SK && lane < SK + TX && gx < nx;
+  const float4* jb = jc + plane(b, S);
+  float jx[EY], jy[EY], jz[EY];
+  {
+    int yw = y0w;
+#pragma unroll
+    for (int r = 0; r < EY; ++r) {
+      const float4 j = jb[yw * nx + gxw];          // S < 2^31: a plane's index fits an int
+      jx[r] = j.x;
+      jy[r] = j.y;
+      jz[r] = j.z;
+      yw = (yw + 1 == ny) ? 0 : yw + 1;
+    }
+  }
+  const float tx = C.f_txt, ty = C.f_tyt;
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    float2 u[EY];
+    {
+      const float2* v0 = v + level(b, 0, i, SK, S);
+      int yw = y0w;
+#pragma unroll
+      for (int r = 0; r < EY; ++r) {
+        u[r] = v0[yw * nx + gxw];
+        yw = (yw + 1 == ny) ? 0 : yw + 1;
+      }
+    }
+#pragma unroll
+    for (int a = 1; a <= SK; ++a) {
+      float2 ya = u[a - 1];                      // row r - 1 at level a - 1
+#pragma unroll
+      for (int r = a; r < EY - a; ++r) {
+        const float2 cc = u[r], yb = u[r + 1];
+        float2 xa, xb;
+        xa.x = __shfl_up_sync(0xffffffffu, cc.x, 1);
+        xa.y = __shfl_up_sync(0xffffffffu, cc.y, 1);
+        xb.x = __shfl_down_sync(0xffffffffu, cc.x, 1);
+        xb.y = __shfl_down_sync(0xffffffffu, cc.y, 1);
+        float2 o;
+        o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(jx[r], cc.y, mul_(jz[r], cc.x))));
+        o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-jz[r], cc.y, mul_(-jy[r], cc.x))));
+        ya = cc;
+        u[r] = o;
+      }
+      if (store_lane) {
+        float2* va = v + level(b, a, i, SK, S) + (tyi * TY * nx + gx);
+#pragma unroll
+        for (int r = 0; r < TY; ++r)
+          if (tyi * TY + r < ny) st_global_now(va + r * nx, u[SK + r]);
+      }
+    }
+  }
+}
+
+// The same levels built by one warp walking down a strip of H rows (form 4), for the three
+// systems together: lane l holds column l of a 32-wide strip (an interior 32 - 2 SK wide).
+// At each row t of level 0 read, level a is formed at row t - a from level a - 1 at rows
+// t - a - 1 .. t - a + 1, so each level keeps a window of three rows in registers and the
+// y halo (SK rows above and below the strip) is computed once per strip instead of once
+// per tile.  Row t + PD of level 0 and of J is loaded before row t is used, so PD rows of
+// loads are in flight while the warp computes.  x neighbours come by shuffles, as in
+// powers_warp.  Same arithmetic on the same values as powers_tile, so the same basis bit
+// for bit.
+template <int SK, int H, int PD>
+__device__ __forceinline__ void powers_stream(const StepParams& p, const float4* __restrict__ jc,
+                                              float2* __restrict__ v, const InstConst& C, int b, int strip) {
+  constexpr int TX = 32 - 2 * SK, NR = H + 2 * SK;
+  constexpr int RJ = SK + 1 + PD, R0 = 3 + PD;    // ring sizes: J rows, level-0 rows
+  static_assert(TX >= 1, "the warp's interior is 32 - 2 SK columns");
+  const int S = p.S, nx = p.nx, ny = p.ny;
+  const int tiles_x = (nx + TX - 1) / TX;
+  const int syi = strip / tiles_x, sxi = strip - syi * tiles_x;
+  const int lane = threadIdx.x & 31;
+  const int gx = sxi * TX - SK + lane;           // this lane's column, before wrapping
+  const int gxw = wrap(gx, nx);
+  const int gy0 = syi * H;                       // the strip's first interior row
+  const bool store_lane = lane >= SK && lane < SK + TX && gx < nx;
+  const float4* jb = jc + plane(b, S);
+  const float2* v0 = v + level(b, 0, 0, SK, S);
+  const float tx = C.f_txt, ty = C.f_tyt;
+  float2 w0[3][R0];                              // level 0: [system][row mod R0]
+  float2 w[3][SK > 1 ? SK - 1 : 1][3];           // levels 1 .. SK - 1: [system][level - 1][row mod 3]
+  float jx[RJ], jy[RJ], jz[RJ];                  // J coefficients: row mod RJ
+  int yw = wrap(gy0 - SK, ny);                   // the next level-0 row to load, wrapped
+  auto load_row = [&](int t) {
+    const int off = yw * nx + gxw;               // S < 2^31: a plane's index fits an int
+    const float4 j = jb[off];
+    jx[t % RJ] = j.x;
+    jy[t % RJ] = j.y;
+    jz[t % RJ] = j.z;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w0[i][t % R0] = v0[(size_t)i * S + off];
+    yw = (yw + 1 == ny) ? 0 : yw + 1;
+  };
+#pragma unroll
+  for (int t = 0; t < PD; ++t) load_row(t);
+#pragma unroll
+  for (int t = 0; t < NR; ++t) {
+    if (t + PD < NR) load_row(t + PD);
+#pragma unroll
+    for (int a = 1; a <= SK; ++a) {
+      const int r = t - a;                       // the row level a is formed at
+      if (t < 2 * a) continue;                   // level a starts SK - a rows above the strip
+      const int q = r % RJ;
+      const bool st = r >= SK && r < SK + H && store_lane && gy0 + r - SK < ny;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float2 cc, ya, yb;
+        if (a == 1) {
+          cc = w0[i][r % R0];
+          ya = w0[i][(r - 1) % R0];
+          yb = w0[i][(r + 1) % R0];
+        } else {
+          cc = w[i][a - 2][r % 3];
+          ya = w[i][a - 2][(r + 2) % 3];
+          yb = w[i][a - 2][(r + 1) % 3];
+        }
+        float2 xa, xb;
+        xa.x = __shfl_up_sync(0xffffffffu, cc.x, 1);
+        xa.y = __shfl_up_sync(0xffffffffu, cc.y, 1);
+        xb.x = __shfl_down_sync(0xffffffffu, cc.x, 1);
+        xb.y = __shfl_down_sync(0xffffffffu, cc.y, 1);
+        float2 o;
+        o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(jx[q], cc.y, mul_(jz[q], cc.x))));
+        o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-jz[q], cc.y, mul_(-jy[q], cc.x))));
+        if (a < SK) w[i][a - 1][r % 3] = o;
+        if (st) st_global_now(v + level(b, a, i, SK, S) + ((size_t)(gy0 + r - SK) * nx + gx), o);
+      }
+    }
   }
 }
 

@@ -747,17 +747,36 @@ def test_general_kinetic_matrix_rejects_bad_input(mb4):
         assert rc == mb4.MB4_ERR_INVALID_ARG and not ctx.value
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("tile", list(range(1, 14)))
 def test_matrix_powers_tiles_give_the_same_steps(mb4, tile):
-    """Every matrix-powers tile shape the tuner chooses among (32x16, 32x32, 64x16, 32x8)
-    builds the same FP32 Krylov basis bit for bit, so the mixed step is the same: a grid
-    whose sides are not multiples of any tile (ragged tiles at both edges)."""
+    """Every form of the FP32 Krylov basis the tuner chooses among (the matrix-powers tiles,
+    and one stencil launch per level) builds the same basis bit for bit, so the mixed step
+    is the same: a grid whose sides are not multiples of any tile (ragged tiles at both
+    edges)."""
     w = inputs.Workload("ragged", 100, 70, h=0.005, steps=10, chi=1.0, W=1.0, defect_fraction=0.01, sigma=5.0)
     with mb4.from_workload(w, precision="mixed", powers_tile=tile) as it:
-        assert it.tile_shape() == [(32, 16), (32, 32), (64, 16), (32, 8), (32, 16), (64, 16), (32, 16), (64, 16)][tile - 1]
+        assert it.tile_shape() == [(32, 16), (32, 32), (64, 16), (32, 8), (32, 16), (64, 16), (32, 16), (64, 16),
+                                   (24, 4), (24, 8), (24, 8), (24, 16), (0, 0)][tile - 1]
         it.step(10)
         got = it.get_state()
     with mb4.from_workload(w, precision="mixed", powers_tile=1) as it:
         it.step(10)
         want = it.get_state()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("s", [2, 3, 5, 6])
+@pytest.mark.parametrize("tile", [9, 10, 11, 12, 13])
+def test_warp_and_level_forms_other_s_and_small_grids(mb4, s, tile):
+    """The one-warp tiles and strips (interior 32 - 2s wide) and the per-level launches at
+    every other s they take, on a grid narrower than one warp tile (17 x 13: the tile wraps
+    onto itself, and a strip is taller than the grid) and on a ragged one: the same steps
+    as the 32 x 16 tile."""
+    for nx, ny in ((17, 13), (61, 45)):
+        w = inputs.Workload("small", nx, ny, h=0.005, steps=6, chi=1.0, W=1.0, defect_fraction=0.02, sigma=3.0)
+        out = []
+        for t in (tile, 1):
+            with mb4.from_workload(w, precision="mixed", krylov_s=s, powers_tile=t) as it:
+                it.step(6)
+                out.append(it.get_state())
+        assert np.array_equal(out[0], out[1]), (nx, ny)
