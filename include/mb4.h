@@ -167,8 +167,9 @@ typedef struct {
                             one warp per tile in registers, (32 - 2 krylov_s) x 4 or x 8
                             sites (neighbours by shuffles, no shared memory); 11, 12 = one
                             warp walking down a strip of (32 - 2 krylov_s) x 8 or x 16 sites,
-                            three rows per level in registers; 2..12 need krylov_s <= 6;
-                            13 = no tiles: one stencil launch per level.
+                            three rows per level in registers; 13, 14 = the same strips with
+                            the rows copied ahead through shared memory (cp.async); 2..14
+                            need krylov_s <= 6; 15 = no tiles: one stencil launch per level.
                             Every form gives the same basis bit for bit.                      */
     long long wait_limit; /* persistent = 1: polls (each followed by a short sleep) that a
                             grid-barrier wait makes before it gives up; the step then fails
@@ -388,7 +389,7 @@ int mb4_batch_get_launch_shape(const mb4_batch* b, int* shape8);
 /* The tile (*tx x *ty sites) of the FP32 matrix-powers Krylov basis that the tuner chose
  * for this batch or context (cast an mb4_ctx* to mb4_batch*: a context is a batch of one),
  * or 0 x 0 where that kernel is not used (FP64 mode, the preconditioner, a general K, or a
- * basis built by one stencil launch per level, option powers_tile = 13 or the tuner's choice).
+ * basis built by one stencil launch per level, option powers_tile = 15 or the tuner's choice).
  * Every tile gives the same basis bit for bit. */
 int mb4_batch_get_tile_shape(const mb4_batch* b, int* tx, int* ty);
 

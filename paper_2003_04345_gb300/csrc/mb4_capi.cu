@@ -439,7 +439,7 @@ long long batch_bytes(int nx, int ny, int B, const mb4_options& o) {
 // candidate: its loop made the default launch 5% slower, so it is not offered.)
 typedef std::tuple<int, int, int, int, int, int, int> TuneKey;   // device, precision, nx, ny, B, s, precond
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 5>> g_tune;   // threads of the four per-site groups, powers tile shape
+std::map<TuneKey, std::array<int, 5>> g_tune;   // threads of the four per-site groups, the FP32 basis form
 
 // which: 0 residual, 1 FP64 stencil basis, 2 update (bs = threads per block), 3 FP32 matrix
 // powers (bs = tile shape index).

@@ -218,20 +218,40 @@ __global__ void __launch_bounds__(32 * kPowWarpsPerBlock, 4)
   powers_stream<SK, H, 2>(p, jc, v, ic[b], b, strip);
 }
 
+// One warp per strip, rows staged through shared memory (form 5).
+template <int SK, int H>
+__global__ void __launch_bounds__(32 * kPowWarpsPerBlock, 4)
+    k_powers_stream_cp(StepParams p, const float4* __restrict__ jc, float2* __restrict__ v,
+                       const InstConst* __restrict__ ic, const InstStatus* is, int nstrips) {
+  pdl_wait();
+  pdl_launch_dependents();
+  const int b = blockIdx.y;
+  if (!is[b].active) return;
+  const int strip = blockIdx.x * kPowWarpsPerBlock + (threadIdx.x >> 5);
+  if (strip >= nstrips) return;                  // whole warps leave: the shuffles see full warps
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  powers_stream_cp<SK, H, kPowStreamAhead>(p, jc, v, ic[b], b, strip,
+                                           smem_raw + (threadIdx.x >> 5) * pow_cp_warp_bytes<kPowStreamAhead>());
+}
+
 template <int SK, int SH>
 void launch_powers_shape(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
   constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
   constexpr int F = kPowShapeForm[SH];
-  if constexpr (F == 3 || F == 4) {
+  if constexpr (F >= 3) {
     constexpr int WX = 32 - 2 * SK;              // the warp's interior width
     const int ntiles = ((p.nx + WX - 1) / WX) * ((p.ny + TY - 1) / TY);
     dim3 grid((ntiles + kPowWarpsPerBlock - 1) / kPowWarpsPerBlock, p.B);
     if constexpr (F == 3)
       launch_k(p.pdl != 0, k_powers_warp<SK, TY>, grid, dim3(32 * kPowWarpsPerBlock), 0, s, p, (const float4*)b.jc,
                (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is, ntiles);
-    else
+    else if constexpr (F == 4)
       launch_k(p.pdl != 0, k_powers_stream<SK, TY>, grid, dim3(32 * kPowWarpsPerBlock), 0, s, p, (const float4*)b.jc,
                (float2*)b.v, (const InstConst*)b.ic, (const InstStatus*)b.is, ntiles);
+    else
+      launch_k(p.pdl != 0, k_powers_stream_cp<SK, TY>, grid, dim3(32 * kPowWarpsPerBlock),
+               kPowWarpsPerBlock * pow_cp_warp_bytes<kPowStreamAhead>(), s, p, (const float4*)b.jc, (float2*)b.v,
+               (const InstConst*)b.ic, (const InstStatus*)b.is, ntiles);
   } else {
     dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), p.B);
     launch_k(p.pdl != 0, k_powers<SK, TX, TY, F>, grid, dim3(kPowThreads),
@@ -255,6 +275,8 @@ void launch_powers_s(const StepParams& p, const DevBuffers& b, cudaStream_t s) {
       case 9: launch_powers_shape<SK, 9>(p, b, s); return;
       case 10: launch_powers_shape<SK, 10>(p, b, s); return;
       case 11: launch_powers_shape<SK, 11>(p, b, s); return;
+      case 12: launch_powers_shape<SK, 12>(p, b, s); return;
+      case 13: launch_powers_shape<SK, 13>(p, b, s); return;
       default: break;
     }
   }
@@ -266,7 +288,9 @@ template <int SK, int SH>
 bool powers_attr() {
   constexpr int TX = kPowShapeTX[SH], TY = kPowShapeTY[SH];
   constexpr int F = kPowShapeForm[SH];
-  if constexpr (F >= 3) return true;             // no shared memory
+  if constexpr (F == 3 || F == 4) return true;   // no shared memory
+  else if constexpr (F == 5)                     // the per-warp rings: under the 48 KB default
+    return kPowWarpsPerBlock * pow_cp_warp_bytes<kPowStreamAhead>() <= 48 * 1024;
   else
     return cudaFuncSetAttribute(k_powers<SK, TX, TY, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pow_smem_bytes<SK, TX, TY, F == 2 ? 1 : 3>()) == cudaSuccess;
@@ -276,7 +300,8 @@ bool powers_attrs() {
   if constexpr (SK <= kPowShapeMaxS)
     return powers_attr<SK, 0>() && powers_attr<SK, 1>() && powers_attr<SK, 2>() && powers_attr<SK, 3>() &&
            powers_attr<SK, 4>() && powers_attr<SK, 5>() && powers_attr<SK, 6>() && powers_attr<SK, 7>() &&
-           powers_attr<SK, 8>() && powers_attr<SK, 9>() && powers_attr<SK, 10>() && powers_attr<SK, 11>();
+           powers_attr<SK, 8>() && powers_attr<SK, 9>() && powers_attr<SK, 10>() && powers_attr<SK, 11>() &&
+           powers_attr<SK, 12>() && powers_attr<SK, 13>();
   else
     return powers_attr<SK, 0>();
 }

@@ -208,6 +208,33 @@ __device__ __forceinline__ void residual_site(const StepParams& p, const double2
 // v_{a+1} = (J/theta) v_a is built for the three right-hand sides together, and
 // (I - h lam_i J) v_a = v_a - sig_i v_{a+1} with sig_i = h lam_i theta.
 // ---------------------------------------------------------------------------
+// v modulo n in 0 .. n - 1 (periodic grid index).
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// (J/theta) x at one site of the grid stencil from the site's value c and its x-1, x+1,
+// y-1, y+1 neighbours a, bb, e, f (every grid form of the basis uses this sequence):
+//   (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
+//   (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
+template <typename TK, int KM>
+__device__ __forceinline__ typename Vec2<TK>::type grid_jx(const JCoef<TK>& j, const typename Vec2<TK>::type c,
+                                                           const typename Vec2<TK>::type a,
+                                                           const typename Vec2<TK>::type bb,
+                                                           const typename Vec2<TK>::type e,
+                                                           const typename Vec2<TK>::type f, TK tx, TK ty) {
+  typename Vec2<TK>::type o;
+  if constexpr (KM == 1) {                       // theta = tx: tx / theta = 1
+    o.x = fma(j.a, c.x, fma(j.e1, c.y, -fma(ty, e.y + f.y, a.y + bb.y)));
+    o.y = fma(-j.e2, c.x, fma(-j.a, c.y, fma(ty, e.x + f.x, a.x + bb.x)));
+  } else {
+    o.x = fma_(-ty, add_(e.y, f.y), fma_(-tx, add_(a.y, bb.y), fma_(j.e1, c.y, mul_(j.a, c.x))));
+    o.y = fma_(ty, add_(e.x, f.x), fma_(tx, add_(a.x, bb.x), fma_(-j.a, c.y, mul_(-j.e2, c.x))));
+  }
+  return o;
+}
+
 template <typename TK, int KM>
 __device__ __forceinline__ void matvec_site_j(const StepParams& p, const JCoef<TK> j,
                                               typename Vec2<TK>::type* __restrict__ v, int a_in, const InstConst& C,
@@ -235,18 +262,7 @@ __device__ __forceinline__ void matvec_site_j(const StepParams& p, const JCoef<T
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const TK2* P = v + level(b, a_in, i, p.s, S);
-      TK2 c = P[k], a = P[n.xm], bb = P[n.xp], e = P[n.ym], f = P[n.yp];
-      TK2 o;
-      // (J x)_re = a xp + e1 xq - tx (xq_x- + xq_x+) - ty (xq_y- + xq_y+)
-      // (J x)_im = -e2 xp - a xq + tx (xp_x- + xp_x+) + ty (xp_y- + xp_y+)
-      if constexpr (KM == 1) {                 // theta = tx: tx / theta = 1
-        o.x = fma(j.a, c.x, fma(j.e1, c.y, -fma(ty, e.y + f.y, a.y + bb.y)));
-        o.y = fma(-j.e2, c.x, fma(-j.a, c.y, fma(ty, e.x + f.x, a.x + bb.x)));
-      } else {
-        o.x = fma_(-ty, add_(e.y, f.y), fma_(-tx, add_(a.y, bb.y), fma_(j.e1, c.y, mul_(j.a, c.x))));
-        o.y = fma_(ty, add_(e.x, f.x), fma_(tx, add_(a.x, bb.x), fma_(-j.a, c.y, mul_(-j.e2, c.x))));
-      }
-      v[level(b, a_in + 1, i, p.s, S) + k] = o;
+      v[level(b, a_in + 1, i, p.s, S) + k] = grid_jx<TK, KM>(j, P[k], P[n.xm], P[n.xp], P[n.ym], P[n.yp], tx, ty);
     }
   }
 }
@@ -287,20 +303,16 @@ constexpr size_t pow_smem_bytes() {
 // memory per block and so the blocks per SM do.
 // Forms 3 and 4 (one warp per tile or per strip: powers_warp, powers_stream) list the warp's
 // extended width, 32: the interior is 32 - 2 s sites wide.
-constexpr int kPowShapes = 12;      // 4, 5: rows in registers; 6, 7: one system at a time; 8, 9: one warp
-                                    // per tile; 10, 11: one warp per strip
-constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64, 32, 64, 32, 32, 32, 32};
-constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16, 16, 16, 4, 8, 8, 16};
-constexpr int kPowShapeForm[kPowShapes] = {0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4};   // 0 tile, 1 rows, 2 by
-                                                                                 // system, 3 warp, 4 strip
+constexpr int kPowShapes = 14;      // 4, 5: rows in registers; 6, 7: one system at a time; 8, 9: one warp
+                                    // per tile; 10, 11: one warp per strip; 12, 13: strips staged by cp.async
+constexpr int kPowShapeTX[kPowShapes] = {32, 32, 64, 32, 32, 64, 32, 64, 32, 32, 32, 32, 32, 32};
+constexpr int kPowShapeTY[kPowShapes] = {16, 32, 16, 8, 16, 16, 16, 16, 4, 8, 8, 16, 8, 16};
+constexpr int kPowShapeForm[kPowShapes] = {0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 5, 5};   // 0 tile, 1 rows,
+                                          // 2 by system, 3 warp, 4 strip, 5 strip staged through shared memory
+constexpr int kPowStreamAhead = 4;   // form 5: rows copied ahead
 constexpr int kPowWarpsPerBlock = 4;   // form 3: warps (tiles) per block
 constexpr int kPowShapeMaxS = 6;   // larger s: the default tile only
 constexpr int kPowLevels = kPowShapes;   // pow_shape value: no tiles, one stencil launch per level
-
-__device__ __forceinline__ int wrap(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
 
 template <int SK, int TX = kPowTX, int TY = kPowTY>
 __device__ __forceinline__ void powers_tile(const StepParams& p, const float4* __restrict__ jc,
@@ -707,6 +719,113 @@ __device__ __forceinline__ void powers_stream(const StepParams& p, const float4*
       }
     }
   }
+}
+
+// Asynchronous copies global -> shared (cp.async): each lane copies its own words, so a
+// lane that waits for its own groups sees its own data without a warp barrier.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared memory of one warp of powers_stream_cp: rings of PD + 1 rows of J and of level 0.
+template <int PD>
+__host__ __device__ constexpr int pow_cp_warp_bytes() {
+  return (PD + 1) * 32 * ((int)sizeof(float4) + 3 * (int)sizeof(float2));
+}
+
+// powers_stream with the rows staged through shared memory (form 5): row t + PD of J and
+// of level 0 is copied asynchronously (cp.async) into a per-warp ring before row t is
+// used, so PD rows of loads are in flight without holding registers.  Row t then moves
+// from the ring into the same register windows as in powers_stream, and the levels are
+// formed by the same code: the same basis bit for bit.
+template <int SK, int H, int PD>
+__device__ __forceinline__ void powers_stream_cp(const StepParams& p, const float4* __restrict__ jc,
+                                                 float2* __restrict__ v, const InstConst& C, int b, int strip,
+                                                 unsigned char* wsmem) {
+  constexpr int TX = 32 - 2 * SK, NR = H + 2 * SK;
+  constexpr int RS = PD + 1;                      // ring slots (rows t .. t + PD)
+  static_assert(TX >= 1, "the warp's interior is 32 - 2 SK columns");
+  const int S = p.S, nx = p.nx, ny = p.ny;
+  const int tiles_x = (nx + TX - 1) / TX;
+  const int syi = strip / tiles_x, sxi = strip - syi * tiles_x;
+  const int lane = threadIdx.x & 31;
+  const int gx = sxi * TX - SK + lane;
+  const int gxw = wrap(gx, nx);
+  const int gy0 = syi * H;
+  const bool store_lane = lane >= SK && lane < SK + TX && gx < nx;
+  const float4* jb = jc + plane(b, S);
+  const float2* v0 = v + level(b, 0, 0, SK, S);
+  float4* sj = reinterpret_cast<float4*>(wsmem);                     // [RS][32]
+  float2* sv = reinterpret_cast<float2*>(wsmem + RS * 32 * sizeof(float4));   // [RS][3][32]
+  const float tx = C.f_txt, ty = C.f_tyt;
+  float2 w0[3][3];                                // level 0: [system][row mod 3]
+  float2 w[3][SK > 1 ? SK - 1 : 1][3];            // levels 1 .. SK - 1
+  float jx[SK + 1], jy[SK + 1], jz[SK + 1];       // J of rows t - SK .. t: row mod SK + 1
+  int yw = wrap(gy0 - SK, ny);                    // the next row to copy, wrapped
+  auto copy_row = [&](int t) {                    // row t into ring slot t mod RS, one group
+    if (t < NR) {
+      const int off = yw * nx + gxw;
+      cp_async16(&sj[(t % RS) * 32 + lane], jb + off);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) cp_async8(&sv[((t % RS) * 3 + i) * 32 + lane], v0 + (size_t)i * S + off);
+      yw = (yw + 1 == ny) ? 0 : yw + 1;
+    }
+    cp_async_commit();                            // (empty past the last row: the count stays uniform)
+  };
+#pragma unroll
+  for (int t = 0; t < PD; ++t) copy_row(t);
+#pragma unroll
+  for (int t = 0; t < NR; ++t) {
+    copy_row(t + PD);
+    cp_async_wait<PD>();                          // this lane's groups up to row t are complete
+    {
+      const float4 j = sj[(t % RS) * 32 + lane];
+      jx[t % (SK + 1)] = j.x;
+      jy[t % (SK + 1)] = j.y;
+      jz[t % (SK + 1)] = j.z;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w0[i][t % 3] = sv[((t % RS) * 3 + i) * 32 + lane];
+    }
+#pragma unroll
+    for (int a = 1; a <= SK; ++a) {
+      const int r = t - a;
+      if (t < 2 * a) continue;
+      const int q = r % (SK + 1);
+      const bool st = r >= SK && r < SK + H && store_lane && gy0 + r - SK < ny;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float2 cc, ya, yb;
+        if (a == 1) {
+          cc = w0[i][r % 3];
+          ya = w0[i][(r + 2) % 3];
+          yb = w0[i][(r + 1) % 3];
+        } else {
+          cc = w[i][a - 2][r % 3];
+          ya = w[i][a - 2][(r + 2) % 3];
+          yb = w[i][a - 2][(r + 1) % 3];
+        }
+        float2 xa, xb;
+        xa.x = __shfl_up_sync(0xffffffffu, cc.x, 1);
+        xa.y = __shfl_up_sync(0xffffffffu, cc.y, 1);
+        xb.x = __shfl_down_sync(0xffffffffu, cc.x, 1);
+        xb.y = __shfl_down_sync(0xffffffffu, cc.y, 1);
+        float2 o;
+        o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(jx[q], cc.y, mul_(jz[q], cc.x))));
+        o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-jz[q], cc.y, mul_(-jy[q], cc.x))));
+        if (a < SK) w[i][a - 1][r % 3] = o;
+        if (st) st_global_now(v + level(b, a, i, SK, S) + ((size_t)(gy0 + r - SK) * nx + gx), o);
+      }
+    }
+  }
+  cp_async_wait<0>();                             // nothing left in flight into this warp's ring
 }
 
 // Gram accumulators.  FP32 mode: products and per-thread sums in FP32, a

@@ -747,7 +747,7 @@ def test_general_kinetic_matrix_rejects_bad_input(mb4):
         assert rc == mb4.MB4_ERR_INVALID_ARG and not ctx.value
 
 
-@pytest.mark.parametrize("tile", list(range(1, 14)))
+@pytest.mark.parametrize("tile", list(range(1, 16)))
 def test_matrix_powers_tiles_give_the_same_steps(mb4, tile):
     """Every form of the FP32 Krylov basis the tuner chooses among (the matrix-powers tiles,
     and one stencil launch per level) builds the same basis bit for bit, so the mixed step
@@ -756,7 +756,7 @@ def test_matrix_powers_tiles_give_the_same_steps(mb4, tile):
     w = inputs.Workload("ragged", 100, 70, h=0.005, steps=10, chi=1.0, W=1.0, defect_fraction=0.01, sigma=5.0)
     with mb4.from_workload(w, precision="mixed", powers_tile=tile) as it:
         assert it.tile_shape() == [(32, 16), (32, 32), (64, 16), (32, 8), (32, 16), (64, 16), (32, 16), (64, 16),
-                                   (24, 4), (24, 8), (24, 8), (24, 16), (0, 0)][tile - 1]
+                                   (24, 4), (24, 8), (24, 8), (24, 16), (24, 8), (24, 16), (0, 0)][tile - 1]
         it.step(10)
         got = it.get_state()
     with mb4.from_workload(w, precision="mixed", powers_tile=1) as it:
@@ -766,7 +766,7 @@ def test_matrix_powers_tiles_give_the_same_steps(mb4, tile):
 
 
 @pytest.mark.parametrize("s", [2, 3, 5, 6])
-@pytest.mark.parametrize("tile", [9, 10, 11, 12, 13])
+@pytest.mark.parametrize("tile", [9, 10, 11, 12, 13, 14, 15])
 def test_warp_and_level_forms_other_s_and_small_grids(mb4, s, tile):
     """The one-warp tiles and strips (interior 32 - 2s wide) and the per-level launches at
     every other s they take, on a grid narrower than one warp tile (17 x 13: the tile wraps
