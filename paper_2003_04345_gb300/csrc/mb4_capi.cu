@@ -477,6 +477,15 @@ int time_site_kernel(mb4_batch* c, int which, int bs, cudaEvent_t e0, cudaEvent_
   return MB4_OK;
 }
 
+// The fastest of n timed candidates, unless it is within 5% of the default: the margin is
+// above the launch-to-launch noise, and the default is what a run without tuning uses.
+int pick_fastest(const float* t, int n, int dflt) {
+  int best = 0;
+  for (int k = 1; k < n; ++k)
+    if (t[k] < t[best]) best = k;
+  return (t[best] < 0.95f * t[dflt]) ? best : dflt;
+}
+
 void apply_shape(StepParams& p, const std::array<int, 5>& t) {
   p.bs_site = t[0];
   p.bs_residual = t[1];
@@ -512,19 +521,14 @@ int autotune_launch_shapes(mb4_batch* c, const mb4_grid* grid) {
     float t[3];
     for (int k = 0; k < 3 && rc == MB4_OK; ++k) rc = time_site_kernel(c, which, cand[k], e0, e1, &t[k]);
     if (rc != MB4_OK) break;
-    int best = 1;                                  // 128 unless another is clearly faster
-    for (int k = 0; k < 3; ++k)
-      if (t[k] < 0.95f * t[best]) best = k;
-    chosen[which] = cand[best];
+    chosen[which] = cand[pick_fastest(t, 3, 1)];  // 128 unless another is clearly faster
   }
   // FP32 matrix-powers tile: the default 32 x 16 unless another shape is clearly faster
   int shape = c->p.pow_shape;                    // a forced tile (option powers_tile) stays
   if (rc == MB4_OK && mixed && c->p.use_powers && c->p.s <= kPowShapeMaxS && !c->forced_tile) {
     float t[kPowShapes + 1];                       // the tile forms, then one launch per level
     for (int k = 0; k <= kPowShapes && rc == MB4_OK; ++k) rc = time_site_kernel(c, 3, k, e0, e1, &t[k]);
-    if (rc == MB4_OK)
-      for (int k = 1; k <= kPowShapes; ++k)
-        if (t[k] < 0.95f * t[shape]) shape = k;
+    if (rc == MB4_OK) shape = pick_fastest(t, kPowShapes + 1, 0);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
