@@ -643,48 +643,6 @@ __device__ __forceinline__ void powers_warp(const StepParams& p, const float4* _
   }
 }
 
-// One row step of a warp strip (powers_stream, powers_stream_cp): with row t of level 0 in
-// its ring, form level a at row t - a for a = 1 .. SK from level a - 1 at rows t - a - 1 ..
-// t - a + 1, keep it in level a's three-row window, and store the strip's interior rows.
-// t is a compile-time constant after unrolling, so every ring index is a register.
-// w0: level 0, row mod R0; w: levels 1 .. SK - 1, row mod 3; jx/jy/jz: J of row mod RJ.
-template <int SK, int H, int R0, int RJ, int NW>
-__device__ __forceinline__ void stream_levels(int t, const float2 (&w0)[3][R0], float2 (&w)[3][NW][3],
-                                              const float (&jx)[RJ], const float (&jy)[RJ], const float (&jz)[RJ],
-                                              float tx, float ty, float2* __restrict__ v, int b, int S, int nx,
-                                              int ny, int gy0, int gx, bool store_lane) {
-#pragma unroll
-  for (int a = 1; a <= SK; ++a) {
-    const int r = t - a;                         // the row level a is formed at
-    if (t < 2 * a) continue;                     // level a starts SK - a rows above the strip
-    const int q = r % RJ;
-    const bool st = r >= SK && r < SK + H && store_lane && gy0 + r - SK < ny;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      float2 cc, ya, yb;
-      if (a == 1) {
-        cc = w0[i][r % R0];
-        ya = w0[i][(r + R0 - 1) % R0];
-        yb = w0[i][(r + 1) % R0];
-      } else {
-        cc = w[i][a - 2][r % 3];
-        ya = w[i][a - 2][(r + 2) % 3];
-        yb = w[i][a - 2][(r + 1) % 3];
-      }
-      float2 xa, xb;
-      xa.x = __shfl_up_sync(0xffffffffu, cc.x, 1);
-      xa.y = __shfl_up_sync(0xffffffffu, cc.y, 1);
-      xb.x = __shfl_down_sync(0xffffffffu, cc.x, 1);
-      xb.y = __shfl_down_sync(0xffffffffu, cc.y, 1);
-      float2 o;
-      o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(jx[q], cc.y, mul_(jz[q], cc.x))));
-      o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-jz[q], cc.y, mul_(-jy[q], cc.x))));
-      if (a < SK) w[i][a - 1][r % 3] = o;
-      if (st) st_global_now(v + level(b, a, i, SK, S) + ((size_t)(gy0 + r - SK) * nx + gx), o);
-    }
-  }
-}
-
 // The same levels built by one warp walking down a strip of H rows (form 4), for the three
 // systems together: lane l holds column l of a 32-wide strip (an interior 32 - 2 SK wide).
 // At each row t of level 0 read, level a is formed at row t - a from level a - 1 at rows
@@ -730,7 +688,36 @@ __device__ __forceinline__ void powers_stream(const StepParams& p, const float4*
 #pragma unroll
   for (int t = 0; t < NR; ++t) {
     if (t + PD < NR) load_row(t + PD);
-    stream_levels<SK, H, R0, RJ>(t, w0, w, jx, jy, jz, tx, ty, v, b, S, nx, ny, gy0, gx, store_lane);
+#pragma unroll
+    for (int a = 1; a <= SK; ++a) {
+      const int r = t - a;                       // the row level a is formed at
+      if (t < 2 * a) continue;                   // level a starts SK - a rows above the strip
+      const int q = r % RJ;
+      const bool st = r >= SK && r < SK + H && store_lane && gy0 + r - SK < ny;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float2 cc, ya, yb;
+        if (a == 1) {
+          cc = w0[i][r % R0];
+          ya = w0[i][(r - 1) % R0];
+          yb = w0[i][(r + 1) % R0];
+        } else {
+          cc = w[i][a - 2][r % 3];
+          ya = w[i][a - 2][(r + 2) % 3];
+          yb = w[i][a - 2][(r + 1) % 3];
+        }
+        float2 xa, xb;
+        xa.x = __shfl_up_sync(0xffffffffu, cc.x, 1);
+        xa.y = __shfl_up_sync(0xffffffffu, cc.y, 1);
+        xb.x = __shfl_down_sync(0xffffffffu, cc.x, 1);
+        xb.y = __shfl_down_sync(0xffffffffu, cc.y, 1);
+        float2 o;
+        o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(jx[q], cc.y, mul_(jz[q], cc.x))));
+        o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-jz[q], cc.y, mul_(-jy[q], cc.x))));
+        if (a < SK) w[i][a - 1][r % 3] = o;
+        if (st) st_global_now(v + level(b, a, i, SK, S) + ((size_t)(gy0 + r - SK) * nx + gx), o);
+      }
+    }
   }
 }
 
@@ -807,7 +794,36 @@ __device__ __forceinline__ void powers_stream_cp(const StepParams& p, const floa
 #pragma unroll
       for (int i = 0; i < 3; ++i) w0[i][t % 3] = sv[((t % RS) * 3 + i) * 32 + lane];
     }
-    stream_levels<SK, H, 3, SK + 1>(t, w0, w, jx, jy, jz, tx, ty, v, b, S, nx, ny, gy0, gx, store_lane);
+#pragma unroll
+    for (int a = 1; a <= SK; ++a) {
+      const int r = t - a;
+      if (t < 2 * a) continue;
+      const int q = r % (SK + 1);
+      const bool st = r >= SK && r < SK + H && store_lane && gy0 + r - SK < ny;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float2 cc, ya, yb;
+        if (a == 1) {
+          cc = w0[i][r % 3];
+          ya = w0[i][(r + 2) % 3];
+          yb = w0[i][(r + 1) % 3];
+        } else {
+          cc = w[i][a - 2][r % 3];
+          ya = w[i][a - 2][(r + 2) % 3];
+          yb = w[i][a - 2][(r + 1) % 3];
+        }
+        float2 xa, xb;
+        xa.x = __shfl_up_sync(0xffffffffu, cc.x, 1);
+        xa.y = __shfl_up_sync(0xffffffffu, cc.y, 1);
+        xb.x = __shfl_down_sync(0xffffffffu, cc.x, 1);
+        xb.y = __shfl_down_sync(0xffffffffu, cc.y, 1);
+        float2 o;
+        o.x = fma_(-ty, add_(ya.y, yb.y), fma_(-tx, add_(xa.y, xb.y), fma_(jx[q], cc.y, mul_(jz[q], cc.x))));
+        o.y = fma_(ty, add_(ya.x, yb.x), fma_(tx, add_(xa.x, xb.x), fma_(-jz[q], cc.y, mul_(-jy[q], cc.x))));
+        if (a < SK) w[i][a - 1][r % 3] = o;
+        if (st) st_global_now(v + level(b, a, i, SK, S) + ((size_t)(gy0 + r - SK) * nx + gx), o);
+      }
+    }
   }
   cp_async_wait<0>();                             // nothing left in flight into this warp's ring
 }
