@@ -145,3 +145,34 @@ def test_batch_bytes_counts_the_planes_a_batch_allocates(mb4):
         assert mb4.batch_bytes(512, 512, 4, precision=precision) >= 4 * per_site * S
     assert mb4.batch_bytes(512, 512, 1, precision="mixed") < mb4.batch_bytes(512, 512, 1, precision="fp64")
     assert mb4.batch_bytes(2, 512, 1) == -1
+
+
+def test_binding_structs_match_the_header(mb4, tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets of its C typedef in
+    include/mb4.h (compiled here by the host C compiler): a field added to, moved in or
+    renamed in the header without the binding fails here, on the CPU."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [(mb4.Grid, "mb4_grid"), (mb4.Potential, "mb4_potential"), (mb4.Nonlinearity, "mb4_nonlinearity"),
+             (mb4.SparseKinetic, "mb4_sparse_kinetic"), (mb4.Options, "mb4_options"), (mb4.Stats, "mb4_stats"),
+             (mb4.Request, "mb4_request"), (mb4.Result, "mb4_result")]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mb4.h"', "int main(void) {"]
+    want = []
+    for cls, cname in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {name}));')
+            want.append(getattr(cls, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                   check=True)
+    got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
